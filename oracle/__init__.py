@@ -1,0 +1,335 @@
+"""CPU FP64 oracle of the chi^2 M2M step with moving priors (test infrastructure only).
+
+Only tests, the smoke check and the benchmark's CPU-baseline leg may import this
+package. It wraps the plain C implementation in m2m_oracle.c through ctypes; the
+C file is compiled by `build()` with gcc into oracle/_build/liboracle.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+MAX_GROUPS = 4
+MAX_KINDS = 8
+POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
+GEOM = {"annuli": 0, "pixels": 1}
+MODE = {"gwr": 0, "mpr": 1}
+ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
+RULE = {"exp": 0, "euler": 1}
+
+
+def kind_code(name: str) -> int:
+    if name == "mass":
+        return 0
+    if name == "v2":
+        return 1
+    if name.startswith("gh"):
+        return 10 + int(name[2:])
+    raise ValueError(name)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle C source into a shared library (gcc, -ffp-contract=off)."""
+    src = os.path.join(_HERE, "m2m_oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "m2m_oracle.h"))):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                        "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Potential(C.Structure):
+    _fields_ = [("kind", C.c_int), ("G", C.c_double), ("M", C.c_double), ("a", C.c_double),
+                ("Ms", C.c_double), ("rs", C.c_double), ("v0", C.c_double), ("r0", C.c_double),
+                ("q", C.c_double)]
+
+
+class Group(C.Structure):
+    _fields_ = [("geometry", C.c_int), ("n_ap", C.c_int), ("edges", C.POINTER(C.c_double)),
+                ("nx", C.c_int), ("ny", C.c_int), ("xlo", C.c_double), ("xhi", C.c_double),
+                ("ylo", C.c_double), ("yhi", C.c_double), ("n_kinds", C.c_int),
+                ("kinds", C.c_int * MAX_KINDS), ("Vp", C.POINTER(C.c_double)),
+                ("sp", C.POINTER(C.c_double))]
+
+
+class Obs(C.Structure):
+    _fields_ = [("incl_deg", C.c_double), ("n_groups", C.c_int), ("g", Group * MAX_GROUPS)]
+
+
+class Prior(C.Structure):
+    _fields_ = [("mode", C.c_int), ("nE", C.c_int), ("nx", C.c_int), ("e_spacing", C.c_int),
+                ("signed_lz", C.c_int), ("update_every", C.c_int), ("Emin", C.c_double),
+                ("Emax", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("mu", C.c_double),
+                ("alpha", C.c_double), ("renormalize", C.c_int), ("update_rule", C.c_int),
+                ("n_relax", C.c_long)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class Particles(C.Structure):
+    _fields_ = [("n", C.c_long)] + [(k, _DP) for k in ("x", "y", "z", "vx", "vy", "vz", "w")]
+
+
+class State(C.Structure):
+    _fields_ = [("cell", C.POINTER(C.c_int)), ("what", _DP), ("grid_mean", _DP),
+                ("grid_count", C.POINTER(C.c_long)), ("ytil", _DP), ("yraw", _DP),
+                ("delta", _DP), ("chi2", C.c_double), ("W0", C.c_double), ("t", C.c_long)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_SO)
+        L.or_phi.restype = C.c_double
+        L.or_phi.argtypes = [C.POINTER(Potential), C.c_double, C.c_double, C.c_double]
+        L.or_accel.argtypes = [C.POINTER(Potential), C.c_double, C.c_double, C.c_double, _DP, _DP, _DP]
+        L.or_leapfrog.argtypes = [C.POINTER(Potential), C.POINTER(Particles), C.c_double]
+        L.or_hermite.restype = C.c_double
+        L.or_hermite.argtypes = [C.c_int, C.c_double]
+        L.or_gh_kernel.restype = C.c_double
+        L.or_gh_kernel.argtypes = [C.c_int, C.c_double]
+        L.or_num_obs.argtypes = [C.POINTER(Obs)]
+        L.or_kernel_matrix.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP]
+        L.or_observe.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP]
+        L.or_circular_L.restype = C.c_double
+        L.or_circular_L.argtypes = [C.POINTER(Potential), C.c_double]
+        L.or_cell.argtypes = [C.POINTER(Potential), C.POINTER(Prior)] + [C.c_double] * 6 + [_DP, _DP]
+        L.or_force.restype = C.c_double
+        L.or_force.argtypes = [C.POINTER(Obs), C.POINTER(Params), C.c_int, C.c_double, C.c_double] + \
+            [C.c_double] * 6 + [_DP, _DP]
+        L.or_init.argtypes = [C.POINTER(Obs), _DP, _DP, C.POINTER(Prior), C.POINTER(Particles),
+                              C.POINTER(State)]
+        L.or_run.argtypes = [C.POINTER(Potential), C.POINTER(Obs), _DP, _DP, C.POINTER(Prior),
+                             C.POINTER(Params), C.POINTER(Particles), C.POINTER(State), C.c_long]
+        L.or_build_targets.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP, _DP, _DP, _DP,
+                                       _DP, _DP, C.POINTER(C.c_int)]
+        _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+# ---------------------------------------------------------------------------
+# descriptor builders (from plain dicts / workload objects)
+# ---------------------------------------------------------------------------
+
+def potential(d: dict) -> Potential:
+    return Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0),
+                     d.get("Ms", 0.0), d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0),
+                     d.get("q", 1.0))
+
+
+class ObsSet:
+    """Observable descriptor; keeps the numpy arrays it points into alive."""
+
+    def __init__(self, groups, incl_deg=0.0, Vp=None, sp=None):
+        self.groups = groups
+        self.o = Obs()
+        self.o.incl_deg = incl_deg
+        self.o.n_groups = len(groups)
+        self._keep = []
+        self.n_ap_total = sum(g.n_ap for g in groups)
+        self.Vp = np.zeros(self.n_ap_total) if Vp is None else np.ascontiguousarray(Vp, np.float64)
+        self.sp = np.ones(self.n_ap_total) if sp is None else np.ascontiguousarray(sp, np.float64)
+        off = 0
+        for gi, g in enumerate(groups):
+            G = self.o.g[gi]
+            G.geometry = GEOM[g.geometry]
+            G.n_ap = g.n_ap
+            if g.geometry == "annuli":
+                e = np.ascontiguousarray(g.edges, np.float64)
+                self._keep.append(e)
+                G.edges = _dp(e)
+            else:
+                G.nx, G.ny = g.nx, g.ny
+                G.xlo, G.xhi, G.ylo, G.yhi = g.box
+            G.n_kinds = len(g.kinds)
+            for k, name in enumerate(g.kinds):
+                G.kinds[k] = kind_code(name)
+            G.Vp = C.cast(self.Vp.ctypes.data + 8 * off, _DP)
+            G.sp = C.cast(self.sp.ctypes.data + 8 * off, _DP)
+            off += g.n_ap
+        self.J = lib().or_num_obs(C.byref(self.o))
+
+
+def prior(d: dict) -> Prior:
+    return Prior(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
+                 d["update_every"], d["Emin"], d["Emax"])
+
+
+def params(d: dict) -> Params:
+    return Params(d["dt"], d["eps"], d["mu"], d["alpha"], d["renormalize"], RULE[d["update_rule"]],
+                  d["n_relax"])
+
+
+class ParticleSet:
+    """Oracle particle arrays (float64 copies) and their ctypes view."""
+
+    def __init__(self, p: dict):
+        self.a = {k: np.array(p[k], dtype=np.float64, copy=True) for k in
+                  ("x", "y", "z", "vx", "vy", "vz", "w")}
+        self.s = Particles(len(self.a["x"]), *[_dp(self.a[k]) for k in
+                                               ("x", "y", "z", "vx", "vy", "vz", "w")])
+
+    def __getitem__(self, k):
+        return self.a[k]
+
+
+# ---------------------------------------------------------------------------
+# functions
+# ---------------------------------------------------------------------------
+
+def phi(pot: dict, x, y, z) -> float:
+    P = potential(pot)
+    return lib().or_phi(C.byref(P), x, y, z)
+
+
+def accel(pot: dict, x, y, z):
+    P = potential(pot)
+    a = [C.c_double(), C.c_double(), C.c_double()]
+    lib().or_accel(C.byref(P), x, y, z, *[C.byref(v) for v in a])
+    return np.array([v.value for v in a])
+
+
+def leapfrog(pot: dict, ps: ParticleSet, dt: float):
+    P = potential(pot)
+    lib().or_leapfrog(C.byref(P), C.byref(ps.s), dt)
+
+
+def hermite(n: int, x: float) -> float:
+    return lib().or_hermite(n, x)
+
+
+def gh_kernel(n: int, nu: float) -> float:
+    return lib().or_gh_kernel(n, nu)
+
+
+def kernel_matrix(obs: ObsSet, ps: ParticleSet) -> np.ndarray:
+    K = np.zeros((ps.s.n, obs.J))
+    lib().or_kernel_matrix(C.byref(obs.o), C.byref(ps.s), _dp(K))
+    return K
+
+
+def observe(obs: ObsSet, ps: ParticleSet) -> np.ndarray:
+    y = np.zeros(obs.J)
+    lib().or_observe(C.byref(obs.o), C.byref(ps.s), _dp(y))
+    return y
+
+
+def circular_L(pot: dict, E: float) -> float:
+    P = potential(pot)
+    return lib().or_circular_L(C.byref(P), E)
+
+
+def cells(pot: dict, pri: dict, ps: ParticleSet):
+    P, G = potential(pot), prior(pri)
+    n = ps.s.n
+    c = np.zeros(n, np.int64)
+    E = np.zeros(n)
+    xc = np.zeros(n)
+    e, xx = C.c_double(), C.c_double()
+    a = ps.a
+    for i in range(n):
+        c[i] = lib().or_cell(C.byref(P), C.byref(G), a["x"][i], a["y"][i], a["z"][i],
+                             a["vx"][i], a["vy"][i], a["vz"][i], C.byref(e), C.byref(xx))
+        E[i], xc[i] = e.value, xx.value
+    return c, E, xc
+
+
+def build_targets(obs: ObsSet, target: ParticleSet, err: np.ndarray, noise=None):
+    """Target Y, sigma, and the fitted per-aperture V_p, sigma_p (written into obs)."""
+    J = obs.J
+    err = np.ascontiguousarray(err, np.float64)
+    Y = np.zeros(J)
+    sig = np.zeros(J)
+    it = C.c_int()
+    nz = None if noise is None else np.ascontiguousarray(noise, np.float64)
+    rc = lib().or_build_targets(C.byref(obs.o), C.byref(target.s), _dp(err),
+                                None if nz is None else _dp(nz), _dp(obs.Vp), _dp(obs.sp),
+                                _dp(Y), _dp(sig), C.byref(it))
+    if rc != 0:
+        raise RuntimeError(f"oracle target construction failed ({rc})")
+    # the C routine re-points the group Vp/sp into the same arrays
+    return Y, sig, it.value
+
+
+class Run:
+    """A whole oracle M2M run: particles, targets, priors and smoothed observables."""
+
+    def __init__(self, pot: dict, obs: ObsSet, Y, sig, pri: dict, par: dict, particles: dict):
+        self.P = potential(pot)
+        self.obs = obs
+        self.Y = np.ascontiguousarray(Y, np.float64)
+        self.sig = np.ascontiguousarray(sig, np.float64)
+        self.G = prior(pri)
+        self.par = params(par)
+        self.ps = ParticleSet(particles)
+        n = self.ps.s.n
+        J = obs.J
+        ncell = pri["nE"] * pri["nx"]
+        self.cell = np.zeros(n, np.int32)
+        self.what = np.zeros(n)
+        self.grid_mean = np.zeros(max(ncell, 1))
+        self.grid_count = np.zeros(max(ncell, 1), np.int64)
+        self.ytil = np.zeros(J)
+        self.yraw = np.zeros(J)
+        self.delta = np.zeros(J)
+        self.st = State(self.cell.ctypes.data_as(C.POINTER(C.c_int)), _dp(self.what),
+                        _dp(self.grid_mean), self.grid_count.ctypes.data_as(C.POINTER(C.c_long)),
+                        _dp(self.ytil), _dp(self.yraw), _dp(self.delta), 0.0, 0.0, 0)
+        lib().or_init(C.byref(obs.o), _dp(self.Y), _dp(self.sig), C.byref(self.G),
+                      C.byref(self.ps.s), C.byref(self.st))
+
+    def step(self, n: int) -> int:
+        return lib().or_run(C.byref(self.P), C.byref(self.obs.o), _dp(self.Y), _dp(self.sig),
+                            C.byref(self.G), C.byref(self.par), C.byref(self.ps.s),
+                            C.byref(self.st), n)
+
+    @property
+    def chi2(self) -> float:
+        return self.st.chi2
+
+    @property
+    def t(self) -> int:
+        return self.st.t
+
+    @property
+    def W0(self) -> float:
+        return self.st.W0
+
+    @property
+    def w(self) -> np.ndarray:
+        return self.ps.a["w"]
+
+    def force(self, i: int) -> float:
+        a = self.ps.a
+        return lib().or_force(C.byref(self.obs.o), C.byref(self.par), self.G.mode, a["w"][i],
+                              self.what[i], a["x"][i], a["y"][i], a["z"][i], a["vx"][i],
+                              a["vy"][i], a["vz"][i], _dp(self.delta), _dp(self.sig))
+
+
+def from_workload(wl, target_particles=None):
+    """Oracle observable set + targets for a workload (targets built by the oracle)."""
+    obs = ObsSet(wl.groups, wl.incl_deg)
+    tp = ParticleSet(wl.target if target_particles is None else target_particles)
+    Y, sig, _ = build_targets(obs, tp, wl.err_per_obs(), wl.noise)
+    return obs, Y, sig

@@ -1,0 +1,572 @@
+/*
+ * Plain single-threaded FP64 oracle of the chi^2 M2M step with moving-prior
+ * regularisation (Morganti & Gerhard 2012, arXiv 1202.2355).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests, the smoke check and the CPU baseline
+ * leg of the benchmark; never by the product path. Written for obviousness,
+ * not speed: every sum is a plain loop in particle order, every kernel value is
+ * recomputed from its definition, the circular angular momentum is found by
+ * bisection. Built with -ffp-contract=off so that x86 and Arm give the same
+ * rounding.
+ *
+ * The step, in the order the method states it (Sec. 2.1, eqs. obs, myts,
+ * delta, chi, modFOC; Sec. 2.3.1 for the priors; eq. S+ for the entropy):
+ *   1. advance every particle by one leap-frog (kick-drift-kick) step (Sec. 4.1);
+ *   2. observables y_j = sum_i w_i K_j(z_i)                            (eq. obs);
+ *   3. temporal smoothing, discretised as ytil <- ytil + alpha (y - ytil) (eq. myts);
+ *   4. residuals Delta_j = (ytil_j - Y_j)/sigma_j, chi^2 = sum Delta_j^2 (eqs. delta, chi);
+ *   5. on prior-update steps: bin the particles on the (E, x = L/Lc(E))
+ *      grid, prior of each cell = mean weight in the cell (Sec. 2.3.1);
+ *   6. force of change dw_i/dt = eps w_i (mu dS/dw_i - sum_j K_ij Delta_j/sigma_j)
+ *      (eq. modFOC) with dS/dw_i = -ln(w_i/what_i) for the moving-prior
+ *      entropy (eq. S+) or -ln(w_i/what_i) - 1 for the global weight entropy
+ *      (eq. entropy), integrated over dt with the force held fixed;
+ *   7. optionally rescale the weights to the initial total weight (Sec. 3.2).
+ */
+#include "m2m_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const double OR_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------ */
+/* Potentials (eq. her; eq. log_halo; NFW halo)                        */
+/* ------------------------------------------------------------------ */
+
+/* Enclosed-mass factor of an NFW halo, ln(1+q) - q/(1+q), with its power
+ * series for small q where the two terms cancel. */
+static double nfw_mu(double q)
+{
+    if (q < 1e-3) {
+        double s = 0.0, qk = q * q;
+        for (int k = 2; k <= 9; ++k) {
+            double term = (double)(k - 1) / (double)k * qk;
+            s += (k % 2 == 0) ? term : -term;
+            qk *= q;
+        }
+        return s;
+    }
+    return log1p(q) - q / (1.0 + q);
+}
+
+double or_phi(const or_potential *p, double x, double y, double z)
+{
+    if (p->kind == OR_POT_LOG) {
+        double D = p->r0 * p->r0 + x * x + y * y + z * z / (p->q * p->q);
+        return 0.5 * p->v0 * p->v0 * log(D);
+    }
+    double r = sqrt(x * x + y * y + z * z);
+    double phi = -p->G * p->M / (r + p->a);
+    if (p->kind == OR_POT_HERNQUIST_NFW) {
+        if (r > 0.0)
+            phi += -p->G * p->Ms * log1p(r / p->rs) / r;
+        else
+            phi += -p->G * p->Ms / p->rs;
+    }
+    return phi;
+}
+
+void or_accel(const or_potential *p, double x, double y, double z,
+              double *ax, double *ay, double *az)
+{
+    if (p->kind == OR_POT_LOG) {
+        double q2 = p->q * p->q;
+        double D = p->r0 * p->r0 + x * x + y * y + z * z / q2;
+        double v2 = p->v0 * p->v0;
+        *ax = -v2 * x / D;
+        *ay = -v2 * y / D;
+        *az = -v2 * z / (q2 * D);
+        return;
+    }
+    double r = sqrt(x * x + y * y + z * z);
+    if (r == 0.0) {
+        *ax = *ay = *az = 0.0;
+        return;
+    }
+    /* g(r) = G M(<r)/r^2; acceleration = -g(r) x/r */
+    double g = p->G * p->M / ((r + p->a) * (r + p->a));
+    if (p->kind == OR_POT_HERNQUIST_NFW)
+        g += p->G * p->Ms * nfw_mu(r / p->rs) / (r * r);
+    *ax = -g * x / r;
+    *ay = -g * y / r;
+    *az = -g * z / r;
+}
+
+void or_leapfrog(const or_potential *p, or_particles *s, double dt)
+{
+    for (long i = 0; i < s->n; ++i) {
+        double ax, ay, az;
+        or_accel(p, s->x[i], s->y[i], s->z[i], &ax, &ay, &az);
+        s->vx[i] += 0.5 * dt * ax;
+        s->vy[i] += 0.5 * dt * ay;
+        s->vz[i] += 0.5 * dt * az;
+        s->x[i] += dt * s->vx[i];
+        s->y[i] += dt * s->vy[i];
+        s->z[i] += dt * s->vz[i];
+        or_accel(p, s->x[i], s->y[i], s->z[i], &ax, &ay, &az);
+        s->vx[i] += 0.5 * dt * ax;
+        s->vy[i] += 0.5 * dt * ay;
+        s->vz[i] += 0.5 * dt * az;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Gauss-Hermite functions (Sec. 3.3, eq. lumghn)                      */
+/* ------------------------------------------------------------------ */
+
+/* Physicists' Hermite polynomial from its explicit sum:
+ * H_n(x) = n! sum_{m=0}^{floor(n/2)} (-1)^m (2x)^(n-2m) / (m! (n-2m)!). */
+double or_hermite(int n, double x)
+{
+    double fact[16];
+    fact[0] = 1.0;
+    for (int k = 1; k < 16; ++k) fact[k] = fact[k - 1] * k;
+    double s = 0.0;
+    for (int m = 0; 2 * m <= n; ++m) {
+        double t = fact[n] / (fact[m] * fact[n - 2 * m]) * pow(2.0 * x, n - 2 * m);
+        s += (m % 2 == 0) ? t : -t;
+    }
+    return s;
+}
+
+/* The kernel value of one particle for b_n, with L = 1:
+ * 2 sqrt(pi) u_n(nu), u_n(nu) = (2^(n+1) pi n!)^(-1/2) H_n(nu) exp(-nu^2/2). */
+double or_gh_kernel(int n, double nu)
+{
+    double nfact = 1.0;
+    for (int k = 2; k <= n; ++k) nfact *= k;
+    double norm = 1.0 / sqrt(pow(2.0, n + 1) * OR_PI * nfact);
+    return 2.0 * sqrt(OR_PI) * norm * or_hermite(n, nu) * exp(-0.5 * nu * nu);
+}
+
+/* ------------------------------------------------------------------ */
+/* Observables (eq. obs; surface density in apertures; eq. lumghn)     */
+/* ------------------------------------------------------------------ */
+
+int or_num_obs(const or_obs *o)
+{
+    int J = 0;
+    for (int g = 0; g < o->n_groups; ++g) J += o->g[g].n_kinds * o->g[g].n_ap;
+    return J;
+}
+
+/* Sky position (X, Y) and line-of-sight velocity for a line of sight
+ * n = (0, sin i, cos i) with sky axes e1 = (1,0,0), e2 = (0, cos i, -sin i). */
+static void project(double incl_deg, double x, double y, double z, double vy, double vz,
+                    double *X, double *Y, double *vlos)
+{
+    double i = incl_deg * OR_PI / 180.0;
+    double si = sin(i), ci = cos(i);
+    *X = x;
+    *Y = y * ci - z * si;
+    *vlos = vy * si + vz * ci;
+}
+
+/* Aperture containing sky point (X, Y), or -1. Annuli are half-open
+ * [edge_p, edge_p+1); pixel p = py*nx + px with px = floor((X-xlo) nx/(xhi-xlo)). */
+static int aperture(const or_group *G, double X, double Y, double *area)
+{
+    if (G->geometry == OR_ANNULI) {
+        double R = sqrt(X * X + Y * Y);
+        for (int p = 0; p < G->n_ap; ++p) {
+            if (G->edges[p] <= R && R < G->edges[p + 1]) {
+                *area = OR_PI * (G->edges[p + 1] * G->edges[p + 1] - G->edges[p] * G->edges[p]);
+                return p;
+            }
+        }
+        return -1;
+    }
+    double fx = floor((X - G->xlo) * G->nx / (G->xhi - G->xlo));
+    double fy = floor((Y - G->ylo) * G->ny / (G->yhi - G->ylo));
+    if (fx < 0.0 || fx >= G->nx || fy < 0.0 || fy >= G->ny) return -1;
+    *area = (G->xhi - G->xlo) / G->nx * ((G->yhi - G->ylo) / G->ny);
+    return (int)fy * G->nx + (int)fx;
+}
+
+/* Non-zero entries K_ij of one particle: observable index and value. */
+int or_kernel_row(const or_obs *o, double x, double y, double z,
+                  double vx, double vy, double vz, int *j_out, double *K_out)
+{
+    (void)vx;
+    double X, Y, vlos;
+    project(o->incl_deg, x, y, z, vy, vz, &X, &Y, &vlos);
+    int cnt = 0, off = 0;
+    for (int g = 0; g < o->n_groups; ++g) {
+        const or_group *G = &o->g[g];
+        double area = 0.0;
+        int p = aperture(G, X, Y, &area);
+        if (p >= 0) {
+            for (int k = 0; k < G->n_kinds; ++k) {
+                int kind = G->kinds[k];
+                double K;
+                if (kind == OR_MASS)
+                    K = 1.0 / area;
+                else if (kind == OR_V2)
+                    K = vlos * vlos;
+                else
+                    K = or_gh_kernel(kind - OR_GH0, (vlos - G->Vp[p]) / G->sp[p]);
+                j_out[cnt] = off + k * G->n_ap + p;
+                K_out[cnt] = K;
+                ++cnt;
+            }
+        }
+        off += G->n_kinds * G->n_ap;
+    }
+    return cnt;
+}
+
+/* Dense N x J kernel matrix (row-major), for brute-force checks on tiny N. */
+void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K)
+{
+    int J = or_num_obs(o);
+    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    memset(K, 0, sizeof(double) * (size_t)s->n * (size_t)J);
+    for (long i = 0; i < s->n; ++i) {
+        int c = or_kernel_row(o, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], jj, kk);
+        for (int e = 0; e < c; ++e) K[(size_t)i * J + jj[e]] = kk[e];
+    }
+}
+
+/* y_j = sum_i w_i K_j(z_i) (eq. obs), summed in particle order. */
+void or_observe(const or_obs *o, const or_particles *s, double *y)
+{
+    int J = or_num_obs(o);
+    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    for (int j = 0; j < J; ++j) y[j] = 0.0;
+    for (long i = 0; i < s->n; ++i) {
+        int c = or_kernel_row(o, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], jj, kk);
+        for (int e = 0; e < c; ++e) y[jj[e]] += s->w[i] * kk[e];
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Moving priors on the (E, x) grid (Sec. 2.3.1; signed L_z, Sec. 5)    */
+/* ------------------------------------------------------------------ */
+
+/* Energy of the circular orbit of radius R in the equatorial plane:
+ * E_c(R) = phi(R,0,0) + R/2 dphi/dR. */
+static double circ_energy(const or_potential *p, double R)
+{
+    double ax, ay, az;
+    or_accel(p, R, 0.0, 0.0, &ax, &ay, &az);
+    return or_phi(p, R, 0.0, 0.0) - 0.5 * R * ax;
+}
+
+/* Lc(E): angular momentum of the circular orbit of energy E, found by
+ * bisection on E_c(R) = E. Returns 0 when no circular orbit has energy E
+ * (E at or below the potential minimum, or E >= 0 in a potential that
+ * vanishes at infinity). */
+double or_circular_L(const or_potential *p, double E)
+{
+    if (p->kind != OR_POT_LOG && E >= 0.0) return 0.0;
+    if (E <= circ_energy(p, 0.0)) return 0.0;
+    double hi = 1.0;
+    while (circ_energy(p, hi) <= E && hi < 1e15) hi *= 2.0;
+    double lo = 0.0;
+    for (int it = 0; it < 400; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (circ_energy(p, mid) <= E)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    double R = 0.5 * (lo + hi);
+    double ax, ay, az;
+    or_accel(p, R, 0.0, 0.0, &ax, &ay, &az);
+    double vc2 = -R * ax;
+    return R * sqrt(vc2);
+}
+
+/* Cell (k, l) -> k*nx + l of one particle: E bin k from the chosen spacing
+ * between Emin and Emax (clamped), circularity bin l from x = L/Lc(E)
+ * (x = Lz/Lc(E) on [-1, 1] for the signed variant). */
+int or_cell(const or_potential *p, const or_prior *g, double x, double y, double z,
+            double vx, double vy, double vz, double *E_out, double *xc_out)
+{
+    double E = 0.5 * (vx * vx + vy * vy + vz * vz) + or_phi(p, x, y, z);
+    double Lx = y * vz - z * vy, Ly = z * vx - x * vz, Lz = x * vy - y * vx;
+    double L = g->signed_lz ? Lz : sqrt(Lx * Lx + Ly * Ly + Lz * Lz);
+    double Lc = or_circular_L(p, E);
+    double xc = (Lc > 0.0) ? L / Lc : 0.0;
+    double xmin = g->signed_lz ? -1.0 : 0.0;
+    if (xc < xmin) xc = xmin;
+    if (xc > 1.0) xc = 1.0;
+
+    double f;
+    if (g->e_spacing == OR_E_LOGNEG) {
+        if (E >= 0.0)
+            f = 1.0;
+        else
+            f = (log(-E) - log(-g->Emin)) / (log(-g->Emax) - log(-g->Emin));
+    } else if (g->e_spacing == OR_E_EXP) {
+        f = (exp(E) - exp(g->Emin)) / (exp(g->Emax) - exp(g->Emin));
+    } else {
+        f = (E - g->Emin) / (g->Emax - g->Emin);
+    }
+    double fk = floor(f * g->nE);
+    int k = fk < 0.0 ? 0 : (fk >= g->nE ? g->nE - 1 : (int)fk);
+    double fl = floor((xc - xmin) / (1.0 - xmin) * g->nx);
+    int l = fl < 0.0 ? 0 : (fl >= g->nx ? g->nx - 1 : (int)fl);
+    if (E_out) *E_out = E;
+    if (xc_out) *xc_out = xc;
+    return k * g->nx + l;
+}
+
+/* ------------------------------------------------------------------ */
+/* Force of change (eq. modFOC with eq. S+ or eq. entropy)             */
+/* ------------------------------------------------------------------ */
+
+/* The bracket of eq. modFOC for one particle:
+ * mu dS/dw_i - sum_j K_ij Delta_j / sigma_j. */
+double or_force(const or_obs *o, const or_params *par, int mode, double w_i, double what_i,
+                double x, double y, double z, double vx, double vy, double vz,
+                const double *delta, const double *sig)
+{
+    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    int c = or_kernel_row(o, x, y, z, vx, vy, vz, jj, kk);
+    double data = 0.0;
+    for (int e = 0; e < c; ++e) data += kk[e] * delta[jj[e]] / sig[jj[e]];
+    double dS = -log(w_i / what_i);
+    if (mode == OR_GWR) dS -= 1.0;
+    return par->mu * dS - data;
+}
+
+static void residuals(int J, const double *Y, const double *sig, or_state *st)
+{
+    double c2 = 0.0;
+    for (int j = 0; j < J; ++j) {
+        st->delta[j] = (st->ytil[j] - Y[j]) / sig[j];
+        c2 += st->delta[j] * st->delta[j];
+    }
+    st->chi2 = c2;
+}
+
+void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior *g,
+             const or_particles *s, or_state *st)
+{
+    int J = or_num_obs(o);
+    double W0 = 0.0;
+    for (long i = 0; i < s->n; ++i) W0 += s->w[i];
+    st->W0 = W0;
+    or_observe(o, s, st->yraw);
+    for (int j = 0; j < J; ++j) st->ytil[j] = st->yraw[j];
+    residuals(J, Y, sig, st);
+    for (long i = 0; i < s->n; ++i) {
+        st->what[i] = W0 / (double)s->n;
+        st->cell[i] = 0;
+    }
+    if (g->mode == OR_MPR) {
+        for (int c = 0; c < g->nE * g->nx; ++c) {
+            st->grid_mean[c] = 0.0;
+            st->grid_count[c] = 0;
+        }
+    }
+    st->t = 0;
+}
+
+int or_run(const or_potential *p, const or_obs *o, const double *Y, const double *sig,
+           const or_prior *g, const or_params *par, or_particles *s, or_state *st, long nsteps)
+{
+    int J = or_num_obs(o);
+    int ncell = g->nE * g->nx;
+    double *gsum = NULL;
+    if (g->mode == OR_MPR) {
+        gsum = (double *)malloc(sizeof(double) * (size_t)ncell);
+        if (!gsum) return OR_EARG;
+    }
+    int status = OR_OK;
+    for (long step = 0; step < nsteps; ++step) {
+        long t = st->t + 1;
+        /* 1. push */
+        or_leapfrog(p, s, par->dt);
+        /* 2. observe */
+        or_observe(o, s, st->yraw);
+        /* 3. temporal smoothing */
+        for (int j = 0; j < J; ++j) st->ytil[j] += par->alpha * (st->yraw[j] - st->ytil[j]);
+        /* 4. residuals and chi^2 */
+        residuals(J, Y, sig, st);
+        /* 5. moving priors */
+        if (g->mode == OR_MPR && (t - 1) % g->update_every == 0) {
+            for (int c = 0; c < ncell; ++c) {
+                gsum[c] = 0.0;
+                st->grid_count[c] = 0;
+            }
+            for (long i = 0; i < s->n; ++i) {
+                int c = or_cell(p, g, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i],
+                                NULL, NULL);
+                st->cell[i] = c;
+                gsum[c] += s->w[i];
+                st->grid_count[c] += 1;
+            }
+            for (int c = 0; c < ncell; ++c)
+                st->grid_mean[c] = st->grid_count[c] > 0 ? gsum[c] / (double)st->grid_count[c] : 0.0;
+            for (long i = 0; i < s->n; ++i) st->what[i] = st->grid_mean[st->cell[i]];
+        }
+        /* 6. force of change */
+        if (t > par->n_relax) {
+            for (long i = 0; i < s->n; ++i) {
+                /* w = 0 (reachable by underflow) is a fixed point of eq. modFOC */
+                if (s->w[i] == 0.0) continue;
+                double F = or_force(o, par, g->mode, s->w[i], st->what[i], s->x[i], s->y[i],
+                                    s->z[i], s->vx[i], s->vy[i], s->vz[i], st->delta, sig);
+                double h = par->dt * par->eps * F;
+                double wn = (par->update_rule == OR_UPDATE_EULER) ? s->w[i] * (1.0 + h)
+                                                                  : s->w[i] * exp(h);
+                if (!isfinite(wn) || wn < 0.0 ||
+                    (par->update_rule == OR_UPDATE_EULER && wn <= 0.0))
+                    status = OR_EWEIGHT;
+                s->w[i] = wn;
+            }
+        }
+        /* 7. renormalisation to the initial total weight */
+        if (par->renormalize) {
+            double W = 0.0;
+            for (long i = 0; i < s->n; ++i) W += s->w[i];
+            for (long i = 0; i < s->n; ++i) s->w[i] *= st->W0 / W;
+        }
+        st->t = t;
+        if (status != OR_OK) break;
+    }
+    free(gsum);
+    return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Target observables from a target particle realisation (Sec. 3.3)    */
+/* ------------------------------------------------------------------ */
+
+/* For every aperture: luminosity l_p, then V_p and sigma_p from the mean and
+ * rms line-of-sight velocity, corrected with dh1 = -dV/(sqrt2 sigma),
+ * dh2 = -dsigma/(sqrt2 sigma) (eq. h1h2) until h1 = h2 = 0; then the target
+ * values Y_j and errors sigma_j:
+ *   mass:  Y = l/A,        sigma = err Y               (err relative)
+ *   v2:    Y = l v_rms^2,  sigma = 2 err Y             (err relative on v_rms)
+ *   GH n:  Y = l h_n,      sigma = l err               (err absolute on h_n)
+ * with Gaussian noise sigma*noise added in the observable's own variable
+ * (Y(1+err g), l (v_rms(1+err g))^2, l (h_n + err g)) when noise is given.
+ * Vp_out/sp_out hold sum over groups of n_ap entries; the obs descriptor's
+ * Vp/sp pointers are set to them. */
+int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
+                     const double *noise, double *Vp_out, double *sp_out,
+                     double *Y_out, double *sig_out, int *iters_out)
+{
+    int J = or_num_obs(o);
+    int apoff = 0;
+    int maxit = 0;
+    int nap_total = 0;
+    for (int g = 0; g < o->n_groups; ++g) nap_total += o->g[g].n_ap;
+    double *lum = (double *)calloc((size_t)nap_total, sizeof(double));
+    for (int g = 0; g < o->n_groups; ++g) {
+        or_group *G = &o->g[g];
+        int n_ap = G->n_ap;
+        double *l = (double *)calloc((size_t)n_ap, sizeof(double));
+        double *m1 = (double *)calloc((size_t)n_ap, sizeof(double));
+        double *m2 = (double *)calloc((size_t)n_ap, sizeof(double));
+        double *b1 = (double *)calloc((size_t)n_ap, sizeof(double));
+        double *b2 = (double *)calloc((size_t)n_ap, sizeof(double));
+        double *V = Vp_out + apoff, *S = sp_out + apoff;
+        int has_gh = 0;
+        for (int k = 0; k < G->n_kinds; ++k) has_gh |= G->kinds[k] >= OR_GH0;
+        for (long i = 0; i < tg->n; ++i) {
+            double X, Y, v, area;
+            project(o->incl_deg, tg->x[i], tg->y[i], tg->z[i], tg->vy[i], tg->vz[i], &X, &Y, &v);
+            int p = aperture(G, X, Y, &area);
+            if (p < 0) continue;
+            l[p] += tg->w[i];
+            m1[p] += tg->w[i] * v;
+            m2[p] += tg->w[i] * v * v;
+        }
+        int bad = 0;
+        for (int p = 0; p < n_ap; ++p) {
+            if (l[p] > 0.0) {
+                V[p] = m1[p] / l[p];
+                double var = m2[p] / l[p] - V[p] * V[p];
+                S[p] = var > 0.0 ? sqrt(var) : 0.0;
+            } else {
+                V[p] = 0.0;
+                S[p] = 1.0;
+            }
+            if (has_gh && !(l[p] > 0.0 && S[p] > 0.0)) bad = 1;
+        }
+        G->Vp = V;
+        G->sp = S;
+        for (int p = 0; p < n_ap; ++p) lum[apoff + p] = l[p];
+        if (bad) {
+            free(l); free(m1); free(m2); free(b1); free(b2); free(lum);
+            return OR_ETARGET;
+        }
+        if (has_gh) {
+            int it;
+            for (it = 0; it < 200; ++it) {
+                for (int p = 0; p < n_ap; ++p) b1[p] = b2[p] = 0.0;
+                for (long i = 0; i < tg->n; ++i) {
+                    double X, Y, v, area;
+                    project(o->incl_deg, tg->x[i], tg->y[i], tg->z[i], tg->vy[i], tg->vz[i],
+                            &X, &Y, &v);
+                    int p = aperture(G, X, Y, &area);
+                    if (p < 0) continue;
+                    double nu = (v - V[p]) / S[p];
+                    b1[p] += tg->w[i] * or_gh_kernel(1, nu);
+                    b2[p] += tg->w[i] * or_gh_kernel(2, nu);
+                }
+                double worst = 0.0;
+                for (int p = 0; p < n_ap; ++p) {
+                    double h1 = b1[p] / l[p], h2 = b2[p] / l[p];
+                    if (fabs(h1) > worst) worst = fabs(h1);
+                    if (fabs(h2) > worst) worst = fabs(h2);
+                    double s_old = S[p];
+                    V[p] += sqrt(2.0) * s_old * h1;
+                    S[p] += sqrt(2.0) * s_old * h2;
+                }
+                if (worst <= 1e-12) break;
+            }
+            if (it > maxit) maxit = it;
+        }
+        apoff += n_ap;
+        free(m1); free(m2); free(b1); free(b2);
+        free(l);
+    }
+    /* final observables with the fitted Gaussian parameters */
+    double *y = (double *)calloc((size_t)J, sizeof(double));
+    or_observe(o, tg, y);
+    int off = 0;
+    apoff = 0;
+    for (int g = 0; g < o->n_groups; ++g) {
+        const or_group *G = &o->g[g];
+        for (int k = 0; k < G->n_kinds; ++k) {
+            for (int p = 0; p < G->n_ap; ++p) {
+                int j = off + k * G->n_ap + p;
+                int kind = G->kinds[k];
+                double gn = noise ? noise[j] : 0.0;
+                if (kind == OR_MASS) {
+                    sig_out[j] = err[j] * y[j];
+                    Y_out[j] = y[j] * (1.0 + err[j] * gn);
+                } else {
+                    double lp = lum[apoff + p]; /* luminosity of the aperture */
+                    if (kind == OR_V2) {
+                        double vrms = sqrt(y[j] / lp);
+                        double vo = vrms * (1.0 + err[j] * gn);
+                        sig_out[j] = 2.0 * err[j] * y[j];
+                        Y_out[j] = lp * vo * vo;
+                    } else {
+                        double h = y[j] / lp;
+                        sig_out[j] = lp * err[j];
+                        Y_out[j] = lp * (h + err[j] * gn);
+                    }
+                }
+            }
+        }
+        off += G->n_kinds * G->n_ap;
+        apoff += G->n_ap;
+    }
+    free(y);
+    free(lum);
+    if (iters_out) *iters_out = maxit;
+    return OR_OK;
+}

@@ -1,0 +1,120 @@
+/*
+ * Plain single-threaded FP64 CPU oracle of the chi^2 made-to-measure step with
+ * moving-prior regularisation (Morganti & Gerhard 2012, arXiv 1202.2355).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path links or calls this
+ * code: it exists so that tests, the smoke check and the CPU baseline of the
+ * benchmark can compare the CUDA implementation against a slow, literal
+ * transcription of the method. It shares no code, header or table with the
+ * CUDA library.
+ *
+ * Units: G, M, a as given by the potential descriptor (the workloads use
+ * G = M = a = 1). All arrays are caller-owned; nothing here allocates memory
+ * that outlives a call, except where documented.
+ */
+#ifndef M2M_ORACLE_H
+#define M2M_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_GROUPS 4
+#define OR_MAX_KINDS 8
+
+enum { OR_POT_HERNQUIST = 0, OR_POT_HERNQUIST_NFW = 1, OR_POT_LOG = 2 };
+enum { OR_ANNULI = 0, OR_PIXELS = 1 };
+/* observable kinds: surface mass density, luminosity-weighted v_los^2,
+ * and Gauss-Hermite b_n = l h_n for n = 0..6 (kind OR_GH0 + n) */
+enum { OR_MASS = 0, OR_V2 = 1, OR_GH0 = 10 };
+enum { OR_GWR = 0, OR_MPR = 1 };
+enum { OR_E_LOGNEG = 0, OR_E_EXP = 1, OR_E_LINEAR = 2 };
+enum { OR_UPDATE_EXP = 0, OR_UPDATE_EULER = 1 };
+enum { OR_OK = 0, OR_EARG = 1, OR_EWEIGHT = 2, OR_ETARGET = 3 };
+
+typedef struct {
+    int kind;
+    double G, M, a;     /* Hernquist: phi = -G M/(r+a) (eq. her) */
+    double Ms, rs;      /* NFW: phi = -G Ms ln(1+r/rs)/r */
+    double v0, r0, q;   /* flattened log halo (eq. log_halo) */
+} or_potential;
+
+typedef struct {
+    int geometry;       /* OR_ANNULI or OR_PIXELS */
+    int n_ap;           /* number of apertures (annuli, or nx*ny pixels) */
+    const double *edges;/* annuli: n_ap+1 increasing projected radii */
+    int nx, ny;         /* pixels */
+    double xlo, xhi, ylo, yhi;
+    int n_kinds;
+    int kinds[OR_MAX_KINDS];
+    const double *Vp, *sp; /* per aperture: Gaussian parameters of the target LOSVD */
+} or_group;
+
+typedef struct {
+    double incl_deg;    /* line of sight n = (0, sin i, cos i) */
+    int n_groups;
+    or_group g[OR_MAX_GROUPS];
+} or_obs;
+
+typedef struct {
+    int mode;           /* OR_GWR or OR_MPR */
+    int nE, nx;
+    int e_spacing;      /* OR_E_LOGNEG, OR_E_EXP, OR_E_LINEAR */
+    int signed_lz;      /* 0: x = L/Lc in [0,1]; 1: x = Lz/Lc in [-1,1] */
+    int update_every;
+    double Emin, Emax;
+} or_prior;
+
+typedef struct {
+    double dt, eps, mu, alpha;
+    int renormalize;
+    int update_rule;    /* OR_UPDATE_EXP or OR_UPDATE_EULER */
+    long n_relax;
+} or_params;
+
+typedef struct {
+    long n;
+    double *x, *y, *z, *vx, *vy, *vz, *w;
+} or_particles;
+
+typedef struct {
+    int *cell;          /* n: prior cell of each particle (MPR) */
+    double *what;       /* n: prior weight of each particle */
+    double *grid_mean;  /* nE*nx: cell mean weights at the last prior update */
+    long *grid_count;   /* nE*nx */
+    double *ytil;       /* J: temporally smoothed observables */
+    double *yraw;       /* J: observables of the current snapshot */
+    double *delta;      /* J: residuals */
+    double chi2, W0;
+    long t;
+} or_state;
+
+int or_num_obs(const or_obs *o);
+double or_phi(const or_potential *p, double x, double y, double z);
+void or_accel(const or_potential *p, double x, double y, double z,
+              double *ax, double *ay, double *az);
+void or_leapfrog(const or_potential *p, or_particles *s, double dt);
+double or_hermite(int n, double x);
+double or_gh_kernel(int n, double nu);
+int or_kernel_row(const or_obs *o, double x, double y, double z,
+                  double vx, double vy, double vz, int *j_out, double *K_out);
+void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K);
+void or_observe(const or_obs *o, const or_particles *s, double *y);
+double or_circular_L(const or_potential *p, double E);
+int or_cell(const or_potential *p, const or_prior *g, double x, double y, double z,
+            double vx, double vy, double vz, double *E_out, double *xc_out);
+double or_force(const or_obs *o, const or_params *par, int mode, double w_i, double what_i,
+                double x, double y, double z, double vx, double vy, double vz,
+                const double *delta, const double *sig);
+void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior *g,
+             const or_particles *s, or_state *st);
+int or_run(const or_potential *p, const or_obs *o, const double *Y, const double *sig,
+           const or_prior *g, const or_params *par, or_particles *s, or_state *st, long nsteps);
+int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
+                     const double *noise, double *Vp_out, double *sp_out,
+                     double *Y_out, double *sig_out, int *iters_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
