@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""M2M particle-steps/s on one GB300 (or N, one independent fit per GPU).
+
+A "step" is one full M2M step over all particles of one fit: the pending force
+of change, the leap-frog push, the observable deposit, the prior binning on
+update steps, and the finalize (smoothing, residuals, chi^2, priors). The
+default workload is the 1,000,000-particle FP64 Hernquist fit (60 surface-
+density annuli, 30 annuli of v2/h3/h4, 50 x 20 prior grid, dt 0.005).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+recorded by the library on its stream; L2 is flushed (256 MiB write) between
+timed steps, outside the timed events. Max over ranks. `e2e` repeats the run
+through the public API from pinned host buffers: load, K x (step, read chi^2),
+read the weights, wall clock. `--impl reference` times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M2M particle-steps/s (push+observe+MPR weight update) at stated chi2 error, 1 GB300"
+UNIT = "particle-steps/s"
+WORKLOADS = {"c1": 0, "c2": 1, "c3": 2, "c4": 3}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while running (SM clock and throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 3 + k and r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def bytes_per_particle_step(precision: str) -> int:
+    # state read (6 coordinates + weight + 2-byte prior cell) and written (6 + weight)
+    return (6 * 8 + 8 + 2 + 7 * 8) if precision == "fp64" else (6 * 4 + 4 + 2 + 7 * 4)
+
+
+def cpu_baseline(wl_name: str, n_sample: int, steps: int):
+    """The oracle as it stands, single-threaded, on the first n_sample particles of the workload."""
+    import oracle as O
+    from paper_1202_2355_gb300 import workloads as W
+    wl = W.make(wl_name, n=n_sample)
+    obs, Y, sig = O.from_workload(wl)
+    run = O.Run(wl.potential, obs, Y, sig, wl.prior, wl.params, wl.model)
+    t0 = time.perf_counter()
+    rc = run.step(steps)
+    dt = time.perf_counter() - t0
+    assert rc == 0
+    return n_sample * steps / dt, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1202_2355_gb300 import workloads as W
+    O.build()
+    n_sample = args.ref_sample
+    wl = W.make(args.workload, n=n_sample)
+    obs, Y, sig = O.from_workload(wl)
+    run = O.Run(wl.potential, obs, Y, sig, wl.prior, wl.params, wl.model)
+    assert run.step(args.warmup) == 0
+    t0 = time.perf_counter()
+    assert run.step(args.steps) == 0
+    dt = time.perf_counter() - t0
+    v = n_sample * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "sample_particles": n_sample,
+                       "note": "CPU FP64 oracle, single thread, on the first particles of the workload"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n_sample} particles of {wl.name}, {args.steps} steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _e2e(B, wl, Y, sig, Vp, sp, stream, n, K, ws):
+    """Wall-clock seconds of a whole job through the public API: load from pinned host
+    buffers, K x (one step, read chi^2), read the weights back."""
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    pos = torch.from_numpy(np.concatenate([wl.model[k] for k in ("x", "y", "z")])).pin_memory()
+    vel = torch.from_numpy(np.concatenate([wl.model[k] for k in ("vx", "vy", "vz")])).pin_memory()
+    wts = torch.from_numpy(np.ascontiguousarray(wl.model["w"])).pin_memory()
+    wout = torch.empty(n, dtype=torch.float64).pin_memory()
+    fit = B.fit_from_workload(wl, Y, sig, Vp, sp, stream=stream.cuda_stream)
+    lib = B.lib()
+    c2 = C.c_double()
+    J = C.c_int32()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    B._check(lib.m2m_load_particles(fit.h, n, C.cast(pos.data_ptr(), B._DP), C.cast(vel.data_ptr(), B._DP),
+                                    C.cast(wts.data_ptr(), B._DP)), fit.h)
+    for _ in range(K):
+        B._check(lib.m2m_step(fit.h, 1), fit.h)
+        B._check(lib.m2m_get_chi2(fit.h, C.byref(c2), C.byref(J), None), fit.h)
+    B._check(lib.m2m_get_weights(fit.h, C.cast(wout.data_ptr(), B._DP), n), fit.h)
+    dt = time.perf_counter() - t0
+    fit.close()
+    if ws > 1:
+        t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t[0])
+    return dt
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1202_2355_gb300 import binding as B
+    from paper_1202_2355_gb300 import build as BUILD
+    from paper_1202_2355_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    BUILD.build()
+    K, Wm = args.steps, args.warmup
+
+    # one independent fit per rank (its own seed): weak scaling, no collective on the data path
+    wl = W.make(args.workload, seed=rank, n=args.n)
+    if args.precision:
+        wl.precision = args.precision
+    n = wl.n
+    Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
+    stream = torch.cuda.Stream()
+    fit = B.fit_from_workload(wl, Y, sig, Vp, sp, stream=stream.cuda_stream)
+    fit.load(wl.model)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(Wm):
+            fit.step(1)
+            flush.fill_(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    fit.set_timing(True)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                fit.step(1)
+                flush.fill_(1)
+        fit.synchronize()
+        torch.cuda.synchronize()
+    step_ms, fin_ms, nt = fit.timing()
+    fit.set_timing(False)
+    assert nt == K
+    total_ms = step_ms + fin_ms
+    chi2 = fit.chi2()
+    if ws > 1:
+        t = torch.tensor([total_ms, step_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, step_ms = float(t[0]), float(t[1])
+        dist.barrier()
+    fit.close()
+    value = ws * n * K / (total_ms / 1e3)
+
+    # end to end through the public API from pinned host buffers
+    e2e_s = None if args.no_e2e else _e2e(B, wl, Y, sig, Vp, sp, stream, n, K, ws)
+
+    peak, peak_src = _peaks()
+    bpp = bytes_per_particle_step(wl.precision)
+    achieved = bpp * n / (step_ms / K / 1e3) / 1e9
+    line = None
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            import oracle as O
+            O.build()
+            v, dt = cpu_baseline(args.workload, args.cpu_sample, args.cpu_steps)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {args.cpu_sample} particles of {wl.name}, {args.cpu_steps} steps, "
+                             f"{dt:.1f} s single-threaded FP64"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32+i64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "n_particles": n, "observables": wl.J,
+                       "prior_grid": f"{wl.prior['nE']}x{wl.prior['nx']} every {wl.prior['update_every']}",
+                       "dt": wl.params["dt"], "precision": wl.precision,
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"{ws} independent fit(s), one per GPU", "chi2_per_J_end": chi2 / wl.J},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                         "kernel": "k_step", "bytes_per_particle_step": bpp,
+                         "kernel_ms_per_step": step_ms / K, "finalize_ms_per_step": fin_ms / K},
+            "cpu_baseline": cpu,
+            "e2e": None if e2e_s is None else {
+                "value": ws * n * K / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 7 * 8 * n / K, "d2h_bytes_per_step": 8 + 8 * n / K,
+                "note": "load from pinned host memory once, K x (step + chi^2 read), weights read"},
+            "gpu_launches": 2 * K,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--cpu-steps", type=int, default=60)
+    ap.add_argument("--ref-sample", type=int, default=10_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="override the particle count (profiling)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default=None, help="override (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

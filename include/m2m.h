@@ -1,0 +1,240 @@
+/*
+ * m2m.h -- C ABI of the GB300 chi^2 made-to-measure (M2M) particle step with
+ * moving-prior regularisation (Morganti & Gerhard 2012, "Regularizing
+ * made-to-measure particle models of galaxies", arXiv 1202.2355).
+ *
+ * One context holds one fit: N weighted test particles orbiting in a fixed
+ * potential, a set of target observables, and the (E, x) grid of moving
+ * priors. Every step advances the particles by leap-frog (Sec. 4.1), deposits
+ * their weights into the model observables y_j = sum_i w_i K_j(z_i) (eq. obs),
+ * smooths them in time (eq. myts), forms Delta_j and chi^2 (eqs. delta, chi),
+ * bins the particles on the (E, L/Lc(E)) grid every `update_every` steps to
+ * refresh the priors (Sec. 2.3.1), and applies the force of change
+ * dw_i/dt = eps w_i (mu dS/dw_i - sum_j K_ij Delta_j / sigma_j) (eq. modFOC)
+ * with the moving-prior entropy of eq. S+ or the global weight entropy of
+ * eq. entropy.
+ *
+ * Conventions for every call:
+ *  - Plain C types and pointers only. "host" pointers are ordinary CPU memory;
+ *    "device" pointers are CUDA global memory of the context's device.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes
+ *    and of every output buffer it provides. The library owns the context and
+ *    the device memory it allocates, released by m2m_destroy.
+ *  - Every call returns an m2m_status. No exception or longjmp crosses the ABI.
+ *    After an error, m2m_last_error(ctx) gives a one-line description.
+ *  - m2m_step is asynchronous on the context's stream. Errors detected on the
+ *    device (non-finite or negative weights, fixed-point range overflow) are
+ *    latched in a device status word and returned by the next synchronising
+ *    call (m2m_synchronize or any m2m_get_*).
+ *  - Units are those of the potential descriptor (the workloads use G=M=a=1).
+ */
+#ifndef M2M_H
+#define M2M_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct m2m_ctx m2m_ctx;
+
+typedef enum {
+    M2M_OK = 0,
+    M2M_ERR_ARG = 1,          /* invalid argument or descriptor */
+    M2M_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    M2M_ERR_OOM = 3,          /* device allocation failed */
+    M2M_ERR_NONFINITE = 4,    /* a weight became NaN or infinite */
+    M2M_ERR_NEG_WEIGHT = 5,   /* the explicit-Euler update made a weight <= 0 */
+    M2M_ERR_OVERFLOW = 6,     /* a deposit left the fixed-point range (|v|^2 or total weight) */
+    M2M_ERR_TIMEOUT = 7,      /* a bounded device wait expired */
+    M2M_ERR_STATE = 8,        /* call not valid in the current state (e.g. no particles) */
+    M2M_ERR_TARGET = 9        /* target construction failed (empty aperture for a GH kind) */
+} m2m_status;
+
+/* Potentials (all spherical ones are functions of r = |x|). */
+enum {
+    M2M_POT_HERNQUIST = 0,     /* phi = -G M/(r+a)                                  (eq. her) */
+    M2M_POT_HERNQUIST_NFW = 1, /* Hernquist + NFW halo phi_h = -G Ms ln(1+r/rs)/r   */
+    M2M_POT_LOG = 2            /* phi = v0^2/2 ln(r0^2 + R^2 + z^2/q^2)             (eq. log_halo) */
+};
+
+/* Aperture geometries on the sky. */
+enum {
+    M2M_GEOM_ANNULI = 0,       /* half-open annuli edges[p] <= R < edges[p+1] */
+    M2M_GEOM_PIXELS = 1        /* nx*ny pixels over [xlo,xhi) x [ylo,yhi); p = py*nx + px */
+};
+
+/* Observable kinds (kernel K_j of eq. obs, with the aperture selection delta_pi). */
+enum {
+    M2M_OBS_MASS = 0,          /* surface mass density: K = 1/area_p */
+    M2M_OBS_V2 = 1,            /* luminosity-weighted second moment: K = v_los^2 */
+    M2M_OBS_GH0 = 10           /* b_n = l h_n: K = 2 sqrt(pi) u_n(nu), nu = (v_los - V_p)/sigma_p,
+                                  kind M2M_OBS_GH0 + n for n = 0..6 (eq. lumghn) */
+};
+
+enum { M2M_REG_GWR = 0, M2M_REG_MPR = 1 };            /* eq. entropy / eq. S+ with moving priors */
+enum { M2M_E_LOGNEG = 0, M2M_E_EXP = 1, M2M_E_LINEAR = 2 }; /* E-axis bins uniform in ln(-E), exp(E), E */
+enum { M2M_PREC_FP64 = 0, M2M_PREC_MIXED = 1 };
+enum { M2M_UPDATE_EXP = 0, M2M_UPDATE_EULER = 1 };
+
+#define M2M_MAX_GROUPS 4
+#define M2M_MAX_KINDS 8
+
+/* Fixed potential. Unused fields are ignored. */
+typedef struct {
+    int32_t kind;
+    double G, M, a;        /* Hernquist mass and scale length */
+    double Ms, rs;         /* NFW characteristic mass and scale radius */
+    double v0, r0, q;      /* logarithmic halo: velocity scale, core radius, flattening */
+} m2m_potential;
+
+/* One group of apertures sharing a geometry; each group carries n_kinds
+ * observable kinds measured in every one of its n_ap apertures. */
+typedef struct {
+    int32_t geometry;              /* M2M_GEOM_* */
+    int32_t n_ap;                  /* annuli: number of annuli; pixels: must equal nx*ny */
+    const double *edges;           /* host, n_ap+1 strictly increasing radii (annuli only) */
+    int32_t nx, ny;                /* pixels only */
+    double xlo, xhi, ylo, yhi;     /* pixels only */
+    int32_t n_kinds;               /* 1..M2M_MAX_KINDS */
+    int32_t kinds[M2M_MAX_KINDS];  /* M2M_OBS_* */
+    const double *Vp, *sp;         /* host, n_ap each: Gaussian parameters V_p, sigma_p of the target
+                                      LOSVD per aperture (Sec. 3.3); required iff a GH kind is present */
+} m2m_obs_group;
+
+/* The observable set. Observable j is ordered group-major, then kind, then
+ * aperture: j = offset(group) + kind_index * n_ap + p. J = sum n_kinds*n_ap. */
+typedef struct {
+    double incl_deg;               /* line of sight n = (0, sin i, cos i); sky axes e1 = (1,0,0),
+                                      e2 = (0, cos i, -sin i); v_los = v . n */
+    int32_t n_groups;              /* 1..M2M_MAX_GROUPS */
+    m2m_obs_group groups[M2M_MAX_GROUPS];
+    const double *Y;               /* host, J target values Y_j */
+    const double *sigY;            /* host, J errors sigma(Y_j) > 0 */
+} m2m_observables;
+
+/* The (E, x) grid of moving priors (Sec. 2.3.1; signed L_z variant of Sec. 5).
+ * Cell (k, l) = k*nx + l. k: E bin, uniform in s(E) = ln(-E), exp(E) or E between
+ * Emin and Emax, clamped to [0, nE-1] (unbound E >= 0 goes to nE-1 with ln(-E)).
+ * l: circularity bin of x = L/Lc(E) in [0,1], or x = Lz/Lc(E) in [-1,1] when
+ * signed_lz, clamped; Lc(E) = 0 (no circular orbit) gives x = 0. For GWR the
+ * grid is unused and the prior is the flat W0/N. */
+typedef struct {
+    int32_t mode;                  /* M2M_REG_GWR or M2M_REG_MPR */
+    int32_t nE, nx;                /* grid shape, nE*nx <= 4096 */
+    int32_t e_spacing;             /* M2M_E_* */
+    int32_t signed_lz;
+    int32_t update_every;          /* priors recomputed at steps t = 1, 1+P, 1+2P, ... */
+    double Emin, Emax;
+} m2m_prior_grid;
+
+typedef struct {
+    int32_t precision;             /* M2M_PREC_FP64: FP64 everywhere. M2M_PREC_MIXED: FP32 state,
+                                      push and kernel values; exact int64 fixed-point bin sums;
+                                      FP64 residuals, chi^2 and prior means */
+    double dt;                     /* leap-frog step */
+    int32_t renormalize;           /* 1: rescale weights to the initial total after each update */
+    int32_t update_rule;           /* M2M_UPDATE_EXP: w <- w exp(eps dt F) (force held fixed over dt);
+                                      M2M_UPDATE_EULER: w <- w (1 + eps dt F) */
+    int64_t n_relax;               /* steps t <= n_relax update no weights (Sec. 4.1) */
+    void *stream;                  /* cudaStream_t to run on; NULL: the library creates one */
+    int32_t block;                 /* threads per block of the step kernel; 0: tuned */
+    int32_t blocks_per_sm;         /* resident blocks per SM; 0: tuned */
+} m2m_options;
+
+/* Create a fit context on the current CUDA device. eps, mu and alpha are the
+ * force-of-change rate (eq. modFOC), the regularisation weight (eq. SF) and the
+ * per-step temporal smoothing factor (eq. myts discretised as
+ * ytil <- ytil + alpha (y - ytil)). All descriptors are copied.
+ * Errors: M2M_ERR_ARG on an invalid descriptor, M2M_ERR_CUDA / M2M_ERR_OOM. */
+m2m_status m2m_create(const m2m_potential *pot, const m2m_observables *obs,
+                      const m2m_prior_grid *prior, double eps, double mu, double alpha,
+                      const m2m_options *opt, m2m_ctx **out);
+
+/* Load n particles from host FP64 arrays: pos = x[0..n) y[0..n) z[0..n) (3n
+ * values, structure of arrays), vel likewise, w = n weights (> 0 or == 0).
+ * Resets the step counter, computes y_0 and sets ytil_0 = y_0, W0 = sum w.
+ * n may be 0. Synchronous. Errors: M2M_ERR_ARG (n < 0, null pointer, weight < 0
+ * or non-finite), M2M_ERR_OOM, M2M_ERR_CUDA. */
+m2m_status m2m_load_particles(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                              const double *w);
+
+/* Same as m2m_load_particles with device FP64 arrays of the same layout. */
+m2m_status m2m_load_particles_device(m2m_ctx *ctx, int64_t n, const double *pos_dev,
+                                     const double *vel_dev, const double *w_dev);
+
+/* Advance nsteps >= 0 M2M steps, asynchronously on the context stream. */
+m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps);
+
+/* Wait for the context stream; report any latched device error. */
+m2m_status m2m_synchronize(m2m_ctx *ctx);
+
+/* Current weights (after the last completed step's update and renormalisation)
+ * into the caller's host array of n values (n must equal the loaded count). */
+m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n);
+
+/* Current positions and velocities, FP64, same layout as m2m_load_particles. */
+m2m_status m2m_get_state(m2m_ctx *ctx, double *pos, double *vel, int64_t n);
+
+/* Smoothed (ytil) and raw (y) observables of the last step; either may be NULL. J must match. */
+m2m_status m2m_get_observables(m2m_ctx *ctx, double *ytil, double *y, int32_t J);
+
+/* chi^2 = sum Delta_j^2 of the last step (eq. chi) and the number of observables J;
+ * delta (J values) receives Delta_j when not NULL. */
+m2m_status m2m_get_chi2(m2m_ctx *ctx, double *chi2, int32_t *J, double *delta);
+
+/* Moving priors of the last update: cell mean weights (nE*nx) and particle counts
+ * (nE*nx); cells (n values) receives each particle's cell. Any may be NULL. */
+m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *counts, int32_t *cells,
+                          int64_t n);
+
+/* Number of steps taken since the last load. */
+m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t);
+
+/* Number of particles currently loaded (0 before the first load). */
+m2m_status m2m_get_particle_count(m2m_ctx *ctx, int64_t *n);
+
+/* Kernel timing. While on, every step kernel and finalize kernel launch is
+ * bracketed by CUDA events recorded on the context stream (graph replay is
+ * off), and m2m_get_timing returns their summed device time in milliseconds
+ * and the number of steps timed since timing was switched on. */
+m2m_status m2m_set_timing(m2m_ctx *ctx, int32_t on);
+m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_kernel_ms, double *finalize_kernel_ms,
+                          int64_t *steps);
+
+/* Write / read the full fit state (particles, weights, priors, smoothed
+ * observables, step counter, pending update) to / from a file. A context
+ * resumed from a file continues bit-identically to an uninterrupted run with
+ * the same descriptors; m2m_load_state rejects a file written for different
+ * descriptors (M2M_ERR_ARG). */
+m2m_status m2m_save_state(m2m_ctx *ctx, const char *path);
+m2m_status m2m_load_state(m2m_ctx *ctx, const char *path);
+
+/* Target observables from a target particle realisation (Sec. 3.3): for each
+ * aperture the luminosity l_p, then V_p and sigma_p from the mean and rms
+ * line-of-sight velocity, corrected with dh1 = -dV/(sqrt2 sigma) and
+ * dh2 = -dsigma/(sqrt2 sigma) (eq. h1h2) until |h1|,|h2| <= 1e-12 (at most 200
+ * iterations); then Y_j and sigma_j from the per-observable error err[j]
+ * (relative on the surface density, relative on v_rms for M2M_OBS_V2, absolute
+ * on h_n for GH kinds) with optional Gaussian noise noise[j] (standard normals,
+ * may be NULL) added in the same variable. obs->Y/sigY and the groups' Vp/sp are
+ * ignored on input. Outputs are host arrays: Y, sigY (J), Vp, sp (sum of n_ap
+ * over groups, group order). Runs on the device in FP64; synchronous.
+ * Errors: M2M_ERR_TARGET for an empty aperture in a group with a GH kind. */
+m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double *pos,
+                             const double *vel, const double *w, const double *err,
+                             const double *noise, double *Y, double *sigY, double *Vp,
+                             double *sp, int32_t *iterations);
+
+/* One-line description of the last error on this context ("" if none); valid
+ * until the next call on the context. ctx may be NULL for creation errors. */
+const char *m2m_last_error(const m2m_ctx *ctx);
+
+/* Release the context and all device memory it owns. NULL is ignored. */
+void m2m_destroy(m2m_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* M2M_H */

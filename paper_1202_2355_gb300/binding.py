@@ -1,0 +1,309 @@
+"""Python binding of the C ABI in include/m2m.h (ctypes; argument marshalling only).
+
+Every step of the M2M method runs in the CUDA library libm2m.so; this module
+only translates Python values into the C descriptors and back. Importing it
+does not load the library; the first call does, and raises if the library is
+missing (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_SO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libm2m.so")
+_lib = None
+
+MAX_GROUPS = 4
+MAX_KINDS = 8
+POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
+GEOM = {"annuli": 0, "pixels": 1}
+MODE = {"gwr": 0, "mpr": 1}
+ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
+PREC = {"fp64": 0, "mixed": 1}
+RULE = {"exp": 0, "euler": 1}
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NONFINITE", 5: "ERR_NEG_WEIGHT",
+          6: "ERR_OVERFLOW", 7: "ERR_TIMEOUT", 8: "ERR_STATE", 9: "ERR_TARGET"}
+
+
+def kind_code(name: str) -> int:
+    if name == "mass":
+        return 0
+    if name == "v2":
+        return 1
+    if name.startswith("gh"):
+        return 10 + int(name[2:])
+    raise ValueError(f"unknown observable kind {name!r}")
+
+
+class M2MError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class Potential(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("G", C.c_double), ("M", C.c_double), ("a", C.c_double),
+                ("Ms", C.c_double), ("rs", C.c_double), ("v0", C.c_double), ("r0", C.c_double),
+                ("q", C.c_double)]
+
+
+class ObsGroup(C.Structure):
+    _fields_ = [("geometry", C.c_int32), ("n_ap", C.c_int32), ("edges", _DP), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("xlo", C.c_double), ("xhi", C.c_double), ("ylo", C.c_double),
+                ("yhi", C.c_double), ("n_kinds", C.c_int32), ("kinds", C.c_int32 * MAX_KINDS),
+                ("Vp", _DP), ("sp", _DP)]
+
+
+class Observables(C.Structure):
+    _fields_ = [("incl_deg", C.c_double), ("n_groups", C.c_int32), ("groups", ObsGroup * MAX_GROUPS),
+                ("Y", _DP), ("sigY", _DP)]
+
+
+class PriorGrid(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("nE", C.c_int32), ("nx", C.c_int32), ("e_spacing", C.c_int32),
+                ("signed_lz", C.c_int32), ("update_every", C.c_int32), ("Emin", C.c_double),
+                ("Emax", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("dt", C.c_double), ("renormalize", C.c_int32),
+                ("update_rule", C.c_int32), ("n_relax", C.c_int64), ("stream", C.c_void_p),
+                ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+def library_path() -> str:
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO):
+            raise RuntimeError(f"CUDA library {_SO} is not built; run paper_1202_2355_gb300.build.build()")
+        L = C.CDLL(_SO)
+        vp = C.c_void_p
+        L.m2m_create.argtypes = [C.POINTER(Potential), C.POINTER(Observables), C.POINTER(PriorGrid),
+                                 C.c_double, C.c_double, C.c_double, C.POINTER(Options), C.POINTER(vp)]
+        L.m2m_load_particles.argtypes = [vp, C.c_int64, _DP, _DP, _DP]
+        L.m2m_load_particles_device.argtypes = [vp, C.c_int64, vp, vp, vp]
+        L.m2m_step.argtypes = [vp, C.c_int64]
+        L.m2m_synchronize.argtypes = [vp]
+        L.m2m_get_weights.argtypes = [vp, _DP, C.c_int64]
+        L.m2m_get_state.argtypes = [vp, _DP, _DP, C.c_int64]
+        L.m2m_get_observables.argtypes = [vp, _DP, _DP, C.c_int32]
+        L.m2m_get_chi2.argtypes = [vp, _DP, C.POINTER(C.c_int32), _DP]
+        L.m2m_get_priors.argtypes = [vp, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int64]
+        L.m2m_get_step_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.m2m_get_particle_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.m2m_set_timing.argtypes = [vp, C.c_int32]
+        L.m2m_get_timing.argtypes = [vp, _DP, _DP, C.POINTER(C.c_int64)]
+        L.m2m_save_state.argtypes = [vp, C.c_char_p]
+        L.m2m_load_state.argtypes = [vp, C.c_char_p]
+        L.m2m_build_targets.argtypes = [C.POINTER(Observables), C.c_int64, _DP, _DP, _DP, _DP, _DP,
+                                        _DP, _DP, _DP, _DP, C.POINTER(C.c_int32)]
+        L.m2m_last_error.restype = C.c_char_p
+        L.m2m_last_error.argtypes = [vp]
+        L.m2m_destroy.argtypes = [vp]
+        for name in ("m2m_create", "m2m_load_particles", "m2m_load_particles_device", "m2m_step",
+                     "m2m_synchronize", "m2m_get_weights", "m2m_get_state", "m2m_get_observables",
+                     "m2m_get_chi2", "m2m_get_priors", "m2m_get_step_count", "m2m_get_particle_count",
+                     "m2m_save_state", "m2m_set_timing", "m2m_get_timing",
+                     "m2m_load_state", "m2m_build_targets"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        raise M2MError(status, lib().m2m_last_error(ctx).decode())
+
+
+def potential(d: dict) -> Potential:
+    return Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0), d.get("Ms", 0.0),
+                     d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0), d.get("q", 1.0))
+
+
+class ObsDesc:
+    """C observable descriptor built from workload groups; keeps its arrays alive."""
+
+    def __init__(self, groups, incl_deg=0.0, Y=None, sig=None, Vp=None, sp=None):
+        self.o = Observables()
+        self.o.incl_deg = incl_deg
+        self.o.n_groups = len(groups)
+        self._keep = []
+        nap = sum(g.n_ap for g in groups)
+        self.Vp = np.zeros(nap) if Vp is None else np.ascontiguousarray(Vp, np.float64)
+        self.sp = np.ones(nap) if sp is None else np.ascontiguousarray(sp, np.float64)
+        off = 0
+        for gi, g in enumerate(groups):
+            G = self.o.groups[gi]
+            G.geometry = GEOM[g.geometry]
+            G.n_ap = g.n_ap
+            if g.geometry == "annuli":
+                e = np.ascontiguousarray(g.edges, np.float64)
+                self._keep.append(e)
+                G.edges = _dp(e)
+            else:
+                G.nx, G.ny = g.nx, g.ny
+                G.xlo, G.xhi, G.ylo, G.yhi = g.box
+            G.n_kinds = len(g.kinds)
+            for k, name in enumerate(g.kinds):
+                G.kinds[k] = kind_code(name)
+            G.Vp = C.cast(self.Vp.ctypes.data + 8 * off, _DP)
+            G.sp = C.cast(self.sp.ctypes.data + 8 * off, _DP)
+            off += g.n_ap
+        self.J = sum(len(g.kinds) * g.n_ap for g in groups)
+        if Y is not None:
+            self.Y = np.ascontiguousarray(Y, np.float64)
+            self.sig = np.ascontiguousarray(sig, np.float64)
+            self.o.Y = _dp(self.Y)
+            self.o.sigY = _dp(self.sig)
+
+
+def prior_grid(d: dict) -> PriorGrid:
+    return PriorGrid(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
+                     d["update_every"], d["Emin"], d["Emax"])
+
+
+def _soa(p: dict, keys):
+    return np.ascontiguousarray(np.concatenate([np.asarray(p[k], np.float64) for k in keys]))
+
+
+def build_targets(groups, incl_deg, particles: dict, err, noise=None):
+    """Target Y, sigma(Y), V_p, sigma_p from a target realisation (m2m_build_targets)."""
+    d = ObsDesc(groups, incl_deg)
+    n = len(particles["x"])
+    pos = _soa(particles, ("x", "y", "z"))
+    vel = _soa(particles, ("vx", "vy", "vz"))
+    w = np.ascontiguousarray(particles["w"], np.float64)
+    err = np.ascontiguousarray(err, np.float64)
+    nz = None if noise is None else np.ascontiguousarray(noise, np.float64)
+    Y, sig = np.zeros(d.J), np.zeros(d.J)
+    Vp, sp = np.zeros(len(d.Vp)), np.zeros(len(d.sp))
+    it = C.c_int32()
+    _check(lib().m2m_build_targets(C.byref(d.o), n, _dp(pos), _dp(vel), _dp(w), _dp(err), _dp(nz), _dp(Y),
+                                   _dp(sig), _dp(Vp), _dp(sp), C.byref(it)))
+    return Y, sig, Vp, sp, it.value
+
+
+class Fit:
+    """One M2M fit held by the CUDA library (m2m_create ... m2m_destroy)."""
+
+    def __init__(self, potential_desc: dict, groups, incl_deg, Y, sig, Vp, sp, prior: dict,
+                 params: dict, precision: str = "fp64", stream=None, block: int = 0,
+                 blocks_per_sm: int = 0):
+        self.desc = ObsDesc(groups, incl_deg, Y, sig, Vp, sp)
+        self.J = self.desc.J
+        self.ncell = prior["nE"] * prior["nx"] if prior["mode"] == "mpr" else 0
+        P = potential(potential_desc)
+        G = prior_grid(prior)
+        opt = Options(PREC[precision], params["dt"], params["renormalize"], RULE[params["update_rule"]],
+                      params["n_relax"], stream, block, blocks_per_sm)
+        h = C.c_void_p()
+        _check(lib().m2m_create(C.byref(P), C.byref(self.desc.o), C.byref(G), params["eps"], params["mu"],
+                                params["alpha"], C.byref(opt), C.byref(h)))
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().m2m_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, s):
+        _check(s, self.h)
+
+    def load(self, particles: dict):
+        n = len(particles["x"])
+        pos = _soa(particles, ("x", "y", "z"))
+        vel = _soa(particles, ("vx", "vy", "vz"))
+        w = np.ascontiguousarray(particles["w"], np.float64)
+        self._ck(lib().m2m_load_particles(self.h, n, _dp(pos), _dp(vel), _dp(w)))
+        self.n = n
+
+    def load_device(self, n: int, pos_ptr: int, vel_ptr: int, w_ptr: int):
+        self._ck(lib().m2m_load_particles_device(self.h, n, pos_ptr, vel_ptr, w_ptr))
+        self.n = n
+
+    def step(self, nsteps: int = 1):
+        self._ck(lib().m2m_step(self.h, nsteps))
+
+    def synchronize(self):
+        self._ck(lib().m2m_synchronize(self.h))
+
+    def weights(self) -> np.ndarray:
+        w = np.zeros(self.n)
+        self._ck(lib().m2m_get_weights(self.h, _dp(w), self.n))
+        return w
+
+    def state(self):
+        pos, vel = np.zeros(3 * self.n), np.zeros(3 * self.n)
+        self._ck(lib().m2m_get_state(self.h, _dp(pos), _dp(vel), self.n))
+        return pos.reshape(3, self.n), vel.reshape(3, self.n)
+
+    def observables(self):
+        yt, y = np.zeros(self.J), np.zeros(self.J)
+        self._ck(lib().m2m_get_observables(self.h, _dp(yt), _dp(y), self.J))
+        return yt, y
+
+    def chi2(self, with_delta: bool = False):
+        c2 = C.c_double()
+        J = C.c_int32()
+        d = np.zeros(self.J) if with_delta else None
+        self._ck(lib().m2m_get_chi2(self.h, C.byref(c2), C.byref(J), _dp(d)))
+        return (c2.value, d) if with_delta else c2.value
+
+    def priors(self):
+        g = np.zeros(max(self.ncell, 1))
+        cnt = np.zeros(max(self.ncell, 1), np.int64)
+        cells = np.zeros(self.n, np.int32)
+        self._ck(lib().m2m_get_priors(self.h, _dp(g), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
+                                      cells.ctypes.data_as(C.POINTER(C.c_int32)), self.n))
+        return g[:self.ncell], cnt[:self.ncell], cells
+
+    def step_count(self) -> int:
+        t = C.c_int64()
+        self._ck(lib().m2m_get_step_count(self.h, C.byref(t)))
+        return t.value
+
+    def set_timing(self, on: bool):
+        self._ck(lib().m2m_set_timing(self.h, 1 if on else 0))
+
+    def timing(self):
+        a, b, k = C.c_double(), C.c_double(), C.c_int64()
+        self._ck(lib().m2m_get_timing(self.h, C.byref(a), C.byref(b), C.byref(k)))
+        return a.value, b.value, k.value
+
+    def save(self, path: str):
+        self._ck(lib().m2m_save_state(self.h, path.encode()))
+
+    def restore(self, path: str):
+        self._ck(lib().m2m_load_state(self.h, path.encode()))
+        n = C.c_int64()
+        self._ck(lib().m2m_get_particle_count(self.h, C.byref(n)))
+        self.n = n.value
+
+
+def fit_from_workload(wl, Y, sig, Vp, sp, precision: str | None = None, params: dict | None = None,
+                      prior: dict | None = None, **kw) -> Fit:
+    return Fit(wl.potential, wl.groups, wl.incl_deg, Y, sig, Vp, sp, prior or wl.prior,
+               params or wl.params, precision or wl.precision, **kw)

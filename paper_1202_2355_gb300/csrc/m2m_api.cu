@@ -1,0 +1,1157 @@
+// Host runtime of the M2M library: the C ABI declared in include/m2m.h.
+//
+// A context owns the particle state (structure of arrays in HBM), the
+// observable and prior tables, the fixed-point accumulators and a small block
+// of per-step scalars in device memory. A step is two kernels: k_step (one
+// pass over the particles) and k_finalize (one block over the observables and
+// prior cells). Every per-step decision is read from device memory, so a
+// chunk of steps is captured once in a CUDA graph and replayed.
+#include "m2m.h"
+#include "m2m_device.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace m2m;
+
+struct m2m_ctx {
+    Model m{};
+    int precision = 0;
+    int internal = 0;  // allows the internal first-moment kind (target construction)
+    double eps = 0, mu = 0, alpha = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int block = 256, bps = 0, nsm = 0, grid = 0;
+    size_t smem_step = 0, smem_mat = 0;
+
+    // host copies of the descriptors
+    std::vector<double> edges, Vp, isp, Y, sig, obs_post, obs_iscale, area_of_obs, lcE;
+    std::vector<int> obs_kind;
+    uint64_t config_hash = 0;
+
+    // device buffers
+    long long n = 0;
+    long long capacity = 0;
+    void *st[7] = {nullptr};
+    uint16_t *cell = nullptr;
+    double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
+    double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
+    int *d_kind = nullptr;
+    double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
+    long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
+    Scalars *d_sc = nullptr;
+    double *d_wout = nullptr;
+    long long wout_cap = 0;
+    bool loaded = false;
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    std::string err;
+
+    // kernel timing (m2m_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // three per timed step
+    size_t timed = 0;
+};
+
+static thread_local std::string g_create_error;
+
+static m2m_status fail(m2m_ctx *c, m2m_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_error = buf;
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? M2M_ERR_OOM : M2M_ERR_CUDA,       \
+                        "%s: %s", #call, cudaGetErrorString(e_));                                  \
+    } while (0)
+
+static double pow2_floor(double x)
+{
+    int e;
+    std::frexp(x, &e);  // x = f 2^e, f in [0.5, 1)
+    return std::ldexp(1.0, e - 1);
+}
+
+static uint64_t fnv(uint64_t h, const void *p, size_t n)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+static bool is_gh(int kind) { return kind >= kKindGH0 && kind <= kKindGH0 + 6; }
+
+template <class T>
+static void free_dev(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+static void free_state(m2m_ctx *c)
+{
+    for (auto &p : c->st) free_dev(p);
+    free_dev(c->cell);
+    free_dev(c->d_wout);
+    c->capacity = 0;
+    c->wout_cap = 0;
+}
+
+// ------------------------------------------------------------------ creation
+
+static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_observables *obs,
+                              const m2m_prior_grid *pg, const m2m_options *opt)
+{
+    Model &m = ctx->m;
+    if (!pot || !obs || !pg || !opt) return fail(ctx, M2M_ERR_ARG, "null descriptor");
+    if (pot->kind < 0 || pot->kind > 2) return fail(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot->kind);
+    m.pot = pot->kind;
+    m.G = pot->G; m.M = pot->M; m.a = pot->a; m.Ms = pot->Ms; m.rs = pot->rs;
+    m.v0 = pot->v0; m.r0 = pot->r0; m.q = pot->q;
+    if (m.pot != 2 && !(m.a > 0 && m.G >= 0 && m.M >= 0))
+        return fail(ctx, M2M_ERR_ARG, "Hernquist needs a > 0, G >= 0, M >= 0");
+    if (m.pot == 1 && !(m.rs > 0 && m.Ms >= 0)) return fail(ctx, M2M_ERR_ARG, "NFW needs rs > 0, Ms >= 0");
+    if (m.pot == 2 && !(m.r0 > 0 && m.q > 0)) return fail(ctx, M2M_ERR_ARG, "log halo needs r0 > 0, q > 0");
+    if (m.pot == 0) m.phi_min = -m.G * m.M / m.a;
+    else if (m.pot == 1) m.phi_min = -m.G * m.M / m.a - m.G * m.Ms / m.rs;
+    else m.phi_min = m.v0 * m.v0 * std::log(m.r0);
+
+    const double inc = obs->incl_deg * 3.14159265358979323846 / 180.0;
+    m.sin_i = std::sin(inc);
+    m.cos_i = std::cos(inc);
+    if (obs->n_groups < 1 || obs->n_groups > kMaxGroups)
+        return fail(ctx, M2M_ERR_ARG, "n_groups must be 1..%d", kMaxGroups);
+    m.n_groups = obs->n_groups;
+    int J = 0, nap = 0, ned = 0;
+    ctx->edges.clear(); ctx->Vp.clear(); ctx->isp.clear();
+    ctx->obs_kind.clear(); ctx->obs_post.clear(); ctx->area_of_obs.clear();
+    for (int g = 0; g < m.n_groups; ++g) {
+        const m2m_obs_group &S = obs->groups[g];
+        GroupDesc &G = m.g[g];
+        G.geometry = S.geometry;
+        G.n_ap = S.n_ap;
+        G.n_kinds = S.n_kinds;
+        if (S.n_ap < 1) return fail(ctx, M2M_ERR_ARG, "group %d: n_ap must be >= 1", g);
+        if (S.n_kinds < 1 || S.n_kinds > kMaxKinds) return fail(ctx, M2M_ERR_ARG, "group %d: n_kinds must be 1..%d", g, kMaxKinds);
+        G.obs_off = J;
+        G.ap_off = nap;
+        G.edge_off = ned;
+        G.max_gh = -1;
+        std::vector<double> area(S.n_ap);
+        if (S.geometry == M2M_GEOM_ANNULI) {
+            if (!S.edges) return fail(ctx, M2M_ERR_ARG, "group %d: annuli need edges", g);
+            for (int p = 0; p <= S.n_ap; ++p) {
+                if (!std::isfinite(S.edges[p]) || S.edges[p] < 0 || (p > 0 && !(S.edges[p] > S.edges[p - 1])))
+                    return fail(ctx, M2M_ERR_ARG, "group %d: edges must be finite, >= 0 and increasing", g);
+                ctx->edges.push_back(S.edges[p]);
+            }
+            for (int p = 0; p < S.n_ap; ++p)
+                area[p] = 3.14159265358979323846 * (S.edges[p + 1] * S.edges[p + 1] - S.edges[p] * S.edges[p]);
+            ned += S.n_ap + 1;
+        } else if (S.geometry == M2M_GEOM_PIXELS) {
+            if (S.nx < 1 || S.ny < 1 || (long long)S.nx * S.ny != S.n_ap || !(S.xhi > S.xlo) || !(S.yhi > S.ylo))
+                return fail(ctx, M2M_ERR_ARG, "group %d: pixels need nx*ny == n_ap and a non-empty box", g);
+            G.nx = S.nx; G.ny = S.ny;
+            G.xlo = S.xlo; G.ylo = S.ylo; G.xw = S.xhi - S.xlo; G.yw = S.yhi - S.ylo;
+            const double a_pix = (S.xhi - S.xlo) / S.nx * ((S.yhi - S.ylo) / S.ny);
+            for (int p = 0; p < S.n_ap; ++p) area[p] = a_pix;
+        } else {
+            return fail(ctx, M2M_ERR_ARG, "group %d: unknown geometry %d", g, S.geometry);
+        }
+        bool has_gh = false;
+        for (int k = 0; k < S.n_kinds; ++k) {
+            const int kind = S.kinds[k];
+            const bool ok = kind == kKindMass || kind == kKindV2 || is_gh(kind) || (ctx->internal && kind == kKindV1);
+            if (!ok) return fail(ctx, M2M_ERR_ARG, "group %d: unknown observable kind %d", g, kind);
+            G.kinds[k] = kind;
+            if (is_gh(kind)) {
+                has_gh = true;
+                if (kind - kKindGH0 > G.max_gh) G.max_gh = kind - kKindGH0;
+            }
+            for (int p = 0; p < S.n_ap; ++p) {
+                ctx->obs_kind.push_back(kind);
+                ctx->obs_post.push_back(kind == kKindMass ? 1.0 / area[p] : 1.0);
+                ctx->area_of_obs.push_back(area[p]);
+            }
+        }
+        for (int p = 0; p < S.n_ap; ++p) {
+            double v = 0.0, s = 1.0;
+            if (has_gh) {
+                if (!S.Vp || !S.sp) return fail(ctx, M2M_ERR_ARG, "group %d: GH kinds need Vp and sp", g);
+                v = S.Vp[p];
+                s = S.sp[p];
+                if (!std::isfinite(v) || !(s > 0) || !std::isfinite(s))
+                    return fail(ctx, M2M_ERR_ARG, "group %d: sp must be finite and > 0", g);
+            }
+            ctx->Vp.push_back(v);
+            ctx->isp.push_back(1.0 / s);
+        }
+        J += S.n_kinds * S.n_ap;
+        nap += S.n_ap;
+    }
+    m.J = J;
+    m.n_ap_total = nap;
+    m.n_edges_total = ned;
+    ctx->Y.assign(J, 0.0);
+    ctx->sig.assign(J, 1.0);
+    if (obs->Y && obs->sigY) {
+        for (int j = 0; j < J; ++j) {
+            ctx->Y[j] = obs->Y[j];
+            ctx->sig[j] = obs->sigY[j];
+            if (!std::isfinite(ctx->Y[j]) || !(ctx->sig[j] > 0) || !std::isfinite(ctx->sig[j]))
+                return fail(ctx, M2M_ERR_ARG, "observable %d: Y finite and sigY > 0 required", j);
+        }
+    } else if (!ctx->internal) {
+        return fail(ctx, M2M_ERR_ARG, "obs->Y and obs->sigY are required");
+    }
+
+    // priors
+    if (pg->mode != M2M_REG_GWR && pg->mode != M2M_REG_MPR) return fail(ctx, M2M_ERR_ARG, "unknown prior mode");
+    m.mode = pg->mode;
+    m.nE = pg->nE; m.nx = pg->nx;
+    m.e_spacing = pg->e_spacing;
+    m.signed_lz = pg->signed_lz ? 1 : 0;
+    m.update_every = pg->update_every;
+    if (m.mode == M2M_REG_MPR) {
+        if (m.nE < 1 || m.nx < 1 || (long long)m.nE * m.nx > 65535 || m.update_every < 1)
+            return fail(ctx, M2M_ERR_ARG, "MPR grid needs nE, nx >= 1, nE*nx <= 65535, update_every >= 1");
+        const double lo = pg->Emin, hi = pg->Emax;
+        if (!(hi > lo)) return fail(ctx, M2M_ERR_ARG, "prior grid needs Emax > Emin");
+        if (m.e_spacing == M2M_E_LOGNEG) {
+            if (!(hi < 0)) return fail(ctx, M2M_ERR_ARG, "ln(-E) spacing needs Emin < Emax < 0");
+            m.s_lo = std::log(-lo);
+            m.s_den = std::log(-hi) - std::log(-lo);
+        } else if (m.e_spacing == M2M_E_EXP) {
+            m.s_lo = std::exp(lo);
+            m.s_den = std::exp(hi) - std::exp(lo);
+        } else if (m.e_spacing == M2M_E_LINEAR) {
+            m.s_lo = lo;
+            m.s_den = hi - lo;
+        } else {
+            return fail(ctx, M2M_ERR_ARG, "unknown E spacing");
+        }
+        m.ncell = m.nE * m.nx;
+    } else {
+        m.ncell = 0;
+        m.update_every = 1;
+    }
+
+    // circular orbits
+    m.lc_closed = (m.pot == 0) ? 1 : 0;
+    ctx->lcE.clear();
+    if (!m.lc_closed) {
+        const int n = 4096;
+        m.lc_n = n;
+        m.lc_lnr0 = std::log(1e-6);
+        m.lc_dlnr = (std::log(1e8) - m.lc_lnr0) / (n - 1);
+        ctx->lcE.resize(n);
+        for (int k = 0; k < n; ++k) {
+            ctx->lcE[k] = circ_energy<double>(m, std::exp(m.lc_lnr0 + k * m.lc_dlnr));
+            if (k > 0 && !(ctx->lcE[k] > ctx->lcE[k - 1]))
+                return fail(ctx, M2M_ERR_ARG, "circular-orbit energy is not increasing with radius");
+        }
+    } else {
+        m.lc_n = 0;
+    }
+
+    // step
+    if (!std::isfinite(opt->dt) || opt->dt < 0) return fail(ctx, M2M_ERR_ARG, "dt must be finite and >= 0");
+    m.dt = opt->dt;
+    m.eps = ctx->eps;
+    m.mu = ctx->mu;
+    m.alpha = ctx->alpha;
+    m.update_rule = opt->update_rule == M2M_UPDATE_EULER ? 1 : 0;
+    m.renormalize = opt->renormalize ? 1 : 0;
+    m.n_relax = opt->n_relax;
+    if (opt->precision != M2M_PREC_FP64 && opt->precision != M2M_PREC_MIXED)
+        return fail(ctx, M2M_ERR_ARG, "unknown precision");
+    ctx->precision = opt->precision;
+    m.wps = ctx->precision == M2M_PREC_FP64 ? 2 : 1;
+    m.off_total = m.J * m.wps;
+    m.off_grid = (m.J + 1) * m.wps;
+    m.off_count = (m.J + 1 + m.ncell) * m.wps;
+    m.hist_words = m.off_count + m.ncell;
+
+    // descriptor hash (for checkpoint compatibility)
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(h, &m, offsetof(Model, fx_w));
+    h = fnv(h, ctx->edges.data(), ctx->edges.size() * 8);
+    h = fnv(h, ctx->Vp.data(), ctx->Vp.size() * 8);
+    h = fnv(h, ctx->isp.data(), ctx->isp.size() * 8);
+    h = fnv(h, ctx->Y.data(), ctx->Y.size() * 8);
+    h = fnv(h, ctx->sig.data(), ctx->sig.size() * 8);
+    h = fnv(h, &ctx->precision, sizeof(int));
+    ctx->config_hash = h;
+    return M2M_OK;
+}
+
+template <class T, int WPS>
+static m2m_status configure_kernels(m2m_ctx *ctx)
+{
+    ctx->smem_step = step_smem_bytes<T>(ctx->m);
+    ctx->smem_mat = ctx->smem_step - sizeof(long long) * size_t(ctx->m.hist_words);
+    int maxsm = 0;
+    CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    if (ctx->smem_step > size_t(maxsm))
+        return fail(ctx, M2M_ERR_ARG, "observable set and prior grid need %zu B of shared memory (limit %d)",
+                    ctx->smem_step, maxsm);
+    CU(cudaFuncSetAttribute(k_step<T, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_step)));
+    CU(cudaFuncSetAttribute(k_materialize<T, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_mat)));
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, WPS>, ctx->block, ctx->smem_step));
+    if (occ < 1) return fail(ctx, M2M_ERR_ARG, "step kernel cannot be resident with block %d", ctx->block);
+    if (ctx->bps <= 0 || ctx->bps > occ) ctx->bps = occ;
+    return M2M_OK;
+}
+
+static m2m_status upload_tables(m2m_ctx *ctx)
+{
+    const Model &m = ctx->m;
+    auto up = [&](double *&d, const std::vector<double> &v) -> m2m_status {
+        free_dev(d);
+        if (v.empty()) return M2M_OK;
+        CU(cudaMalloc(&d, v.size() * sizeof(double)));
+        CU(cudaMemcpy(d, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        return M2M_OK;
+    };
+    m2m_status s;
+    if ((s = up(ctx->d_edges, ctx->edges)) != M2M_OK) return s;
+    if ((s = up(ctx->d_Vp, ctx->Vp)) != M2M_OK) return s;
+    if ((s = up(ctx->d_isp, ctx->isp)) != M2M_OK) return s;
+    if ((s = up(ctx->d_lcE, ctx->lcE)) != M2M_OK) return s;
+    if ((s = up(ctx->d_Y, ctx->Y)) != M2M_OK) return s;
+    if ((s = up(ctx->d_sig, ctx->sig)) != M2M_OK) return s;
+    if ((s = up(ctx->d_post, ctx->obs_post)) != M2M_OK) return s;
+    free_dev(ctx->d_kind);
+    CU(cudaMalloc(&ctx->d_kind, sizeof(int) * m.J));
+    CU(cudaMemcpy(ctx->d_kind, ctx->obs_kind.data(), sizeof(int) * m.J, cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&ctx->d_iscale, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_c, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_ytil, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_yraw, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_delta, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_prior, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMalloc(&ctx->d_prior_count, sizeof(long long) * (m.ncell + 1)));
+    CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * m.hist_words));
+    CU(cudaMalloc(&ctx->d_acc, sizeof(long long) * 2));
+    CU(cudaMalloc(&ctx->d_sc, sizeof(Scalars)));
+    CU(cudaMemset(ctx->d_c, 0, sizeof(double) * m.J));
+    CU(cudaMemset(ctx->d_ytil, 0, sizeof(double) * m.J));
+    CU(cudaMemset(ctx->d_yraw, 0, sizeof(double) * m.J));
+    CU(cudaMemset(ctx->d_delta, 0, sizeof(double) * m.J));
+    CU(cudaMemset(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMemset(ctx->d_prior_count, 0, sizeof(long long) * (m.ncell + 1)));
+    CU(cudaMemset(ctx->d_hist, 0, sizeof(long long) * m.hist_words));
+    CU(cudaMemset(ctx->d_sc, 0, sizeof(Scalars)));
+    return M2M_OK;
+}
+
+static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs,
+                              const m2m_prior_grid *pg, double eps, double mu, double alpha,
+                              const m2m_options *opt, int internal, m2m_ctx **out)
+{
+    if (!out) return fail(nullptr, M2M_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!std::isfinite(eps) || eps < 0 || !std::isfinite(mu) || mu < 0 || !std::isfinite(alpha) || alpha < 0 || alpha > 1)
+        return fail(nullptr, M2M_ERR_ARG, "eps, mu >= 0 and 0 <= alpha <= 1 required");
+    m2m_ctx *ctx = new (std::nothrow) m2m_ctx();
+    if (!ctx) return fail(nullptr, M2M_ERR_OOM, "host allocation failed");
+    ctx->internal = internal;
+    ctx->eps = eps;
+    ctx->mu = mu;
+    ctx->alpha = alpha;
+    m2m_status s = build_model(ctx, pot, obs, pg, opt);
+    if (s == M2M_OK) {
+        cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    if (s == M2M_OK) {
+        ctx->block = (opt->block > 0) ? opt->block : 256;
+        if (ctx->block % 32 != 0 || ctx->block > 256) s = fail(ctx, M2M_ERR_ARG, "block must be a multiple of 32, <= 256");
+        ctx->bps = opt->blocks_per_sm;
+    }
+    if (s == M2M_OK) {
+        s = ctx->precision == M2M_PREC_FP64 ? configure_kernels<double, 2>(ctx) : configure_kernels<float, 1>(ctx);
+    }
+    if (s == M2M_OK) {
+        if (opt->stream) {
+            ctx->stream = static_cast<cudaStream_t>(opt->stream);
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+            else ctx->own_stream = true;
+        }
+    }
+    if (s == M2M_OK) s = upload_tables(ctx);
+    if (s != M2M_OK) {
+        g_create_error = ctx->err;
+        m2m_destroy(ctx);
+        return s;
+    }
+    *out = ctx;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_create(const m2m_potential *pot, const m2m_observables *obs,
+                                 const m2m_prior_grid *prior, double eps, double mu, double alpha,
+                                 const m2m_options *opt, m2m_ctx **out)
+{
+    return create_impl(pot, obs, prior, eps, mu, alpha, opt, 0, out);
+}
+
+// ------------------------------------------------------------------ launches
+
+static Buffers buffers(m2m_ctx *c)
+{
+    Buffers b;
+    b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE;
+    b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
+    b.c = c->d_c; b.prior = c->d_prior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
+    return b;
+}
+
+template <class T>
+static State<T> state(m2m_ctx *c)
+{
+    State<T> s;
+    s.x = (T *)c->st[0]; s.y = (T *)c->st[1]; s.z = (T *)c->st[2];
+    s.vx = (T *)c->st[3]; s.vy = (T *)c->st[4]; s.vz = (T *)c->st[5]; s.w = (T *)c->st[6];
+    s.cell = c->cell;
+    s.n = c->n;
+    return s;
+}
+
+static int grid_for(m2m_ctx *c)
+{
+    long long need = (c->n + c->block - 1) / c->block;
+    long long g = (long long)c->nsm * c->bps;
+    if (need < g) g = need;
+    return g < 1 ? 1 : int(g);
+}
+
+template <class T, int WPS>
+static void launch_step(m2m_ctx *c, int push, int init)
+{
+    k_step<T, WPS><<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, state<T>(c), buffers(c), push, init);
+    k_finalize<WPS><<<1, 1024, 0, c->stream>>>(c->m, buffers(c), c->n, init);
+}
+
+static void launch_one(m2m_ctx *c, int push, int init)
+{
+    if (c->precision == M2M_PREC_FP64) launch_step<double, 2>(c, push, init);
+    else launch_step<float, 1>(c, push, init);
+}
+
+template <class T, int WPS>
+static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
+{
+    cudaEventRecord(ev[0], c->stream);
+    k_step<T, WPS><<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, state<T>(c), buffers(c), 1, 0);
+    cudaEventRecord(ev[1], c->stream);
+    k_finalize<WPS><<<1, 1024, 0, c->stream>>>(c->m, buffers(c), c->n, 0);
+    cudaEventRecord(ev[2], c->stream);
+}
+
+// ------------------------------------------------------------------ particles
+
+static size_t elem_size(const m2m_ctx *c) { return c->precision == M2M_PREC_FP64 ? 8 : 4; }
+
+static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
+{
+    if (n <= ctx->capacity && ctx->st[0]) return M2M_OK;
+    free_state(ctx);
+    const long long cap = n > 0 ? n : 1;
+    for (auto &p : ctx->st) CU(cudaMalloc(&p, cap * elem_size(ctx)));
+    CU(cudaMalloc(&ctx->cell, cap * sizeof(uint16_t)));
+    ctx->capacity = cap;
+    return M2M_OK;
+}
+
+// Sets the fixed-point scales from the loaded particles, then deposits y_0.
+static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, const double *dz,
+                              const double *dvx, const double *dvy, const double *dvz,
+                              const double *dw, double W0_host)
+{
+    Model &m = ctx->m;
+    unsigned long long *d_v2 = nullptr;
+    unsigned *d_bad = nullptr;
+    CU(cudaMalloc(&d_v2, sizeof(unsigned long long) + sizeof(unsigned)));
+    d_bad = reinterpret_cast<unsigned *>(d_v2 + 1);
+    CU(cudaMemsetAsync(d_v2, 0, sizeof(unsigned long long) + sizeof(unsigned), ctx->stream));
+    if (ctx->n > 0)
+        k_load_stats<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(m, dx, dy, dz, dvx, dvy, dvz, dw, ctx->n, d_v2, d_bad);
+    unsigned long long v2bits = 0;
+    unsigned bad = 0;
+    cudaError_t e = cudaMemcpyAsync(&v2bits, d_v2, sizeof v2bits, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof bad, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d_v2);
+    if (e != cudaSuccess) return fail(ctx, M2M_ERR_CUDA, "load statistics: %s", cudaGetErrorString(e));
+    if (bad) return fail(ctx, M2M_ERR_ARG, "particles must be finite with weights >= 0");
+    double v2max;
+    std::memcpy(&v2max, &v2bits, sizeof v2max);
+    // fixed-point ranges. Weights are deposited before renormalisation, so the total
+    // may exceed W0 by the largest single-step growth exp(eps dt F): FP64 mode keeps
+    // 2^24 W0 of range (the second word still resolves 2^-70 W0), mixed mode 2^12 W0
+    // (resolution 2^-50 W0). Beyond the range the step reports M2M_ERR_OVERFLOW.
+    const double W = W0_host > 0 ? W0_host : 1.0;
+    const double Wb = (ctx->precision == M2M_PREC_FP64 ? 16777216.0 : 4096.0) * W;
+    m.v2max = 2.0 * (v2max > 0 ? v2max : 1.0);
+    const double two62 = 4611686018427387904.0;
+    m.fx_w = pow2_floor(two62 / Wb);
+    m.fx_v2 = pow2_floor(two62 / (Wb * (m.v2max > 1.0 ? m.v2max : 1.0)));
+    m.fx_gh = pow2_floor(two62 / (Wb * 1.5));  // |2 sqrt(pi) u_n| <= sqrt(2) (Cramer's inequality)
+    ctx->obs_iscale.resize(m.J);
+    for (int j = 0; j < m.J; ++j) {
+        const int k = ctx->obs_kind[j];
+        const double s = k == kKindMass ? m.fx_w : ((k == kKindV2 || k == kKindV1) ? m.fx_v2 : m.fx_gh);
+        ctx->obs_iscale[j] = 1.0 / s;
+    }
+    CU(cudaMemcpyAsync(ctx->d_iscale, ctx->obs_iscale.data(), sizeof(double) * m.J, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_hist, 0, sizeof(long long) * m.hist_words, ctx->stream));
+    Scalars sc0{};
+    sc0.Wrange = 9.2233720368547758e18 / m.fx_w;
+    CU(cudaMemcpyAsync(ctx->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_prior_count, 0, sizeof(long long) * (m.ncell + 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->cell, 0, sizeof(uint16_t) * (ctx->n > 0 ? ctx->n : 1), ctx->stream));
+    launch_one(ctx, 0, 1);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    ctx->loaded = true;
+    return M2M_OK;
+}
+
+static m2m_status load_common(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                              const double *w, bool device)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (n < 0 || (n > 0 && (!pos || !vel || !w))) return fail(ctx, M2M_ERR_ARG, "n >= 0 and non-null arrays required");
+    if (n > 0x7fffffffll * 64) return fail(ctx, M2M_ERR_ARG, "too many particles");
+    ctx->loaded = false;
+    m2m_status s = ensure_capacity(ctx, n);
+    if (s != M2M_OK) return s;
+    ctx->n = n;
+    // stage FP64 inputs on the device
+    double *stage = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    CU(cudaMalloc(&stage, bytes * 7));
+    const double *src[7];
+    double W0 = 0.0;
+    if (device) {
+        for (int k = 0; k < 3; ++k) src[k] = pos + k * n;
+        for (int k = 0; k < 3; ++k) src[3 + k] = vel + k * n;
+        src[6] = w;
+        for (int k = 0; k < 7; ++k)
+            if (n > 0) CU(cudaMemcpyAsync(stage + k * n, src[k], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        std::vector<double> hw(n);
+        if (n > 0) CU(cudaMemcpyAsync(hw.data(), w, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (long long i = 0; i < n; ++i) W0 += hw[i];
+    } else {
+        if (n > 0) {
+            CU(cudaMemcpyAsync(stage, pos, bytes * 3, cudaMemcpyHostToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(stage + 3 * n, vel, bytes * 3, cudaMemcpyHostToDevice, ctx->stream));
+            CU(cudaMemcpyAsync(stage + 6 * n, w, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        }
+        for (long long i = 0; i < n; ++i) W0 += w[i];
+    }
+    if (n > 0) {
+        if (ctx->precision == M2M_PREC_FP64) {
+            for (int k = 0; k < 7; ++k)
+                CU(cudaMemcpyAsync(ctx->st[k], stage + k * n, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            for (int k = 0; k < 7; ++k)
+                k_convert_in<float><<<ctx->nsm * 4, 256, 0, ctx->stream>>>(stage + k * n, (float *)ctx->st[k], n);
+        }
+    }
+    s = finish_load(ctx, stage, stage + n, stage + 2 * n, stage + 3 * n, stage + 4 * n, stage + 5 * n,
+                    stage + 6 * n, W0);
+    cudaFree(stage);
+    return s;
+}
+
+extern "C" m2m_status m2m_load_particles(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                                         const double *w)
+{
+    return load_common(ctx, n, pos, vel, w, false);
+}
+
+extern "C" m2m_status m2m_load_particles_device(m2m_ctx *ctx, int64_t n, const double *pos_dev,
+                                                const double *vel_dev, const double *w_dev)
+{
+    return load_common(ctx, n, pos_dev, vel_dev, w_dev, true);
+}
+
+// ------------------------------------------------------------------ stepping
+
+static const int kGraphSteps = 16;
+
+static m2m_status build_graph(m2m_ctx *ctx)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < kGraphSteps; ++k) launch_one(ctx, 1, 0);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return fail(ctx, M2M_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->graph = nullptr;
+        return fail(ctx, M2M_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    ctx->graph_steps = kGraphSteps;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    if (nsteps < 0) return fail(ctx, M2M_ERR_ARG, "nsteps must be >= 0");
+    if (ctx->timing) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            while (ctx->events.size() < 3 * (ctx->timed + 1)) {
+                cudaEvent_t e;
+                CU(cudaEventCreate(&e));
+                ctx->events.push_back(e);
+            }
+            cudaEvent_t *ev = &ctx->events[3 * ctx->timed];
+            if (ctx->precision == M2M_PREC_FP64) launch_step_timed<double, 2>(ctx, ev);
+            else launch_step_timed<float, 1>(ctx, ev);
+            ++ctx->timed;
+        }
+        CU(cudaGetLastError());
+        return M2M_OK;
+    }
+    int64_t left = nsteps;
+    if (left >= kGraphSteps && !ctx->graph) {
+        m2m_status s = build_graph(ctx);
+        if (s != M2M_OK) return s;
+    }
+    while (left >= kGraphSteps) {
+        CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left) launch_one(ctx, 1, 0);
+    CU(cudaGetLastError());
+    return M2M_OK;
+}
+
+static m2m_status check_device_errors(m2m_ctx *ctx)
+{
+    Scalars sc;
+    CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (sc.err & kErrNegWeight) return fail(ctx, M2M_ERR_NEG_WEIGHT, "the force of change made a weight negative");
+    if (sc.err & kErrOverflow) return fail(ctx, M2M_ERR_OVERFLOW, "a deposit left the fixed-point range");
+    if (sc.err & kErrNonFinite) return fail(ctx, M2M_ERR_NONFINITE, "a weight became non-finite");
+    if (sc.err) return fail(ctx, M2M_ERR_CUDA, "device error word %u", sc.err);
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_synchronize(m2m_ctx *ctx)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->loaded) return M2M_OK;
+    return check_device_errors(ctx);
+}
+
+// ------------------------------------------------------------------ getters
+
+template <class T, int WPS>
+static void launch_materialize(m2m_ctx *c)
+{
+    const int g = grid_for(c);
+    cudaMemsetAsync(c->d_acc, 0, 2 * sizeof(long long), c->stream);
+    k_materialize<T, WPS><<<g, c->block, c->smem_mat, c->stream>>>(c->m, state<T>(c), buffers(c), c->d_wout, c->d_acc);
+    k_scale<<<g, c->block, 0, c->stream>>>(c->d_wout, c->n, c->d_acc, c->m, c->d_sc);
+}
+
+extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    if (n != ctx->n || (n > 0 && !w)) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count (%lld)", ctx->n);
+    if (n == 0) return m2m_synchronize(ctx);
+    if (ctx->wout_cap < n) {
+        free_dev(ctx->d_wout);
+        CU(cudaMalloc(&ctx->d_wout, sizeof(double) * n));
+        ctx->wout_cap = n;
+    }
+    if (ctx->precision == M2M_PREC_FP64) launch_materialize<double, 2>(ctx);
+    else launch_materialize<float, 1>(ctx);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(w, ctx->d_wout, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    return m2m_synchronize(ctx);
+}
+
+extern "C" m2m_status m2m_get_state(m2m_ctx *ctx, double *pos, double *vel, int64_t n)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    if (n != ctx->n) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count");
+    if (n == 0) return m2m_synchronize(ctx);
+    double *tmp = nullptr;
+    CU(cudaMalloc(&tmp, sizeof(double) * n));
+    for (int k = 0; k < 6; ++k) {
+        double *dst = k < 3 ? (pos ? pos + k * n : nullptr) : (vel ? vel + (k - 3) * n : nullptr);
+        if (!dst) continue;
+        if (ctx->precision == M2M_PREC_FP64) {
+            CU(cudaMemcpyAsync(dst, ctx->st[k], sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        } else {
+            k_convert_out<float><<<ctx->nsm * 4, 256, 0, ctx->stream>>>((const float *)ctx->st[k], tmp, n);
+            CU(cudaMemcpyAsync(dst, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+            CU(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(tmp);
+    return m2m_synchronize(ctx);
+}
+
+extern "C" m2m_status m2m_get_observables(m2m_ctx *ctx, double *ytil, double *y, int32_t J)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    if (J != ctx->m.J) return fail(ctx, M2M_ERR_ARG, "J must be %d", ctx->m.J);
+    if (ytil) CU(cudaMemcpyAsync(ytil, ctx->d_ytil, sizeof(double) * J, cudaMemcpyDeviceToHost, ctx->stream));
+    if (y) CU(cudaMemcpyAsync(y, ctx->d_yraw, sizeof(double) * J, cudaMemcpyDeviceToHost, ctx->stream));
+    return m2m_synchronize(ctx);
+}
+
+extern "C" m2m_status m2m_get_chi2(m2m_ctx *ctx, double *chi2, int32_t *J, double *delta)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    Scalars sc;
+    CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
+    if (delta) CU(cudaMemcpyAsync(delta, ctx->d_delta, sizeof(double) * ctx->m.J, cudaMemcpyDeviceToHost, ctx->stream));
+    m2m_status s = m2m_synchronize(ctx);
+    if (chi2) *chi2 = sc.chi2;
+    if (J) *J = ctx->m.J;
+    return s;
+}
+
+extern "C" m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *counts, int32_t *cells, int64_t n)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    const int nc = ctx->m.ncell;
+    if (grid_mean && nc) CU(cudaMemcpyAsync(grid_mean, ctx->d_prior, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    if (counts && nc) CU(cudaMemcpyAsync(counts, ctx->d_prior_count, sizeof(int64_t) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cells) {
+        if (n != ctx->n) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count");
+        std::vector<uint16_t> c16(n);
+        if (n > 0) CU(cudaMemcpyAsync(c16.data(), ctx->cell, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        for (long long i = 0; i < n; ++i) cells[i] = c16[i];
+    }
+    return m2m_synchronize(ctx);
+}
+
+extern "C" m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t)
+{
+    if (!ctx || !t) return M2M_ERR_ARG;
+    Scalars sc;
+    CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *t = sc.t;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_get_particle_count(m2m_ctx *ctx, int64_t *n)
+{
+    if (!ctx || !n) return M2M_ERR_ARG;
+    *n = ctx->n;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_set_timing(m2m_ctx *ctx, int32_t on)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->timing = on != 0;
+    ctx->timed = 0;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_ms, double *fin_ms, int64_t *steps)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    double a = 0.0, b = 0.0;
+    for (size_t k = 0; k < ctx->timed; ++k) {
+        float t1 = 0.f, t2 = 0.f;
+        CU(cudaEventElapsedTime(&t1, ctx->events[3 * k], ctx->events[3 * k + 1]));
+        CU(cudaEventElapsedTime(&t2, ctx->events[3 * k + 1], ctx->events[3 * k + 2]));
+        a += t1;
+        b += t2;
+    }
+    if (step_ms) *step_ms = a;
+    if (fin_ms) *fin_ms = b;
+    if (steps) *steps = (int64_t)ctx->timed;
+    return M2M_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t precision;
+    uint64_t config_hash;
+    int64_t n;
+    int32_t J, ncell;
+    double fx_w, fx_v2, fx_gh, v2max;
+};
+
+extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return M2M_ERR_ARG;
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    m2m_status s = m2m_synchronize(ctx);
+    if (s != M2M_OK) return s;
+    const Model &m = ctx->m;
+    CkptHeader hd{};
+    std::memcpy(hd.magic, "M2MSTATE", 8);
+    hd.version = 1;
+    hd.precision = ctx->precision;
+    hd.config_hash = ctx->config_hash;
+    hd.n = ctx->n;
+    hd.J = m.J;
+    hd.ncell = m.ncell;
+    hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
+    const size_t es = elem_size(ctx), n = size_t(ctx->n);
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.ncell) + 8 * m.ncell + sizeof(Scalars));
+    char *p = buf.data();
+    for (int k = 0; k < 7; ++k) {
+        if (n) CU(cudaMemcpy(p, ctx->st[k], es * n, cudaMemcpyDeviceToHost));
+        p += es * n;
+    }
+    if (n) CU(cudaMemcpy(p, ctx->cell, 2 * n, cudaMemcpyDeviceToHost));
+    p += 2 * n;
+    double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
+    for (auto d : dv) {
+        CU(cudaMemcpy(p, d, sizeof(double) * m.J, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * m.J;
+    }
+    if (m.ncell) {
+        CU(cudaMemcpy(p, ctx->d_prior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(p, ctx->d_prior_count, 8 * m.ncell, cudaMemcpyDeviceToHost));
+        p += 8 * m.ncell;
+    }
+    CU(cudaMemcpy(p, ctx->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(ctx, M2M_ERR_ARG, "short write to %s", path);
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
+{
+    if (!ctx || !path) return M2M_ERR_ARG;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
+    CkptHeader hd{};
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 1) {
+        std::fclose(f);
+        return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
+    }
+    Model &m = ctx->m;
+    if (hd.config_hash != ctx->config_hash || hd.precision != ctx->precision || hd.J != m.J || hd.ncell != m.ncell) {
+        std::fclose(f);
+        return fail(ctx, M2M_ERR_ARG, "%s was written for different descriptors", path);
+    }
+    const size_t es = elem_size(ctx), n = size_t(hd.n);
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.ncell) + 8 * m.ncell + sizeof(Scalars));
+    const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+    std::fclose(f);
+    if (!ok) return fail(ctx, M2M_ERR_ARG, "%s is truncated", path);
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->loaded = false;
+    m2m_status s = ensure_capacity(ctx, hd.n);
+    if (s != M2M_OK) return s;
+    ctx->n = hd.n;
+    m.fx_w = hd.fx_w; m.fx_v2 = hd.fx_v2; m.fx_gh = hd.fx_gh; m.v2max = hd.v2max;
+    ctx->obs_iscale.resize(m.J);
+    for (int j = 0; j < m.J; ++j) {
+        const int k = ctx->obs_kind[j];
+        ctx->obs_iscale[j] = 1.0 / (k == kKindMass ? m.fx_w : ((k == kKindV2 || k == kKindV1) ? m.fx_v2 : m.fx_gh));
+    }
+    CU(cudaMemcpy(ctx->d_iscale, ctx->obs_iscale.data(), sizeof(double) * m.J, cudaMemcpyHostToDevice));
+    const char *p = buf.data();
+    for (int k = 0; k < 7; ++k) {
+        if (n) CU(cudaMemcpy(ctx->st[k], p, es * n, cudaMemcpyHostToDevice));
+        p += es * n;
+    }
+    if (n) CU(cudaMemcpy(ctx->cell, p, 2 * n, cudaMemcpyHostToDevice));
+    p += 2 * n;
+    double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
+    for (auto d : dv) {
+        CU(cudaMemcpy(d, p, sizeof(double) * m.J, cudaMemcpyHostToDevice));
+        p += sizeof(double) * m.J;
+    }
+    if (m.ncell) {
+        CU(cudaMemcpy(ctx->d_prior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
+        p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(ctx->d_prior_count, p, 8 * m.ncell, cudaMemcpyHostToDevice));
+        p += 8 * m.ncell;
+    }
+    CU(cudaMemcpy(ctx->d_sc, p, sizeof(Scalars), cudaMemcpyHostToDevice));
+    CU(cudaMemset(ctx->d_hist, 0, sizeof(long long) * m.hist_words));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    ctx->loaded = true;
+    return M2M_OK;
+}
+
+// ------------------------------------------------------------------ targets
+
+static m2m_status observe_now(m2m_ctx *c, std::vector<double> &y)
+{
+    m2m_ctx *ctx = c;
+    CU(cudaMemcpyAsync(c->d_Vp, c->Vp.data(), sizeof(double) * c->Vp.size(), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_isp, c->isp.data(), sizeof(double) * c->isp.size(), cudaMemcpyHostToDevice, c->stream));
+    Scalars sc0{};
+    sc0.Wrange = 9.2233720368547758e18 / c->m.fx_w;
+    CU(cudaMemcpyAsync(c->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    launch_one(c, 0, 1);
+    CU(cudaGetLastError());
+    y.resize(c->m.J);
+    CU(cudaMemcpyAsync(y.data(), c->d_yraw, sizeof(double) * c->m.J, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return check_device_errors(c);
+}
+
+extern "C" m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double *pos,
+                                        const double *vel, const double *w, const double *err,
+                                        const double *noise, double *Y, double *sigY, double *Vp,
+                                        double *sp, int32_t *iterations)
+{
+    m2m_ctx *ctx = nullptr;
+    if (!obs || !err || !Y || !sigY || !Vp || !sp || n < 0 || (n > 0 && (!pos || !vel || !w)))
+        return fail(nullptr, M2M_ERR_ARG, "m2m_build_targets: null argument");
+    if (obs->n_groups < 1 || obs->n_groups > kMaxGroups) return fail(nullptr, M2M_ERR_ARG, "n_groups must be 1..%d", kMaxGroups);
+    m2m_potential pot{};
+    pot.kind = M2M_POT_HERNQUIST;
+    pot.G = 1; pot.M = 1; pot.a = 1;
+    m2m_prior_grid pg{};
+    pg.mode = M2M_REG_GWR;
+    pg.update_every = 1;
+    m2m_options opt{};
+    opt.precision = M2M_PREC_FP64;
+    // pass 1: luminosity, first and second moments per aperture
+    m2m_observables o1 = *obs;
+    o1.Y = o1.sigY = nullptr;
+    int nap_total = 0;
+    for (int g = 0; g < o1.n_groups; ++g) {
+        o1.groups[g].n_kinds = 3;
+        o1.groups[g].kinds[0] = kKindMass;
+        o1.groups[g].kinds[1] = kKindV1;
+        o1.groups[g].kinds[2] = kKindV2;
+        o1.groups[g].Vp = o1.groups[g].sp = nullptr;
+        nap_total += obs->groups[g].n_ap;
+    }
+    m2m_status s = create_impl(&pot, &o1, &pg, 0, 0, 0, &opt, 1, &ctx);
+    if (s != M2M_OK) return s;
+    s = m2m_load_particles(ctx, n, pos, vel, w);
+    std::vector<double> y;
+    if (s == M2M_OK) s = observe_now(ctx, y);
+    if (s != M2M_OK) {
+        g_create_error = ctx->err;
+        m2m_destroy(ctx);
+        return s;
+    }
+    std::vector<double> lum(nap_total), V(nap_total), S(nap_total);
+    std::vector<char> has_gh(o1.n_groups, 0);
+    int ap = 0;
+    for (int g = 0; g < o1.n_groups; ++g) {
+        const GroupDesc &G = ctx->m.g[g];
+        for (int k = 0; k < obs->groups[g].n_kinds; ++k) has_gh[g] |= is_gh(obs->groups[g].kinds[k]);
+        for (int p = 0; p < G.n_ap; ++p, ++ap) {
+            const int jm = G.obs_off + p;
+            const double l = y[jm] * ctx->area_of_obs[jm];
+            lum[ap] = l;
+            if (l > 0) {
+                V[ap] = y[G.obs_off + G.n_ap + p] / l;
+                const double var = y[G.obs_off + 2 * G.n_ap + p] / l - V[ap] * V[ap];
+                S[ap] = var > 0 ? std::sqrt(var) : 0.0;
+            } else {
+                V[ap] = 0.0;
+                S[ap] = 1.0;
+            }
+            if (has_gh[g] && !(l > 0 && S[ap] > 0)) {
+                m2m_destroy(ctx);
+                return fail(nullptr, M2M_ERR_TARGET, "group %d aperture %d is empty or has zero dispersion", g, p);
+            }
+        }
+    }
+    m2m_destroy(ctx);
+    ctx = nullptr;
+    // pass 2: correct V_p, sigma_p until h1 = h2 = 0 (eq. h1h2)
+    m2m_observables o2 = *obs;
+    o2.Y = o2.sigY = nullptr;
+    std::vector<std::vector<double>> vbuf(o2.n_groups), sbuf(o2.n_groups);
+    ap = 0;
+    for (int g = 0; g < o2.n_groups; ++g) {
+        const int na = obs->groups[g].n_ap;
+        vbuf[g].assign(V.begin() + ap, V.begin() + ap + na);
+        sbuf[g].assign(S.begin() + ap, S.begin() + ap + na);
+        for (int p = 0; p < na; ++p)
+            if (!(sbuf[g][p] > 0)) sbuf[g][p] = 1.0;
+        o2.groups[g].n_kinds = 2;
+        o2.groups[g].kinds[0] = kKindGH0 + 1;
+        o2.groups[g].kinds[1] = kKindGH0 + 2;
+        o2.groups[g].Vp = vbuf[g].data();
+        o2.groups[g].sp = sbuf[g].data();
+        ap += na;
+    }
+    s = create_impl(&pot, &o2, &pg, 0, 0, 0, &opt, 1, &ctx);
+    if (s != M2M_OK) return s;
+    s = m2m_load_particles(ctx, n, pos, vel, w);
+    int it = 0, maxit = 0;
+    std::vector<char> active(o2.n_groups);
+    for (int g = 0; g < o2.n_groups; ++g) active[g] = has_gh[g];
+    for (it = 0; s == M2M_OK && it < 200; ++it) {
+        bool any = false;
+        for (int g = 0; g < o2.n_groups; ++g) any |= active[g] != 0;
+        if (!any) break;
+        s = observe_now(ctx, y);
+        if (s != M2M_OK) break;
+        ap = 0;
+        for (int g = 0; g < o2.n_groups; ++g) {
+            const GroupDesc &G = ctx->m.g[g];
+            double worst = 0.0;
+            for (int p = 0; p < G.n_ap; ++p) {
+                const int a = ap + p;
+                if (!active[g]) continue;
+                const double h1 = y[G.obs_off + p] / lum[a];
+                const double h2 = y[G.obs_off + G.n_ap + p] / lum[a];
+                worst = std::fmax(worst, std::fmax(std::fabs(h1), std::fabs(h2)));
+                const double s_old = 1.0 / ctx->isp[a];
+                ctx->Vp[a] += std::sqrt(2.0) * s_old * h1;
+                ctx->isp[a] = 1.0 / (s_old + std::sqrt(2.0) * s_old * h2);
+            }
+            if (active[g]) {
+                if (worst <= 1e-12) active[g] = 0;
+                maxit = it;
+            }
+            ap += G.n_ap;
+        }
+    }
+    std::vector<double> Vfin(ctx->Vp), Sfin(ctx->isp.size());
+    for (size_t a = 0; a < Sfin.size(); ++a) Sfin[a] = 1.0 / ctx->isp[a];
+    if (s != M2M_OK) g_create_error = ctx->err;
+    m2m_destroy(ctx);
+    ctx = nullptr;
+    if (s != M2M_OK) return s;
+    // pass 3: the requested observables with the fitted Gaussian parameters
+    m2m_observables o3 = *obs;
+    o3.Y = o3.sigY = nullptr;
+    ap = 0;
+    for (int g = 0; g < o3.n_groups; ++g) {
+        const int na = obs->groups[g].n_ap;
+        vbuf[g].assign(Vfin.begin() + ap, Vfin.begin() + ap + na);
+        sbuf[g].assign(Sfin.begin() + ap, Sfin.begin() + ap + na);
+        o3.groups[g].Vp = vbuf[g].data();
+        o3.groups[g].sp = sbuf[g].data();
+        ap += na;
+    }
+    s = create_impl(&pot, &o3, &pg, 0, 0, 0, &opt, 1, &ctx);
+    if (s != M2M_OK) return s;
+    s = m2m_load_particles(ctx, n, pos, vel, w);
+    if (s == M2M_OK) s = observe_now(ctx, y);
+    if (s != M2M_OK) {
+        g_create_error = ctx->err;
+        m2m_destroy(ctx);
+        return s;
+    }
+    ap = 0;
+    for (int g = 0; g < o3.n_groups; ++g) {
+        const GroupDesc &G = ctx->m.g[g];
+        for (int k = 0; k < G.n_kinds; ++k) {
+            for (int p = 0; p < G.n_ap; ++p) {
+                const int j = G.obs_off + k * G.n_ap + p;
+                const int kind = G.kinds[k];
+                const double gn = noise ? noise[j] : 0.0;
+                const double l = lum[ap + p];
+                if (kind == kKindMass) {
+                    sigY[j] = err[j] * y[j];
+                    Y[j] = y[j] * (1.0 + err[j] * gn);
+                } else if (kind == kKindV2) {
+                    const double vrms = std::sqrt(y[j] / l);
+                    const double vo = vrms * (1.0 + err[j] * gn);
+                    sigY[j] = 2.0 * err[j] * y[j];
+                    Y[j] = l * vo * vo;
+                } else {
+                    sigY[j] = l * err[j];
+                    Y[j] = l * (y[j] / l + err[j] * gn);
+                }
+            }
+        }
+        ap += G.n_ap;
+    }
+    for (int a = 0; a < nap_total; ++a) {
+        Vp[a] = Vfin[a];
+        sp[a] = Sfin[a];
+    }
+    if (iterations) *iterations = maxit;
+    m2m_destroy(ctx);
+    return M2M_OK;
+}
+
+// ------------------------------------------------------------------ misc
+
+extern "C" const char *m2m_last_error(const m2m_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" void m2m_destroy(m2m_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    free_state(ctx);
+    free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE);
+    free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
+    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_prior); free_dev(ctx->d_ytil);
+    free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
+    free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}

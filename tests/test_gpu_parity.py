@@ -1,0 +1,286 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 mode within 1e-10 of the oracle on observables (measured as
+|y_gpu - y_ora| / max(|y_ora|, sigma_j)), weights, chi^2 and positions after
+100 steps; mixed mode within 1e-4 on observables and 1 % on chi^2/J after the
+full run (the tolerances the method's precision plan states). Integer results
+(prior cells and counts) must match exactly.
+"""
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1202_2355_gb300 import binding as B
+from paper_1202_2355_gb300 import synth
+from paper_1202_2355_gb300 import workloads as W
+from paper_1202_2355_gb300.workloads import Group
+
+from _common import Pair, obs_err, weight_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1202_2355_gb300 import build
+    build.build()
+    O.build()
+
+
+@pytest.fixture(scope="module")
+def c1_targets():
+    wl = W.make("c1")
+    return O.from_workload(wl)
+
+
+def _assert_fp64(e, tol=FP64_TOL):
+    assert e["ytil"] < tol and e["yraw"] < tol, e
+    assert e["w"] < tol, e
+    assert e["chi2"] < tol, e
+    assert e["pos"] < 1e-12 and e["vel"] < 1e-12, e
+
+
+def test_c1_fp64_100_steps(c1_targets):
+    """Hernquist, N = 20,000, J = 60, 30 x 10 grid every 25 steps: 100 steps (4 prior updates)."""
+    wl = W.make("c1")
+    pr = Pair(wl, targets=c1_targets)
+    e0 = pr.errors()
+    _assert_fp64(e0)
+    for _ in range(4):
+        pr.step(25)
+        _assert_fp64(pr.errors())
+    g, cnt, cells = pr.fit.priors()
+    assert np.array_equal(cnt, pr.ora.grid_count)
+    assert np.array_equal(cells, pr.ora.cell)
+    # 2-word fixed-point cell sums resolve 2^-90 W0; below that a mean reads as 0
+    assert np.allclose(g, pr.ora.grid_mean, rtol=FP64_TOL, atol=1e-26 * pr.ora.W0)
+    assert pr.fit.step_count() == 100
+    pr.close()
+
+
+def test_ragged_sizes_and_frequent_priors(c1_targets):
+    """N not a multiple of the block, several tiles, priors every 7 steps."""
+    wl = W.make("c1", n=1013)
+    pr = Pair(wl, prior=dict(wl.prior, update_every=7), targets=c1_targets)
+    pr.step(43)
+    _assert_fp64(pr.errors())
+    pr.close()
+
+
+@pytest.mark.parametrize("mode,rule,renorm,relax", [("gwr", "exp", 1, 0), ("gwr", "euler", 0, 5),
+                                                    ("mpr", "euler", 1, 3), ("mpr", "exp", 0, 0)])
+def test_regularisation_and_update_variants(c1_targets, mode, rule, renorm, relax):
+    wl = W.make("c1", n=3001)
+    # explicit Euler stays positive only for eps dt |F| < 1: eps = 2e-5 with N = 3001
+    par = dict(wl.params, update_rule=rule, renormalize=renorm, n_relax=relax,
+               eps=2e-5 if rule == "euler" else wl.params["eps"], mu=0.5)
+    pr = Pair(wl, prior=dict(wl.prior, mode=mode, update_every=10), params=par, targets=c1_targets)
+    pr.step(30)
+    _assert_fp64(pr.errors())
+    pr.close()
+
+
+def test_hernquist_nfw_fp64(_built):
+    """Composite potential: the circular-orbit table path and the NFW force."""
+    wl = W.make("c3", n=5000, n_target=50_000)
+    pr = Pair(wl, precision="fp64", prior=dict(wl.prior, update_every=10))
+    pr.step(50)
+    _assert_fp64(pr.errors())
+    _, cnt, cells = pr.fit.priors()
+    assert np.array_equal(cells, pr.ora.cell) and np.array_equal(cnt, pr.ora.grid_count)
+    pr.close()
+
+
+def test_flattened_log_pixel_maps_fp64(_built):
+    """Inclined pixel maps of mass and h1..h4, signed-Lz grid with exp(E) spacing."""
+    wl = W.make("c4", n=20_000, n_target=200_000)
+    wl.groups = [Group("pixels", ["mass", "gh1", "gh2", "gh3", "gh4"], [0.02] * 5, nx=16, ny=16,
+                       box=(-4.0, 4.0, -4.0, 4.0))]
+    # 2 % errors on 16 x 16 maps of N = 20,000 make eps dt F ~ 10^3 at eps = 1e-3 (weights
+    # overflow in any precision); eps = 1e-6 keeps the fit finite
+    pr = Pair(wl, precision="fp64", prior=dict(wl.prior, update_every=10), params=dict(wl.params, eps=1e-6))
+    pr.step(40)
+    _assert_fp64(pr.errors())
+    _, cnt, cells = pr.fit.priors()
+    assert np.array_equal(cells, pr.ora.cell) and np.array_equal(cnt, pr.ora.grid_count)
+    pr.close()
+
+
+def test_target_construction_matches_oracle():
+    wl = W.make("c3", n=1000, n_target=200_000)
+    obs = O.ObsSet(wl.groups, wl.incl_deg)
+    Yo, so, ito = O.build_targets(obs, O.ParticleSet(wl.target), wl.err_per_obs(), wl.noise)
+    Yg, sg, Vp, sp, itg = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
+    assert np.max(np.abs(Vp - obs.Vp) / obs.sp) < 1e-10
+    assert np.max(np.abs(sp - obs.sp) / obs.sp) < 1e-10
+    assert np.max(obs_err(Yg, Yo, so)) < 1e-10
+    assert np.allclose(sg, so, rtol=1e-10)
+
+
+def test_bitwise_deterministic(c1_targets):
+    wl = W.make("c1", n=5000)
+    obs, Y, sig = c1_targets
+    out = []
+    for _ in range(2):
+        f = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+        f.load(wl.model)
+        f.step(40)
+        out.append((f.weights(), f.observables()[0], f.chi2()))
+        f.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_resume_is_bit_identical(c1_targets, precision):
+    wl = W.make("c1", n=4000)
+    obs, Y, sig = c1_targets
+    a = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, precision=precision)
+    a.load(wl.model)
+    a.step(60)
+    ref = (a.weights(), a.observables()[0], a.chi2())
+    b = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, precision=precision)
+    b.load(wl.model)
+    b.step(37)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "fit.m2m")
+        b.save(path)
+        b.close()
+        c = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, precision=precision)
+        c.restore(path)
+        assert c.step_count() == 37
+        c.step(23)
+        got = (c.weights(), c.observables()[0], c.chi2())
+        c.close()
+    assert np.array_equal(ref[0], got[0]) and np.array_equal(ref[1], got[1]) and ref[2] == got[2]
+    a.close()
+
+
+def test_checkpoint_rejects_other_descriptors(c1_targets):
+    wl = W.make("c1", n=500)
+    obs, Y, sig = c1_targets
+    a = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+    a.load(wl.model)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "fit.m2m")
+        a.save(path)
+        b = B.fit_from_workload(wl, Y, sig * 1.5, obs.Vp, obs.sp)
+        with pytest.raises(B.M2MError) as ei:
+            b.restore(path)
+        assert ei.value.status == 1
+        b.close()
+    a.close()
+
+
+def test_empty_single_and_outside_particles(c1_targets):
+    wl = W.make("c1", n=10)
+    obs, Y, sig = c1_targets
+    # empty: observables zero, chi^2 = sum (Y/sigma)^2
+    f = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+    f.load({k: np.zeros(0) for k in ("x", "y", "z", "vx", "vy", "vz", "w")})
+    f.step(3)
+    yt, yr = f.observables()
+    assert np.all(yt == 0) and np.all(yr == 0)
+    assert f.chi2() == pytest.approx(np.sum((Y / sig) ** 2), rel=1e-14)
+    assert f.weights().size == 0
+    f.close()
+    # one particle inside, one far outside every aperture, one with zero weight
+    p = {k: np.array(v, np.float64) for k, v in dict(
+        x=[0.3, 80.0, 0.5], y=[0.1, 0.0, -0.2], z=[0.0, 3.0, 0.1], vx=[0.0, 0.0, 0.1],
+        vy=[0.4, 0.05, 0.0], vz=[0.1, 0.0, 0.2], w=[0.5, 0.3, 0.0]).items()}
+    pr = Pair(wl, particles=p, targets=c1_targets)
+    pr.step(12)
+    _assert_fp64(pr.errors())
+    assert pr.fit.weights()[2] == 0.0
+    pr.close()
+
+
+def test_device_load_matches_host_load(c1_targets):
+    torch = pytest.importorskip("torch")
+    wl = W.make("c1", n=2000)
+    obs, Y, sig = c1_targets
+    a = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+    a.load(wl.model)
+    a.step(20)
+    b = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+    m = wl.model
+    pos = torch.tensor(np.concatenate([m["x"], m["y"], m["z"]]), device="cuda")
+    vel = torch.tensor(np.concatenate([m["vx"], m["vy"], m["vz"]]), device="cuda")
+    w = torch.tensor(m["w"], device="cuda")
+    torch.cuda.synchronize()
+    b.load_device(wl.n, pos.data_ptr(), vel.data_ptr(), w.data_ptr())
+    b.step(20)
+    assert np.array_equal(a.weights(), b.weights())
+    assert np.array_equal(a.observables()[0], b.observables()[0])
+    a.close()
+    b.close()
+
+
+def test_errors_are_reported_not_trapped(c1_targets):
+    wl = W.make("c1", n=2000)
+    obs, Y, sig = c1_targets
+    # explicit Euler with the configured eps drives weights negative at the first update
+    f = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, params=dict(wl.params, update_rule="euler"))
+    f.load(wl.model)
+    f.step(3)
+    with pytest.raises(B.M2MError) as ei:
+        f.synchronize()
+    assert ei.value.status == 5
+    f.close()
+    # invalid arguments
+    with pytest.raises(B.M2MError) as ei:
+        B.fit_from_workload(wl, Y, -sig, obs.Vp, obs.sp)
+    assert ei.value.status == 1
+    with pytest.raises(B.M2MError) as ei:
+        B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, prior=dict(wl.prior, Emax=-2.0))
+    assert ei.value.status == 1
+    f = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp)
+    bad = dict(wl.model)
+    bad["w"] = bad["w"].copy()
+    bad["w"][5] = np.nan
+    with pytest.raises(B.M2MError) as ei:
+        f.load(bad)
+    assert ei.value.status == 1
+    with pytest.raises(B.M2MError) as ei:
+        f.step(1)
+    assert ei.value.status == 8
+    f.close()
+
+
+def test_c2_full_size_fp64():
+    """N = 1,000,000, J = 150, 50 x 20 grid, in the launch configuration of the benchmark:
+    10 steps against the oracle on every observable and a sample of weights."""
+    wl = W.make("c2")
+    pr = Pair(wl)
+    pr.step(10)
+    yt, yr = pr.fit.observables()
+    assert np.max(obs_err(yt, pr.ora.ytil, pr.sig)) < FP64_TOL
+    assert np.max(obs_err(yr, pr.ora.yraw, pr.sig)) < FP64_TOL
+    w = pr.fit.weights()
+    idx = np.arange(0, wl.n, 997)
+    assert np.max(weight_err(w[idx], pr.ora.w[idx], pr.ora.W0, wl.n)) < FP64_TOL
+    assert abs(pr.fit.chi2() - pr.ora.chi2) < FP64_TOL * pr.ora.chi2
+    _, cnt, _ = pr.fit.priors()
+    assert np.array_equal(cnt, pr.ora.grid_count)
+    pr.close()
+
+
+def test_c1_mixed_full_run(c1_targets):
+    """Mixed precision against the FP64 oracle after the full 2,000-step C1 run."""
+    wl = W.make("c1")
+    pr = Pair(wl, precision="mixed", targets=c1_targets)
+    pr.step(wl.steps)
+    e = pr.errors()
+    J = len(pr.Y)
+    c2g = pr.fit.chi2() / J
+    c2o = pr.ora.chi2 / J
+    print(f"mixed C1 after {wl.steps} steps: obs err {e['ytil']:.3e}, chi2/J gpu {c2g:.5f} oracle {c2o:.5f}")
+    assert abs(c2g - c2o) <= 0.01 * c2o
+    assert e["ytil"] < 1e-4, e
+    pr.close()
