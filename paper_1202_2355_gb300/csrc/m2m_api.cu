@@ -2,13 +2,14 @@
 //
 // A context owns the particle state (structure of arrays in HBM), the
 // observable and prior tables, the fixed-point accumulators and a small block
-// of per-step scalars in device memory. A step is two kernels: k_step (one
-// pass over the particles) and k_finalize (one block over the observables and
-// prior cells). Every per-step decision is read from device memory, so a
-// chunk of steps is captured once in a CUDA graph and replayed.
+// of per-step scalars in device memory. A step is one kernel, k_step: one pass
+// over the particles, whose last block to finish runs the finalize over the
+// observables and prior cells. Every per-step decision is read from device
+// memory, so a chunk of steps is captured once in a CUDA graph and replayed.
 #include "m2m.h"
 #include "m2m_device.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -32,6 +33,7 @@ struct m2m_ctx {
     // host copies of the descriptors
     std::vector<double> edges, Vp, isp, Y, sig, obs_post, obs_iscale, area_of_obs, lcE;
     std::vector<int> obs_kind;
+    std::vector<unsigned short> lut;
     uint64_t config_hash = 0;
 
     // device buffers
@@ -40,9 +42,11 @@ struct m2m_ctx {
     void *st[7] = {nullptr};
     uint16_t *cell = nullptr;
     double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
+    unsigned short *d_lut = nullptr;
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
     int *d_kind = nullptr;
     double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
+    double *d_rec = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
     Scalars *d_sc = nullptr;
     double *d_wout = nullptr;
@@ -52,6 +56,7 @@ struct m2m_ctx {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     std::string err;
+    void *kstep = nullptr;  // the step kernel picked for the observable shape
 
     // kernel timing (m2m_set_timing)
     bool timing = false;
@@ -142,7 +147,7 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         return fail(ctx, M2M_ERR_ARG, "n_groups must be 1..%d", kMaxGroups);
     m.n_groups = obs->n_groups;
     int J = 0, nap = 0, ned = 0;
-    ctx->edges.clear(); ctx->Vp.clear(); ctx->isp.clear();
+    ctx->edges.clear(); ctx->Vp.clear(); ctx->isp.clear(); ctx->lut.clear();
     ctx->obs_kind.clear(); ctx->obs_post.clear(); ctx->area_of_obs.clear();
     for (int g = 0; g < m.n_groups; ++g) {
         const m2m_obs_group &S = obs->groups[g];
@@ -156,6 +161,9 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         G.ap_off = nap;
         G.edge_off = ned;
         G.max_gh = -1;
+        G.has_v2 = 0;
+        G.k_mass = G.k_v2 = G.k_v1 = -1;
+        for (int n = 0; n < 7; ++n) G.k_gh[n] = -1;
         std::vector<double> area(S.n_ap);
         if (S.geometry == M2M_GEOM_ANNULI) {
             if (!S.edges) return fail(ctx, M2M_ERR_ARG, "group %d: annuli need edges", g);
@@ -167,11 +175,41 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
             for (int p = 0; p < S.n_ap; ++p)
                 area[p] = 3.14159265358979323846 * (S.edges[p + 1] * S.edges[p + 1] - S.edges[p] * S.edges[p]);
             ned += S.n_ap + 1;
+            // FP32 lookup: buckets uniform in log2(R^2) over the group. With edges uniform
+            // in log R (to 1e-9) bucket b is annulus b; otherwise each bucket holds a
+            // candidate annulus from a table. The device corrects by exact comparisons.
+            const double e0 = std::fmax(S.edges[0], 1e-30), e1 = S.edges[S.n_ap];
+            bool logu = S.n_ap >= 2 && S.edges[0] > 0;
+            for (int p = 1; logu && p < S.n_ap; ++p)
+                logu = std::fabs(std::log(S.edges[p + 1] / S.edges[p]) - std::log(S.edges[1] / S.edges[0])) <
+                       1e-9 * std::fabs(std::log(S.edges[1] / S.edges[0]));
+            const int nb = logu ? S.n_ap : std::max(64, 4 * S.n_ap);
+            G.lut_identity = logu ? 1 : 0;
+            G.lut_off = int(ctx->lut.size());
+            G.lut_n = nb;
+            G.l0 = float(std::log2(e0 * e0));
+            G.lscale = float(nb / (std::log2(e1 * e1) - std::log2(e0 * e0)));
+            for (int b = 0; b < nb; ++b) {
+                // annulus at the lower boundary of bucket b - 1: never above the true
+                // annulus when the device's approximate log2 is off by one bucket
+                const double R2 = std::exp2(double(G.l0) + (b - 1) / double(G.lscale)) * (1.0 - 1e-5);
+                int p = 0;
+                while (p + 1 < S.n_ap && float(S.edges[p + 1] * S.edges[p + 1]) <= float(R2)) ++p;
+                ctx->lut.push_back((unsigned short)p);
+            }
+            G.e0sq_f = float(S.edges[0] * S.edges[0]);
+            G.ensq_f = float(S.edges[S.n_ap] * S.edges[S.n_ap]);
         } else if (S.geometry == M2M_GEOM_PIXELS) {
             if (S.nx < 1 || S.ny < 1 || (long long)S.nx * S.ny != S.n_ap || !(S.xhi > S.xlo) || !(S.yhi > S.ylo))
                 return fail(ctx, M2M_ERR_ARG, "group %d: pixels need nx*ny == n_ap and a non-empty box", g);
             G.nx = S.nx; G.ny = S.ny;
             G.xlo = S.xlo; G.ylo = S.ylo; G.xw = S.xhi - S.xlo; G.yw = S.yhi - S.ylo;
+            G.ixw = float(S.nx / (S.xhi - S.xlo));
+            G.iyw = float(S.ny / (S.yhi - S.ylo));
+            G.xlo_f = float(S.xlo);
+            G.ylo_f = float(S.ylo);
+            G.lut_off = int(ctx->lut.size());
+            G.lut_n = 0;
             const double a_pix = (S.xhi - S.xlo) / S.nx * ((S.yhi - S.ylo) / S.ny);
             for (int p = 0; p < S.n_ap; ++p) area[p] = a_pix;
         } else {
@@ -183,6 +221,13 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
             const bool ok = kind == kKindMass || kind == kKindV2 || is_gh(kind) || (ctx->internal && kind == kKindV1);
             if (!ok) return fail(ctx, M2M_ERR_ARG, "group %d: unknown observable kind %d", g, kind);
             G.kinds[k] = kind;
+            for (int k2 = 0; k2 < k; ++k2)
+                if (S.kinds[k2] == kind) return fail(ctx, M2M_ERR_ARG, "group %d: kind %d listed twice", g, kind);
+            if (kind == kKindMass) G.k_mass = k;
+            if (kind == kKindV2) G.k_v2 = k;
+            if (kind == kKindV1) G.k_v1 = k;
+            if (is_gh(kind)) G.k_gh[kind - kKindGH0] = k;
+            if (kind == kKindV2) G.has_v2 = 1;
             if (is_gh(kind)) {
                 has_gh = true;
                 if (kind - kKindGH0 > G.max_gh) G.max_gh = kind - kKindGH0;
@@ -211,6 +256,10 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.J = J;
     m.n_ap_total = nap;
     m.n_edges_total = ned;
+    m.n_lut = int(ctx->lut.size());
+    int max_gh = -1;
+    for (int g = 0; g < m.n_groups; ++g) max_gh = std::max(max_gh, m.g[g].max_gh);
+    m.rec_len = 5 + (max_gh + 1);
     ctx->Y.assign(J, 0.0);
     ctx->sig.assign(J, 1.0);
     if (obs->Y && obs->sigY) {
@@ -264,8 +313,9 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         m.lc_lnr0 = std::log(1e-6);
         m.lc_dlnr = (std::log(1e8) - m.lc_lnr0) / (n - 1);
         ctx->lcE.resize(n);
+        const Cst<double> kd = make_cst<double>(m);
         for (int k = 0; k < n; ++k) {
-            ctx->lcE[k] = circ_energy<double>(m, std::exp(m.lc_lnr0 + k * m.lc_dlnr));
+            ctx->lcE[k] = circ_energy<double>(m, kd, std::exp(m.lc_lnr0 + k * m.lc_dlnr));
             if (k > 0 && !(ctx->lcE[k] > ctx->lcE[k - 1]))
                 return fail(ctx, M2M_ERR_ARG, "circular-orbit energy is not increasing with radius");
         }
@@ -304,20 +354,68 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     return M2M_OK;
 }
 
+// Step kernels: a generic one reading the observable shape at run time, and
+// versions compiled for common shapes (mass annuli + kinematic annuli; one pixel
+// group of mass and h1..h4), picked at creation by matching the group masks.
+template <class T>
+struct StepKernel {
+    using Fn = void (*)(const Model, const Cst<T>, const State<T>, const Buffers, int, int);
+};
+
+// Resident blocks per SM the kernels are compiled for (register budget).
+template <class T>
+constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
+
+template <class T, int WPS, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+static typename StepKernel<T>::Fn step_fn() { return k_step<T, WPS, kMinBlocks<T>, M0, M1, M2, M3>; }
+
+static unsigned group_mask(const GroupDesc &G)
+{
+    unsigned mk = 0;
+    if (G.k_mass >= 0) mk |= kBitMass;
+    if (G.k_v2 >= 0) mk |= kBitV2;
+    if (G.k_v1 >= 0) mk |= kBitV1;
+    for (int n = 0; n < 7; ++n)
+        if (G.k_gh[n] >= 0) mk |= bit_gh(n);
+    if (G.geometry == 1) mk |= kBitPix;
+    return mk;
+}
+
+template <class T, int WPS>
+static typename StepKernel<T>::Fn pick_step(const Model &m)
+{
+    unsigned mk[4] = {0, 0, 0, 0};
+    for (int g = 0; g < m.n_groups; ++g) mk[g] = group_mask(m.g[g]);
+    constexpr unsigned kin1 = kBitV2 | bit_gh(4), kin2 = kBitV2 | bit_gh(3) | bit_gh(4);
+    constexpr unsigned map = kBitPix | kBitMass | bit_gh(1) | bit_gh(2) | bit_gh(3) | bit_gh(4);
+    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin1) return step_fn<T, WPS, kBitMass, kin1, 0u, 0u>();
+    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin2) return step_fn<T, WPS, kBitMass, kin2, 0u, 0u>();
+    if (m.n_groups == 1 && mk[0] == map) return step_fn<T, WPS, map, 0u, 0u, 0u>();
+    return step_fn<T, WPS, kDyn, kDyn, kDyn, kDyn>();
+}
+
+template <class T>
+static typename StepKernel<T>::Fn step_kernel(const m2m_ctx *c)
+{
+    return reinterpret_cast<typename StepKernel<T>::Fn>(c->kstep);
+}
+
 template <class T, int WPS>
 static m2m_status configure_kernels(m2m_ctx *ctx)
 {
-    ctx->smem_step = step_smem_bytes<T>(ctx->m);
-    ctx->smem_mat = ctx->smem_step - sizeof(long long) * size_t(ctx->m.hist_words);
+    // the finalize reuses the start of the dynamic shared memory for a block reduction
+    ctx->smem_step = std::max(smem_bytes<T>(ctx->m, 1), size_t(256) * sizeof(double));
+    ctx->smem_mat = smem_bytes<T>(ctx->m, 0);
     int maxsm = 0;
     CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     if (ctx->smem_step > size_t(maxsm))
         return fail(ctx, M2M_ERR_ARG, "observable set and prior grid need %zu B of shared memory (limit %d)",
                     ctx->smem_step, maxsm);
-    CU(cudaFuncSetAttribute(k_step<T, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_step)));
-    CU(cudaFuncSetAttribute(k_materialize<T, WPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_mat)));
+    ctx->kstep = reinterpret_cast<void *>(pick_step<T, WPS>(ctx->m));
+    CU(cudaFuncSetAttribute(step_kernel<T>(ctx), cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_step)));
+    CU(cudaFuncSetAttribute(k_materialize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_mat)));
     int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step<T, WPS>, ctx->block, ctx->smem_step));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, step_kernel<T>(ctx), ctx->block, ctx->smem_step));
     if (occ < 1) return fail(ctx, M2M_ERR_ARG, "step kernel cannot be resident with block %d", ctx->block);
     if (ctx->bps <= 0 || ctx->bps > occ) ctx->bps = occ;
     return M2M_OK;
@@ -341,11 +439,17 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     if ((s = up(ctx->d_Y, ctx->Y)) != M2M_OK) return s;
     if ((s = up(ctx->d_sig, ctx->sig)) != M2M_OK) return s;
     if ((s = up(ctx->d_post, ctx->obs_post)) != M2M_OK) return s;
+    free_dev(ctx->d_lut);
+    CU(cudaMalloc(&ctx->d_lut, sizeof(unsigned short) * (ctx->lut.size() + 1)));
+    if (!ctx->lut.empty())
+        CU(cudaMemcpy(ctx->d_lut, ctx->lut.data(), sizeof(unsigned short) * ctx->lut.size(), cudaMemcpyHostToDevice));
     free_dev(ctx->d_kind);
     CU(cudaMalloc(&ctx->d_kind, sizeof(int) * m.J));
     CU(cudaMemcpy(ctx->d_kind, ctx->obs_kind.data(), sizeof(int) * m.J, cudaMemcpyHostToDevice));
     CU(cudaMalloc(&ctx->d_iscale, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_c, sizeof(double) * m.J));
+    CU(cudaMalloc(&ctx->d_rec, sizeof(double) * m.n_ap_total * m.rec_len));
+    CU(cudaMemset(ctx->d_rec, 0, sizeof(double) * m.n_ap_total * m.rec_len));
     CU(cudaMalloc(&ctx->d_ytil, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_yraw, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_delta, sizeof(double) * m.J));
@@ -402,6 +506,12 @@ static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *o
             else ctx->own_stream = true;
         }
     }
+    if (s == M2M_OK) {
+        double h[7][7];
+        herm_table(h);
+        cudaError_t e = cudaMemcpyToSymbol(kHerm, h, sizeof h);
+        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "Hermite table: %s", cudaGetErrorString(e));
+    }
     if (s == M2M_OK) s = upload_tables(ctx);
     if (s != M2M_OK) {
         g_create_error = ctx->err;
@@ -424,9 +534,9 @@ extern "C" m2m_status m2m_create(const m2m_potential *pot, const m2m_observables
 static Buffers buffers(m2m_ctx *c)
 {
     Buffers b;
-    b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE;
+    b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
-    b.c = c->d_c; b.prior = c->d_prior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
 }
@@ -447,14 +557,17 @@ static int grid_for(m2m_ctx *c)
     long long need = (c->n + c->block - 1) / c->block;
     long long g = (long long)c->nsm * c->bps;
     if (need < g) g = need;
+    // no block may process more than kMaxParticlesPerBlock particles (exact 32-bit sums)
+    const long long floor_g = (c->n + kMaxParticlesPerBlock - 1) / kMaxParticlesPerBlock;
+    if (g < floor_g) g = floor_g;
     return g < 1 ? 1 : int(g);
 }
 
 template <class T, int WPS>
 static void launch_step(m2m_ctx *c, int push, int init)
 {
-    k_step<T, WPS><<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, state<T>(c), buffers(c), push, init);
-    k_finalize<WPS><<<1, 1024, 0, c->stream>>>(c->m, buffers(c), c->n, init);
+    step_kernel<T>(c)<<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c),
+                                                                              buffers(c), push, init);
 }
 
 static void launch_one(m2m_ctx *c, int push, int init)
@@ -467,9 +580,9 @@ template <class T, int WPS>
 static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
 {
     cudaEventRecord(ev[0], c->stream);
-    k_step<T, WPS><<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, state<T>(c), buffers(c), 1, 0);
+    step_kernel<T>(c)<<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c),
+                                                                              buffers(c), 1, 0);
     cudaEventRecord(ev[1], c->stream);
-    k_finalize<WPS><<<1, 1024, 0, c->stream>>>(c->m, buffers(c), c->n, 0);
     cudaEventRecord(ev[2], c->stream);
 }
 
@@ -500,7 +613,8 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     d_bad = reinterpret_cast<unsigned *>(d_v2 + 1);
     CU(cudaMemsetAsync(d_v2, 0, sizeof(unsigned long long) + sizeof(unsigned), ctx->stream));
     if (ctx->n > 0)
-        k_load_stats<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(m, dx, dy, dz, dvx, dvy, dvz, dw, ctx->n, d_v2, d_bad);
+        k_load_stats<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(m, make_cst<double>(m), dx, dy, dz, dvx, dvy, dvz, dw,
+                                                             ctx->n, d_v2, d_bad);
     unsigned long long v2bits = 0;
     unsigned bad = 0;
     cudaError_t e = cudaMemcpyAsync(&v2bits, d_v2, sizeof v2bits, cudaMemcpyDeviceToHost, ctx->stream);
@@ -690,7 +804,8 @@ static void launch_materialize(m2m_ctx *c)
 {
     const int g = grid_for(c);
     cudaMemsetAsync(c->d_acc, 0, 2 * sizeof(long long), c->stream);
-    k_materialize<T, WPS><<<g, c->block, c->smem_mat, c->stream>>>(c->m, state<T>(c), buffers(c), c->d_wout, c->d_acc);
+    k_materialize<T><<<g, c->block, c->smem_mat, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c), buffers(c),
+                                                              c->d_wout, c->d_acc);
     k_scale<<<g, c->block, 0, c->stream>>>(c->d_wout, c->n, c->d_acc, c->m, c->d_sc);
 }
 
@@ -849,7 +964,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.ncell = m.ncell;
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.ncell) + 8 * m.ncell + sizeof(Scalars));
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + m.ncell) +
+                          8 * m.ncell + sizeof(Scalars));
     char *p = buf.data();
     for (int k = 0; k < 7; ++k) {
         if (n) CU(cudaMemcpy(p, ctx->st[k], es * n, cudaMemcpyDeviceToHost));
@@ -862,6 +978,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
         CU(cudaMemcpy(p, d, sizeof(double) * m.J, cudaMemcpyDeviceToHost));
         p += sizeof(double) * m.J;
     }
+    CU(cudaMemcpy(p, ctx->d_rec, sizeof(double) * m.n_ap_total * m.rec_len, cudaMemcpyDeviceToHost));
+    p += sizeof(double) * m.n_ap_total * m.rec_len;
     if (m.ncell) {
         CU(cudaMemcpy(p, ctx->d_prior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
         p += sizeof(double) * m.ncell;
@@ -893,7 +1011,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         return fail(ctx, M2M_ERR_ARG, "%s was written for different descriptors", path);
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.ncell) + 8 * m.ncell + sizeof(Scalars));
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + m.ncell) +
+                          8 * m.ncell + sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
     if (!ok) return fail(ctx, M2M_ERR_ARG, "%s is truncated", path);
@@ -921,6 +1040,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         CU(cudaMemcpy(d, p, sizeof(double) * m.J, cudaMemcpyHostToDevice));
         p += sizeof(double) * m.J;
     }
+    CU(cudaMemcpy(ctx->d_rec, p, sizeof(double) * m.n_ap_total * m.rec_len, cudaMemcpyHostToDevice));
+    p += sizeof(double) * m.n_ap_total * m.rec_len;
     if (m.ncell) {
         CU(cudaMemcpy(ctx->d_prior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
         p += sizeof(double) * m.ncell;
@@ -1147,9 +1268,9 @@ extern "C" void m2m_destroy(m2m_ctx *ctx)
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_state(ctx);
-    free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE);
+    free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
-    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_prior); free_dev(ctx->d_ytil);
+    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

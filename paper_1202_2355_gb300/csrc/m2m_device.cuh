@@ -1,7 +1,6 @@
 // Device side of the M2M step: model description, per-particle arithmetic and
-// the kernels. Templated on the state type T (double: FP64 mode; float: mixed
-// mode) and on the number of int64 words per fixed-point sum (2 in FP64 mode,
-// 1 in mixed mode).
+// the step kernel. Templated on the state type T: double (FP64 mode) or float
+// (mixed mode: FP32 state, push and kernel values; exact integer bin sums).
 //
 // Method (arXiv 1202.2355): leap-frog push (Sec. 4.1), observables
 // y_j = sum_i w_i K_j(z_i) (eq. obs) with the Gauss-Hermite kernels of
@@ -11,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace m2m {
@@ -32,9 +32,20 @@ struct GroupDesc {
     int ap_off;     // first aperture index (into Vp / 1/sp arrays)
     int edge_off;   // first edge (annuli)
     int max_gh;     // highest Gauss-Hermite order used, -1 if none
+    int has_v2;     // the group deposits v_los^2 (range-checked against v2max)
     int nx, ny;
     int kinds[kMaxKinds];
     double xlo, ylo, xw, yw;  // pixel box origin and widths (xhi - xlo, yhi - ylo)
+    // FP32 versions: pixel origin and nx/xw, ny/yw; annulus lookup: bucket
+    // b = floor((log2 R^2 - l0) lscale) -> first candidate annulus lut[lut_off + b]
+    float xlo_f, ylo_f, ixw, iyw;
+    int lut_off, lut_n;
+    float l0, lscale;
+    float e0sq_f, ensq_f;     // squared first and last edge (FP32 annuli)
+    int lut_identity;         // edges uniform in log R: bucket b is annulus b (no table load)
+    // plan: kind index (0..n_kinds-1) of each kernel in the group, or -1
+    int k_mass, k_v2, k_v1;
+    int k_gh[7];
 };
 
 struct Model {
@@ -45,7 +56,7 @@ struct Model {
     // projection
     double sin_i, cos_i;
     // observables
-    int n_groups, J, n_ap_total, n_edges_total;
+    int n_groups, J, n_ap_total, n_edges_total, n_lut;
     GroupDesc g[kMaxGroups];
     // priors
     int mode, nE, nx, e_spacing, signed_lz, update_every, ncell;
@@ -59,11 +70,99 @@ struct Model {
     long long n_relax;
     // fixed point: value = words / scale
     double fx_w, fx_v2, fx_gh, v2max;
-    int wps;                      // int64 words per sum
+    int wps;                      // int64 words per sum in the global sums
     int hist_words, off_total, off_grid, off_count;
+    int rec_len;                  // doubles per aperture record of the force of change
 };
 
-// Per-fit scalars living in device memory, written by the finalize kernel.
+// Compile-time shape of an observable group, for step kernels specialised to a
+// configuration: bits for the kernels it deposits and its geometry. kDyn: read the
+// shape from the runtime GroupDesc (the generic kernel); 0: no such group.
+constexpr unsigned kBitMass = 1u, kBitV2 = 2u, kBitV1 = 4u, kBitPix = 1u << 15;
+constexpr unsigned kDyn = 0xFFFFFFFFu;
+__host__ __device__ constexpr unsigned bit_gh(int n) { return 8u << n; }
+__host__ __device__ constexpr int mask_max_gh(unsigned m, int n = 6)
+{
+    return n < 0 ? -1 : ((m & bit_gh(n)) ? n : mask_max_gh(m, n - 1));
+}
+
+template <unsigned M>
+struct GP {
+    static constexpr unsigned mask = M;
+    static constexpr bool dyn = M == kDyn;
+    __device__ static bool present(const Model &m, int g)
+    {
+        if constexpr (dyn) return g < m.n_groups;
+        else return M != 0u;
+    }
+    __device__ static bool pixels(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.geometry == 1;
+        else return (M & kBitPix) != 0u;
+    }
+    __device__ static bool mass(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.k_mass >= 0;
+        else return (M & kBitMass) != 0u;
+    }
+    __device__ static bool v2(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.k_v2 >= 0;
+        else return (M & kBitV2) != 0u;
+    }
+    __device__ static bool v1(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.k_v1 >= 0;
+        else return (M & kBitV1) != 0u;
+    }
+    __device__ static bool gh(const GroupDesc &G, int n)
+    {
+        if constexpr (dyn) return G.k_gh[n] >= 0;
+        else return (M & bit_gh(n)) != 0u;
+    }
+    __device__ static int max_gh(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.max_gh;
+        else return mask_max_gh(M);
+    }
+};
+
+// Calls f(GP<M>{}, g) for each present group g, with g a compile-time constant.
+template <int G0, unsigned M, unsigned... Rest, class F>
+__device__ __forceinline__ void each_group(const Model &m, F &&f)
+{
+    if (GP<M>::present(m, G0)) f(GP<M>{}, G0);
+    if constexpr (sizeof...(Rest) > 0) each_group<G0 + 1, Rest...>(m, f);
+}
+
+// Model constants in the state type, so that the FP32 path runs no FP64 operation.
+template <class T>
+struct Cst {
+    T GM, a, GMs, rs, v0sq, r0sq, q2, phi_min, hn_phi0, sin_i, cos_i;
+    T dt, hdt, dteps, mu, v2max, fx_w, fx_v2, fx_gh;
+    T s_lo, s_den, e_scale, nE, nx;
+    T lc_lnr0, lc_dlnr, lc_r0, lc_rmax;
+};
+
+template <class T>
+inline Cst<T> make_cst(const Model &m)
+{
+    Cst<T> k;
+    k.GM = T(m.G * m.M); k.a = T(m.a); k.GMs = T(m.G * m.Ms); k.rs = T(m.rs);
+    k.v0sq = T(m.v0 * m.v0); k.r0sq = T(m.r0 * m.r0); k.q2 = T(m.q * m.q);
+    k.phi_min = T(m.phi_min); k.hn_phi0 = T(m.rs > 0 ? -m.G * m.Ms / m.rs : 0.0);
+    k.sin_i = T(m.sin_i); k.cos_i = T(m.cos_i);
+    k.dt = T(m.dt); k.hdt = T(0.5 * m.dt); k.dteps = T(m.dt * m.eps); k.mu = T(m.mu);
+    k.v2max = T(m.v2max); k.fx_w = T(m.fx_w); k.fx_v2 = T(m.fx_v2); k.fx_gh = T(m.fx_gh);
+    k.s_lo = T(m.s_lo); k.s_den = T(m.s_den);
+    k.e_scale = T(m.G * m.M > 0 ? m.a / (m.G * m.M) : 0.0);
+    k.nE = T(m.nE); k.nx = T(m.nx);
+    k.lc_lnr0 = T(m.lc_lnr0); k.lc_dlnr = T(m.lc_dlnr);
+    k.lc_r0 = T(exp(m.lc_lnr0)); k.lc_rmax = T(exp(m.lc_lnr0 + (m.lc_n - 1) * m.lc_dlnr));
+    return k;
+}
+
+// Per-fit scalars living in device memory, written by the finalize.
 struct Scalars {
     long long t;        // steps completed
     double wscale;      // current weight = wscale * stored weight
@@ -75,6 +174,7 @@ struct Scalars {
     double Wrange;      // largest total weight the fixed-point sums can hold
     int pending;        // the previous step's force of change is still to be applied
     unsigned err;       // latched kErr* bits
+    unsigned blocks_done;  // blocks of the running step kernel that have flushed their sums
 };
 
 template <class T>
@@ -86,26 +186,54 @@ struct State {
 
 struct Buffers {
     const double *edges, *Vp, *isp;  // per group edges, per aperture V_p and 1/sigma_p
+    const unsigned short *lut;       // annulus lookup tables (FP32 path)
     const double *lcE;               // E_c table
     const double *Y, *sig;
     const int *obs_kind;             // per observable: kind
     const double *obs_post;          // per observable: factor applied to the raw sum (1/area for mass)
     const double *obs_iscale;        // per observable: 1/fixed-point scale
     double *c;                       // per observable: coefficient of the force of change
+    double *rec;                     // per aperture: the data term of eq. modFOC as polynomials in nu
     double *prior;                   // per cell: prior (cell mean weight)
     long long *prior_count;          // per cell: particle count at the last update
-    long long *hist;                 // fixed-point accumulators
+    long long *hist;                 // global fixed-point sums
     double *ytil, *yraw, *delta;
     Scalars *sc;
 };
 
 // ---------------------------------------------------------------- math helpers
+// FP32 (mixed mode) uses the hardware approximations on the device: exp and log
+// through ex2/lg2 (relative error ~2^-21 |x| for exp), division through rcp. FP64
+// keeps the correctly rounded functions.
 __host__ __device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
 __host__ __device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
-__host__ __device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__host__ __device__ __forceinline__ float d_exp(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __expf(x);
+#else
+    return expf(x);
+#endif
+}
 __host__ __device__ __forceinline__ double d_exp(double x) { return exp(x); }
-__host__ __device__ __forceinline__ float d_log(float x) { return logf(x); }
+__host__ __device__ __forceinline__ float d_log(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __logf(x);
+#else
+    return logf(x);
+#endif
+}
 __host__ __device__ __forceinline__ double d_log(double x) { return log(x); }
+__host__ __device__ __forceinline__ float d_div(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+__host__ __device__ __forceinline__ double d_div(double a, double b) { return a / b; }
 __host__ __device__ __forceinline__ float d_log1p(float x) { return log1pf(x); }
 __host__ __device__ __forceinline__ double d_log1p(double x) { return log1p(x); }
 __host__ __device__ __forceinline__ float d_floor(float x) { return floorf(x); }
@@ -137,7 +265,7 @@ __host__ __device__ __forceinline__ T nfw_mu(T qq)
             return qq * qq * s;
         }
     } else if (qq < T(0.3)) {
-        const T t = qq / (T(1) + qq);
+        const T t = d_div(qq, T(1) + qq);
         T s = T(1.0 / 14.0);
         s = T(1.0 / 13.0) + t * s;
         s = T(1.0 / 12.0) + t * s;
@@ -153,33 +281,32 @@ __host__ __device__ __forceinline__ T nfw_mu(T qq)
         s = T(0.5) + t * s;
         return t * t * s;
     }
-    return d_log1p(qq) - qq / (T(1) + qq);
+    return d_log1p(qq) - d_div(qq, T(1) + qq);
 }
 
 template <class T>
-__host__ __device__ __forceinline__ T potential(const Model &m, T x, T y, T z)
+__host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k, T x, T y, T z)
 {
     if (m.pot == 2) {
-        const T q2 = T(m.q * m.q);
-        const T D = T(m.r0 * m.r0) + x * x + y * y + z * z / q2;
-        return T(0.5 * m.v0 * m.v0) * d_log(D);
+        const T D = k.r0sq + x * x + y * y + d_div(z * z, k.q2);
+        return T(0.5) * k.v0sq * d_log(D);
     }
     const T r = d_sqrt(x * x + y * y + z * z);
-    T phi = -T(m.G * m.M) / (r + T(m.a));
-    if (m.pot == 1) phi += (r > T(0)) ? -T(m.G * m.Ms) * d_log1p(r / T(m.rs)) / r : -T(m.G * m.Ms / m.rs);
+    T phi = -d_div(k.GM, r + k.a);
+    if (m.pot == 1) phi += (r > T(0)) ? -d_div(k.GMs * d_log1p(d_div(r, k.rs)), r) : k.hn_phi0;
     return phi;
 }
 
 template <class T>
-__host__ __device__ __forceinline__ void accel(const Model &m, T x, T y, T z, T &ax, T &ay, T &az)
+__host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay,
+                                               T &az)
 {
     if (m.pot == 2) {
-        const T q2 = T(m.q * m.q);
-        const T D = T(m.r0 * m.r0) + x * x + y * y + z * z / q2;
-        const T f = -T(m.v0 * m.v0) / D;
+        const T D = k.r0sq + x * x + y * y + d_div(z * z, k.q2);
+        const T f = -d_div(k.v0sq, D);
         ax = f * x;
         ay = f * y;
-        az = f * z / q2;
+        az = d_div(f * z, k.q2);
         return;
     }
     const T r2 = x * x + y * y + z * z;
@@ -188,10 +315,10 @@ __host__ __device__ __forceinline__ void accel(const Model &m, T x, T y, T z, T 
         ax = ay = az = T(0);
         return;
     }
-    const T ra = r + T(m.a);
+    const T ra = r + k.a;
     // -g(r)/r with g = G M(<r) / r^2
-    T f = T(m.G * m.M) / (ra * ra * r);
-    if (m.pot == 1) f += T(m.G * m.Ms) * nfw_mu(r / T(m.rs)) / (r2 * r);
+    T f = d_div(k.GM, ra * ra * r);
+    if (m.pot == 1) f += d_div(k.GMs * nfw_mu(d_div(r, k.rs)), r2 * r);
     ax = -f * x;
     ay = -f * y;
     az = -f * z;
@@ -199,41 +326,43 @@ __host__ __device__ __forceinline__ void accel(const Model &m, T x, T y, T z, T 
 
 // One kick-drift-kick leap-frog step.
 template <class T>
-__device__ __forceinline__ void leapfrog(const Model &m, T &x, T &y, T &z, T &vx, T &vy, T &vz)
+__device__ __forceinline__ void leapfrog(const Model &m, const Cst<T> &k, T &x, T &y, T &z, T &vx, T &vy, T &vz)
 {
-    const T hdt = T(0.5 * m.dt), dt = T(m.dt);
     T ax, ay, az;
-    accel(m, x, y, z, ax, ay, az);
-    vx += hdt * ax;
-    vy += hdt * ay;
-    vz += hdt * az;
-    x += dt * vx;
-    y += dt * vy;
-    z += dt * vz;
-    accel(m, x, y, z, ax, ay, az);
-    vx += hdt * ax;
-    vy += hdt * ay;
-    vz += hdt * az;
+    accel(m, k, x, y, z, ax, ay, az);
+    vx += k.hdt * ax;
+    vy += k.hdt * ay;
+    vz += k.hdt * az;
+    x += k.dt * vx;
+    y += k.dt * vy;
+    z += k.dt * vz;
+    accel(m, k, x, y, z, ax, ay, az);
+    vx += k.hdt * ax;
+    vy += k.hdt * ay;
+    vz += k.hdt * az;
 }
 
 // ---------------------------------------------------------------- observables
 
+// Sky coordinates for the line of sight n = (0, sin i, cos i): X = x (not
+// returned), Y = y cos i - z sin i, v_los = vy sin i + vz cos i.
 template <class T>
-__device__ __forceinline__ void project(const Model &m, T y, T z, T vy, T vz, T &Y, T &vlos)
+__device__ __forceinline__ void project(const Cst<T> &k, T y, T z, T vy, T vz, T &Y, T &vlos)
 {
-    const T si = T(m.sin_i), ci = T(m.cos_i);
-    Y = y * ci - z * si;
-    vlos = vy * si + vz * ci;
+    Y = y * k.cos_i - z * k.sin_i;
+    vlos = vy * k.sin_i + vz * k.cos_i;
 }
 
-// Aperture of sky point (X, Y) in group G, or -1. Annuli: binary search of the
-// half-open intervals edges[p] <= R < edges[p+1].
-template <class T>
-__device__ __forceinline__ int aperture(const GroupDesc &G, const T *edges, T X, T Y)
+// Aperture of sky point (X, Y) in group G, or -1. FP64 evaluates the definition:
+// half-open annuli [edge_p, edge_p+1) in R = sqrt(X^2 + Y^2) (binary search), pixel
+// p = py nx + px with px = floor((X - xlo) nx / (xhi - xlo)).
+template <unsigned M>
+__device__ __forceinline__ int aperture(const GroupDesc &G, const double *edges, const float *,
+                                        const unsigned short *, double X, double Y)
 {
-    if (G.geometry == 0) {
-        const T R = d_sqrt(X * X + Y * Y);
-        const T *e = edges + G.edge_off;
+    if (!GP<M>::pixels(G)) {
+        const double R = sqrt(X * X + Y * Y);
+        const double *e = edges + G.edge_off;
         if (!(R >= e[0]) || !(R < e[G.n_ap])) return -1;
         int lo = 0, hi = G.n_ap;  // e[lo] <= R < e[hi]
         while (hi - lo > 1) {
@@ -243,96 +372,157 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const T *edges, T X,
         }
         return lo;
     }
-    const T fx = d_floor((X - T(G.xlo)) * T(G.nx) / T(G.xw));
-    const T fy = d_floor((Y - T(G.ylo)) * T(G.ny) / T(G.yw));
-    if (!(fx >= T(0)) || !(fx < T(G.nx)) || !(fy >= T(0)) || !(fy < T(G.ny))) return -1;
+    const double fx = floor((X - G.xlo) * G.nx / G.xw);
+    const double fy = floor((Y - G.ylo) * G.ny / G.yw);
+    if (!(fx >= 0.0) || !(fx < G.nx) || !(fy >= 0.0) || !(fy < G.ny)) return -1;
     return int(fy) * G.nx + int(fx);
 }
 
-// Gauss-Hermite kernel values K_n = 2 sqrt(pi) u_n(nu) = sqrt(2^(1-n)/n!) H_n(nu) e^(-nu^2/2)
-// for n = 0..nmax, with H_n by the three-term recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}.
-template <class T>
-__device__ __forceinline__ void gh_values(T nu, int nmax, T *K)
+// FP32: the squared radius against squared edges, starting from a candidate found
+// from log2 R^2 (the annulus itself for log-uniform edges, else a lookup table) and
+// corrected by exact comparisons.
+template <unsigned M>
+__device__ __forceinline__ int aperture(const GroupDesc &G, const float *, const float *e2s,
+                                        const unsigned short *lut, float X, float Y)
 {
-    const T e = d_exp(T(-0.5) * nu * nu);
-    T hm1 = T(1), h = T(2) * nu;
-    K[0] = T(1.4142135623730950488) * e;
-    if (nmax >= 1) K[1] = h * e;  // sqrt(2^0/1!) = 1
-    // c_n = sqrt(2^(1-n)/n!)
-    const T cn[7] = {T(1.4142135623730950488), T(1.0), T(0.5), T(0.20412414523193150818),
-                     T(0.072168783648703220563), T(0.022821773229381921355),
-                     T(0.0065881721129167866018)};
-    for (int n = 1; n < nmax; ++n) {
-        const T hn1 = T(2) * nu * h - T(2 * n) * hm1;
-        hm1 = h;
-        h = hn1;
-        K[n + 1] = cn[n + 1] * h * e;
+    if (!GP<M>::pixels(G)) {
+        const float R2 = X * X + Y * Y;
+        if (!(R2 >= G.e0sq_f) || !(R2 < G.ensq_f)) return -1;
+        int b = __float2int_rd((__log2f(R2) - G.l0) * G.lscale);
+        b = b < 0 ? 0 : (b >= G.lut_n ? G.lut_n - 1 : b);
+        int p = G.lut_identity ? b : int(lut[G.lut_off + b]);
+        const float *e = e2s + G.edge_off;
+        while (p > 0 && R2 < e[p]) --p;
+        while (R2 >= e[p + 1]) ++p;
+        return p;
+    }
+    const float fx = floorf((X - G.xlo_f) * G.ixw);
+    const float fy = floorf((Y - G.ylo_f) * G.iyw);
+    if (!(fx >= 0.f) || !(fx < float(G.nx)) || !(fy >= 0.f) || !(fy < float(G.ny))) return -1;
+    return int(fy) * G.nx + int(fx);
+}
+
+// ---------------------------------------------------------------- kernel values
+
+// c_n = sqrt(2^(1-n)/n!): K_n = 2 sqrt(pi) u_n(nu) = c_n H_n(nu) exp(-nu^2/2) (eq. lumghn).
+__host__ __device__ constexpr double gh_c(int n)
+{
+    return n == 0 ? 1.4142135623730950488
+         : n == 1 ? 1.0
+         : n == 2 ? 0.5
+         : n == 3 ? 0.20412414523193150818
+         : n == 4 ? 0.072168783648703220563
+         : n == 5 ? 0.022821773229381921355
+                  : 0.0065881721129167866018;
+}
+
+enum { kClassMass = 0, kClassVel = 1, kClassGH = 2 };  // fixed-point scale class
+
+template <class T>
+struct Tables {
+    const T *edges;       // per group edges (FP64 path)
+    const float *e2;      // squared edges (FP32 path)
+    const unsigned short *lut;
+    const T *vp, *isp;
+};
+
+// Emits emit(slot, w K_slot, class) for every kernel of group G at aperture p:
+// surface mass (K = 1), v_los^2, v_los, and the Gauss-Hermite b_n with H_n from the
+// recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}, evaluated once up to the group's
+// highest order.
+template <unsigned M, class T, class F>
+__device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T> &tb, int p, T vlos, T w, F &&emit)
+{
+    using P = GP<M>;
+    const int base = G.obs_off + p;
+    if (P::mass(G)) emit(base + G.k_mass * G.n_ap, w, kClassMass);
+    if (P::v2(G)) emit(base + G.k_v2 * G.n_ap, w * vlos * vlos, kClassVel);
+    if (P::v1(G)) emit(base + G.k_v1 * G.n_ap, w * vlos, kClassVel);
+    const int nmax = P::max_gh(G);
+    if (nmax >= 0) {
+        const T nu = (vlos - tb.vp[G.ap_off + p]) * tb.isp[G.ap_off + p];
+        const T we = w * d_exp(T(-0.5) * nu * nu);
+        T hm1 = T(1), h = T(2) * nu;
+        if (P::gh(G, 0)) emit(base + G.k_gh[0] * G.n_ap, T(gh_c(0)) * we, kClassGH);
+        if (P::gh(G, 1)) emit(base + G.k_gh[1] * G.n_ap, h * we, kClassGH);
+#pragma unroll
+        for (int n = 1; n < 6; ++n) {
+            if (n < nmax) {
+                const T hn1 = T(2) * nu * h - T(2 * n) * hm1;
+                hm1 = h;
+                h = hn1;
+                if (P::gh(G, n + 1)) emit(base + G.k_gh[n + 1] * G.n_ap, T(gh_c(n + 1)) * h * we, kClassGH);
+            }
+        }
     }
 }
 
-// Calls f(j, K_j) for every observable j with K_j(z) != 0 for the particle with
-// sky position (X, Y) and line-of-sight velocity vlos.
-template <class T, class F>
-__device__ __forceinline__ void for_each_kernel(const Model &m, const T *edges, const T *vp,
-                                                const T *isp, T X, T Y, T vlos, F &&f)
+// The data term of eq. modFOC, sum_j K_j c_j, for one particle. In aperture p of a
+// group every kernel is a polynomial in nu = (v_los - V_p)/sigma_p, the Gauss-
+// Hermite ones times exp(-nu^2/2), so the finalize folds the coefficients c_j into
+// one record per aperture, r = [V_p, 1/sigma_p, q0, q1, q2, p0 .. p_nmax], and
+// sum_j K_j c_j = q0 + q1 nu + q2 nu^2 + exp(-nu^2/2) sum_n p_n nu^n
+// (groups without Gauss-Hermite kernels use V = 0, 1/sigma = 1, i.e. nu = v_los).
+template <unsigned... Ms, class T>
+__device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, const T *rec, T X, T Y, T vlos)
 {
-#pragma unroll
-    for (int g = 0; g < kMaxGroups; ++g) {
-        if (g >= m.n_groups) break;
+    T data = T(0);
+    each_group<0, Ms...>(m, [&](auto P, int g) {
+        constexpr unsigned M = decltype(P)::mask;
         const GroupDesc &G = m.g[g];
-        const int p = aperture(G, edges, X, Y);
-        if (p < 0) continue;
-        T gh[7];
-        if (G.max_gh >= 0) {
-            const T nu = (vlos - vp[G.ap_off + p]) * isp[G.ap_off + p];
-            gh_values(nu, G.max_gh, gh);
+        const int p = aperture<M>(G, tb.edges, tb.e2, tb.lut, X, Y);
+        if (p >= 0) {
+            const T *r = rec + (G.ap_off + p) * m.rec_len;
+            const T nu = (vlos - r[0]) * r[1];
+            T d = r[2] + nu * (r[3] + nu * r[4]);
+            const int nmax = GP<M>::max_gh(G);
+            if (nmax >= 0) {
+                T poly = T(0);
+#pragma unroll
+                for (int n = 6; n >= 0; --n)
+                    if (n <= nmax) poly = poly * nu + r[5 + n];
+                d += d_exp(T(-0.5) * nu * nu) * poly;
+            }
+            data += d;
         }
-        for (int k = 0; k < G.n_kinds; ++k) {
-            const int kind = G.kinds[k];
-            T K;
-            if (kind == kKindMass) K = T(1);
-            else if (kind == kKindV2) K = vlos * vlos;
-            else if (kind == kKindV1) K = vlos;
-            else K = gh[kind - kKindGH0];
-            f(G.obs_off + k * G.n_ap + p, kind, K);
-        }
-    }
+    });
+    return data;
 }
 
 // ---------------------------------------------------------------- priors
 
 // Energy of the circular orbit of radius R in the equatorial plane.
 template <class T>
-__host__ __device__ __forceinline__ T circ_energy(const Model &m, T R)
+__host__ __device__ __forceinline__ T circ_energy(const Model &m, const Cst<T> &k, T R)
 {
     T ax, ay, az;
-    accel(m, R, T(0), T(0), ax, ay, az);
-    return potential(m, R, T(0), T(0)) - T(0.5) * R * ax;
+    accel(m, k, R, T(0), T(0), ax, ay, az);
+    return potential(m, k, R, T(0), T(0)) - T(0.5) * R * ax;
 }
 
 // Lc(E): closed form for the Hernquist potential (E_c = -(u+1)/(2u^2) GM/a with
 // u = R/a + 1), otherwise the host table of E_c(ln R) bracketed by binary search,
 // interpolated, and refined by secant steps on E_c(R) = E.
 template <class T>
-__device__ T circular_L(const Model &m, const double *lcE, T E)
+__device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
 {
     if (m.pot != 2 && !(E < T(0))) return T(0);
     if (m.lc_closed) {
-        const T e = E * T(m.a / (m.G * m.M));
+        const T e = E * k.e_scale;
         if (!(e > T(-1))) return T(0);
-        const T u = (T(-1) - d_sqrt(T(1) - T(8) * e)) / (T(4) * e);
-        const T R = T(m.a) * (u - T(1));
-        const T ra = R + T(m.a);
-        return R * d_sqrt(T(m.G * m.M) * R) / ra;
+        const T u = d_div(T(-1) - d_sqrt(T(1) - T(8) * e), T(4) * e);
+        const T R = k.a * (u - T(1));
+        const T ra = R + k.a;
+        return d_div(R * d_sqrt(k.GM * R), ra);
     }
-    if (!(E > T(m.phi_min))) return T(0);
+    if (!(E > k.phi_min)) return T(0);
     const int n = m.lc_n;
     int lo = 0, hi = n - 1;
     T R;
     if (!(E > T(__ldg(lcE)))) {
-        R = T(exp(m.lc_lnr0));
+        R = k.lc_r0;
     } else if (!(E < T(__ldg(lcE + n - 1)))) {
-        R = T(exp(m.lc_lnr0 + (n - 1) * m.lc_dlnr));
+        R = k.lc_rmax;
     } else {
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -340,17 +530,17 @@ __device__ T circular_L(const Model &m, const double *lcE, T E)
             else hi = mid;
         }
         const T e0 = T(__ldg(lcE + lo)), e1 = T(__ldg(lcE + hi));
-        const T fr = (E - e0) / (e1 - e0);
-        R = d_exp(T(m.lc_lnr0) + (T(lo) + fr) * T(m.lc_dlnr));
+        const T fr = d_div(E - e0, e1 - e0);
+        R = d_exp(k.lc_lnr0 + (T(lo) + fr) * k.lc_dlnr);
         // secant refinement, starting from the table segment's slope
-        const T Ra = d_exp(T(m.lc_lnr0) + T(lo) * T(m.lc_dlnr));
-        const T Rb = d_exp(T(m.lc_lnr0) + T(hi) * T(m.lc_dlnr));
-        T r0 = R, f0 = circ_energy(m, r0) - E;
-        T r1 = r0 - f0 * (Rb - Ra) / (e1 - e0);
+        const T Ra = d_exp(k.lc_lnr0 + T(lo) * k.lc_dlnr);
+        const T Rb = d_exp(k.lc_lnr0 + T(hi) * k.lc_dlnr);
+        T r0 = R, f0 = circ_energy(m, k, r0) - E;
+        T r1 = r0 - f0 * d_div(Rb - Ra, e1 - e0);
         for (int it = 0; it < 3; ++it) {
-            const T f1 = circ_energy(m, r1) - E;
+            const T f1 = circ_energy(m, k, r1) - E;
             if (f1 == f0) break;
-            const T r2 = r1 - f1 * (r1 - r0) / (f1 - f0);
+            const T r2 = r1 - f1 * d_div(r1 - r0, f1 - f0);
             r0 = r1;
             f0 = f1;
             r1 = r2;
@@ -358,15 +548,17 @@ __device__ T circular_L(const Model &m, const double *lcE, T E)
         R = r1;
     }
     T ax, ay, az;
-    accel(m, R, T(0), T(0), ax, ay, az);
+    accel(m, k, R, T(0), T(0), ax, ay, az);
     return R * d_sqrt(-R * ax);
 }
 
+// Cell k*nx + l of a particle: E bin from the chosen spacing (clamped), circularity
+// bin from x = L/Lc(E) (x = Lz/Lc(E) on [-1, 1] for the signed variant, clamped).
 template <class T>
-__device__ __forceinline__ int prior_cell(const Model &m, const double *lcE, T x, T y, T z, T vx,
-                                          T vy, T vz)
+__device__ __forceinline__ int prior_cell(const Model &m, const Cst<T> &k, const double *lcE, T x, T y, T z,
+                                          T vx, T vy, T vz)
 {
-    const T E = T(0.5) * (vx * vx + vy * vy + vz * vz) + potential(m, x, y, z);
+    const T E = T(0.5) * (vx * vx + vy * vy + vz * vz) + potential(m, k, x, y, z);
     const T Lz = x * vy - y * vx;
     T L;
     if (m.signed_lz) {
@@ -375,62 +567,168 @@ __device__ __forceinline__ int prior_cell(const Model &m, const double *lcE, T x
         const T Lx = y * vz - z * vy, Ly = z * vx - x * vz;
         L = d_sqrt(Lx * Lx + Ly * Ly + Lz * Lz);
     }
-    const T Lc = circular_L(m, lcE, E);
-    T xc = (Lc > T(0)) ? L / Lc : T(0);
+    const T Lc = circular_L(m, k, lcE, E);
+    T xc = (Lc > T(0)) ? d_div(L, Lc) : T(0);
     const T xmin = m.signed_lz ? T(-1) : T(0);
     xc = xc < xmin ? xmin : (xc > T(1) ? T(1) : xc);
     T f;
-    if (m.e_spacing == 0) f = (E >= T(0)) ? T(1) : (d_log(-E) - T(m.s_lo)) / T(m.s_den);
-    else if (m.e_spacing == 1) f = (d_exp(E) - T(m.s_lo)) / T(m.s_den);
-    else f = (E - T(m.s_lo)) / T(m.s_den);
-    const T fk = d_floor(f * T(m.nE));
-    const int k = !(fk >= T(0)) ? 0 : (fk >= T(m.nE) ? m.nE - 1 : int(fk));
-    const T fl = d_floor((xc - xmin) / (T(1) - xmin) * T(m.nx));
-    const int l = !(fl >= T(0)) ? 0 : (fl >= T(m.nx) ? m.nx - 1 : int(fl));
-    return k * m.nx + l;
+    if (m.e_spacing == 0) f = (E >= T(0)) ? T(1) : d_div(d_log(-E) - k.s_lo, k.s_den);
+    else if (m.e_spacing == 1) f = d_div(d_exp(E) - k.s_lo, k.s_den);
+    else f = d_div(E - k.s_lo, k.s_den);
+    const T fk = d_floor(f * k.nE);
+    const int kb = !(fk >= T(0)) ? 0 : (fk >= k.nE ? m.nE - 1 : int(fk));
+    const T fl = d_floor(d_div(xc - xmin, T(1) - xmin) * k.nx);
+    const int lb = !(fl >= T(0)) ? 0 : (fl >= k.nx ? m.nx - 1 : int(fl));
+    return kb * m.nx + lb;
 }
 
 // ---------------------------------------------------------------- fixed point
+//
+// Global sums are int64 words: FP64 mode uses two per slot (integer part and the
+// next 32 fraction bits of v*scale), mixed mode one (round(v*scale)). Integer
+// sums are exact, so the result does not depend on the order of the additions.
 
-// Adds v * scale to a fixed-point sum. One word: round to nearest int64. Two
-// words: integer part and the next 32 fraction bits, each summed exactly.
-template <int WPS>
-__device__ __forceinline__ void fx_add(long long *h, int slot, double v, double scale)
+__device__ __forceinline__ void fx2(double v, double scale, long long &hi, long long &lo)
 {
     const double s = v * scale;
-    if (WPS == 1) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(h + slot),
-                  static_cast<unsigned long long>(__double2ll_rn(s)));
-    } else {
-        const double hi = floor(s);
-        const long long ihi = static_cast<long long>(hi);
-        const long long ilo = __double2ll_rn((s - hi) * 4294967296.0);
-        atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot), static_cast<unsigned long long>(ihi));
-        atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot + 1), static_cast<unsigned long long>(ilo));
-    }
+    const double h = floor(s);
+    hi = static_cast<long long>(h);
+    lo = __double2ll_rn((s - h) * 4294967296.0);
 }
 
-template <int WPS>
-__device__ __forceinline__ void fx_add_f(long long *h, int slot, float v, float scale)
+// Mixed mode: round(v*scale) as three signed 32-bit limbs, computed with FP32 and
+// int32 operations only. With a = |v*scale| (exact power-of-two scaling),
+// hf = floor(a 2^-32) and lf = a - hf 2^32 are exact in FP32 (a below 2^24 gives
+// hf = 0, lf = a; a above 2^32 has an ulp of at least 2^9, so lf has at most 23
+// significant bits); u = rint(lf) < 2^32. The value is sign * (hf 2^32 + u).
+struct Limbs {
+    int hi, mid, lo;  // value = hi 2^32 + mid 2^16 + lo
+};
+
+__device__ __forceinline__ Limbs split(float v, float scale)
 {
-    // mixed mode (WPS == 1): the product carries 24 significant bits
-    atomicAdd(reinterpret_cast<unsigned long long *>(h + slot),
-              static_cast<unsigned long long>(__float2ll_rn(v * scale)));
+    const float t = v * scale;
+    const float a = fabsf(t);
+    const float hf = floorf(a * 2.3283064365386963e-10f);
+    const float lf = fmaf(-hf, 4294967296.0f, a);
+    const unsigned u = __float2uint_rn(lf);
+    Limbs r;
+    r.hi = __float2int_rz(hf);
+    r.mid = static_cast<int>(u >> 16);
+    r.lo = static_cast<int>(u & 0xFFFFu);
+    if (t < 0.f) {
+        r.hi = -r.hi;
+        r.mid = -r.mid;
+        r.lo = -r.lo;
+    }
+    return r;
 }
+
+__device__ __forceinline__ long long limbs_value(long long hi, long long mid, long long lo)
+{
+    return hi * 4294967296ll + mid * 65536ll + lo;
+}
+
+// Block-shared sums. FP64 mode: the two int64 words of each slot, added with
+// 64-bit shared atomics. Mixed mode: three int32 limbs per slot added with native
+// 32-bit shared atomics; at most kMaxParticlesPerBlock particles per block keep
+// |sum of mid| and |sum of lo| below 2^31 (each term below 2^16 in magnitude), and
+// |sum of hi| < 2^31 follows from the fixed-point range. The block flush
+// recombines the limbs into the int64 word exactly.
+constexpr long long kMaxParticlesPerBlock = 32768;
+
+template <class T>
+struct Acc;
+
+template <>
+struct Acc<double> {
+    static __host__ __device__ size_t bytes(const Model &m) { return sizeof(long long) * size_t(m.hist_words); }
+    __device__ static void add(void *base, const Model &, int slot, double v, double scale)
+    {
+        if (v == 0.0) return;
+        long long *h = static_cast<long long *>(base);
+        long long hi, lo;
+        fx2(v, scale, hi, lo);
+        atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot), static_cast<unsigned long long>(hi));
+        if (lo) atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot + 1), static_cast<unsigned long long>(lo));
+    }
+    __device__ static void count(void *base, const Model &m, int c)
+    {
+        atomicAdd(reinterpret_cast<unsigned long long *>(static_cast<long long *>(base) + m.off_count + c), 1ull);
+    }
+    // global word k of the block's sums
+    __device__ static long long word(const void *base, const Model &, int k) { return static_cast<const long long *>(base)[k]; }
+};
+
+template <>
+struct Acc<float> {
+    static __host__ __device__ size_t bytes(const Model &m)
+    {
+        return sizeof(int) * (3 * size_t(m.J + 1 + m.ncell) + size_t(m.ncell)) + 8;
+    }
+    __device__ static void add(void *base, const Model &, int slot, float v, float scale)
+    {
+        if (v == 0.f) return;
+        const Limbs l = split(v, scale);
+        int *h = static_cast<int *>(base) + 3 * slot;
+        if (l.hi) atomicAdd(h, l.hi);
+        atomicAdd(h + 1, l.mid);
+        atomicAdd(h + 2, l.lo);
+    }
+    __device__ static void count(void *base, const Model &m, int c)
+    {
+        atomicAdd(static_cast<int *>(base) + 3 * (m.J + 1 + m.ncell) + c, 1);
+    }
+    __device__ static long long word(const void *base, const Model &m, int k)
+    {
+        const int *h = static_cast<const int *>(base);
+        if (k >= m.off_count) return static_cast<long long>(h[3 * (m.J + 1 + m.ncell) + (k - m.off_count)]);
+        const int *q = h + 3 * k;
+        return limbs_value(q[0], q[1], q[2]);
+    }
+};
+
+// Per-thread running total of the deposited weight, in the same fixed point.
+template <class T>
+struct Total;
+
+template <>
+struct Total<double> {
+    long long hi = 0, lo = 0;
+    __device__ void add(double v, double scale)
+    {
+        long long a, b;
+        fx2(v, scale, a, b);
+        hi += a;
+        lo += b;
+    }
+    __device__ long long word(int q, double) const { return q == 0 ? hi : lo; }
+};
+
+// Mixed mode: a compensated (Kahan) FP32 sum of the thread's weights, converted to
+// the fixed point once per thread; the order is fixed, so the result is reproducible.
+template <>
+struct Total<float> {
+    float s = 0.f, c = 0.f;
+    __device__ void add(float v, float)
+    {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ long long word(int, float scale) const
+    {
+        const Limbs l = split(s, scale);
+        return limbs_value(l.hi, l.mid, l.lo);
+    }
+};
 
 template <int WPS>
 __device__ __forceinline__ double fx_read(const long long *h, int slot)
 {
-    if (WPS == 1) return double(h[slot]);
-    return double(h[2 * slot]) + double(h[2 * slot + 1]) * (1.0 / 4294967296.0);
-}
-
-template <class T, int WPS>
-__device__ __forceinline__ void deposit(long long *h, int slot, T v, double scale)
-{
-    if (v == T(0)) return;
-    if (sizeof(T) == 4) fx_add_f<WPS>(h, slot, float(v), float(scale));
-    else fx_add<WPS>(h, slot, double(v), scale);
+    if (WPS == 1) return double(__ldcg(h + slot));
+    return double(__ldcg(h + 2 * slot)) + double(__ldcg(h + 2 * slot + 1)) * (1.0 / 4294967296.0);
 }
 
 // ---------------------------------------------------------------- force of change
@@ -439,21 +737,19 @@ __device__ __forceinline__ void deposit(long long *h, int slot, T v, double scal
 // values taken at the particle's current position and the priors held fixed:
 // F = mu dS/dw - sum_j K_j c_j, c_j = Delta_j/sigma_j (times 1/area for mass),
 // dS/dw = -ln(w/what) (eq. S+) or -ln(w/what) - 1 (eq. entropy).
-template <class T>
-__device__ __forceinline__ T foc_update(const Model &m, const T *edges, const T *vp, const T *isp,
-                                        const T *c, T prior, T w, T x, T y, T z, T vy, T vz,
-                                        unsigned &err)
+template <unsigned... Ms, class T>
+__device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec, T prior,
+                                        T w, T x, T y, T z, T vy, T vz, unsigned &err)
 {
     if (w == T(0)) return w;  // w = 0 is a fixed point
     T Y, vlos;
-    project(m, y, z, vy, vz, Y, vlos);
-    T data = T(0);
-    for_each_kernel(m, edges, vp, isp, x, Y, vlos, [&](int j, int, T K) { data += K * c[j]; });
+    project(k, y, z, vy, vz, Y, vlos);
+    const T data = data_term<Ms...>(m, tb, rec, x, Y, vlos);
     // A cell mean below the resolution of the fixed-point cell sums reads as 0;
     // the particle's weight is then unresolved too and the entropy term is dropped.
-    T dS = prior > T(0) ? -d_log(w / prior) : T(0);
+    T dS = prior > T(0) ? -d_log(d_div(w, prior)) : T(0);
     if (m.mode == 0) dS -= T(1);
-    const T h = T(m.dt * m.eps) * (T(m.mu) * dS - data);
+    const T h = k.dteps * (k.mu * dS - data);
     T wn;
     if (m.update_rule == 0) wn = w * d_exp(h);
     else wn = w * (T(1) + h);
@@ -462,143 +758,150 @@ __device__ __forceinline__ T foc_update(const Model &m, const T *edges, const T 
     return wn;
 }
 
-// Loads the per-aperture tables (edges, V_p, 1/sigma_p) into shared memory.
+// ---------------------------------------------------------------- shared-memory layout
+
 template <class T>
-__device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, T *edges_s, T *vp_s,
-                                            T *isp_s)
+struct Smem {
+    void *h;               // fixed-point sums of the block (layout of Acc<T>)
+    T *c, *prior, *edges, *vp, *isp;  // c: the force-of-change records
+    float *e2;
+    unsigned short *lut;
+};
+
+template <class T>
+__host__ __device__ inline size_t acc_bytes_padded(const Model &m)
 {
-    for (int k = threadIdx.x; k < m.n_edges_total; k += blockDim.x) edges_s[k] = T(b.edges[k]);
+    return (Acc<T>::bytes(m) + 15) / 16 * 16;
+}
+
+template <class T>
+__host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist)
+{
+    size_t b = with_hist ? acc_bytes_padded<T>(m) : 0;
+    b += sizeof(T) * size_t(m.n_ap_total * m.rec_len + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
+    b += sizeof(float) * size_t(m.n_edges_total);
+    b += sizeof(unsigned short) * size_t(m.n_lut) + 16;
+    return b;
+}
+
+template <class T>
+__device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, int with_hist)
+{
+    Smem<T> s;
+    s.h = base;
+    T *t = reinterpret_cast<T *>(base + (with_hist ? acc_bytes_padded<T>(m) : 0));
+    s.c = t;
+    s.prior = s.c + m.n_ap_total * m.rec_len;
+    s.edges = s.prior + m.ncell;
+    s.vp = s.edges + m.n_edges_total;
+    s.isp = s.vp + m.n_ap_total;
+    s.e2 = reinterpret_cast<float *>(s.isp + m.n_ap_total);
+    s.lut = reinterpret_cast<unsigned short *>(s.e2 + m.n_edges_total);
+    return s;
+}
+
+template <class T>
+__device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, const Smem<T> &s)
+{
+    for (int k = threadIdx.x; k < m.n_edges_total; k += blockDim.x) {
+        s.edges[k] = T(b.edges[k]);
+        s.e2[k] = float(b.edges[k] * b.edges[k]);
+    }
     for (int k = threadIdx.x; k < m.n_ap_total; k += blockDim.x) {
-        vp_s[k] = T(b.Vp[k]);
-        isp_s[k] = T(b.isp[k]);
+        s.vp[k] = T(b.Vp[k]);
+        s.isp[k] = T(b.isp[k]);
     }
+    for (int k = threadIdx.x; k < m.n_lut; k += blockDim.x) s.lut[k] = b.lut[k];
 }
 
-// Shared-memory layout of the step kernel (bytes).
-template <class T>
-__host__ __device__ inline size_t step_smem_bytes(const Model &m)
+// ---------------------------------------------------------------- force-of-change records
+
+// Folds the coefficients c_j of every aperture into its record (see data_term): with
+// v_los = V + s nu (s = sigma_p), mass contributes c to q0, v_los^2 contributes
+// c (V^2, 2 V s, s^2) and v_los contributes c (V, s) to (q0, q1, q2); b_n contributes
+// c c_n H_n(nu) to the Hermite part, with the monomial coefficients of H_n from the
+// recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}. Called by every thread of one block.
+// Coefficient of nu^q in the physicists' H_n, set on the host from the recurrence
+// H_{n+1} = 2 nu H_n - 2 n H_{n-1} (see herm_table).
+__constant__ double kHerm[7][7];
+
+inline void herm_table(double h[7][7])
 {
-    return sizeof(long long) * size_t(m.hist_words) +
-           sizeof(T) * size_t(m.J + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
+    for (int n = 0; n < 7; ++n)
+        for (int q = 0; q < 7; ++q) h[n][q] = 0.0;
+    h[0][0] = 1.0;
+    h[1][1] = 2.0;
+    for (int n = 1; n < 6; ++n)
+        for (int q = 0; q < 7; ++q) h[n + 1][q] = (q > 0 ? 2.0 * h[n][q - 1] : 0.0) - 2.0 * n * h[n - 1][q];
 }
 
-// ---------------------------------------------------------------- step kernel
-//
-// One M2M step over all particles, one read and one write of the particle
-// state: (a) the previous step's force of change at the current position,
-// (b) kick-drift-kick push, (c) deposit of w K_j into block-local fixed-point
-// sums, (d) on prior-update steps the (E, x) cell of every particle and the
-// per-cell weight sums and counts. Block sums are added to the global sums
-// with integer atomics, so the result does not depend on the order.
-template <class T, int WPS>
-__global__ void __launch_bounds__(256) k_step(const Model m, const State<T> P, const Buffers b,
-                                              int push, int init)
+__device__ void build_records(const Model &m, const Buffers &b)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    long long *h = reinterpret_cast<long long *>(smem);
-    T *c_s = reinterpret_cast<T *>(h + m.hist_words);
-    T *pri_s = c_s + m.J;
-    T *edges_s = pri_s + m.ncell;
-    T *vp_s = edges_s + m.n_edges_total;
-    T *isp_s = vp_s + m.n_ap_total;
-
-    const Scalars sc = *b.sc;
-    const long long t = sc.t + 1;
-    const int pending = init ? 0 : sc.pending;
-    const int prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
-    const T wscale = init ? T(1) : T(sc.wscale);
-    const T what_flat = T(sc.what_flat);
-
-    for (int k = threadIdx.x; k < m.hist_words; k += blockDim.x) h[k] = 0;
-    if (pending) {
-        for (int k = threadIdx.x; k < m.J; k += blockDim.x) c_s[k] = T(b.c[k]);
-        if (m.mode == 1)
-            for (int k = threadIdx.x; k < m.ncell; k += blockDim.x) pri_s[k] = T(b.prior[k]);
-    }
-    load_tables(m, b, edges_s, vp_s, isp_s);
-    __syncthreads();
-
-    unsigned err = 0;
-    double wdep = 0.0;  // weight deposited by this thread, for the fixed-point range check
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-        T x = P.x[i], y = P.y[i], z = P.z[i];
-        T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
-        T w = P.w[i] * wscale;
-        if (pending) {
-            const T pr = (m.mode == 1) ? pri_s[P.cell[i]] : what_flat;
-            w = foc_update(m, edges_s, vp_s, isp_s, c_s, pr, w, x, y, z, vy, vz, err);
+    for (int g = 0; g < m.n_groups; ++g) {
+        const GroupDesc &G = m.g[g];
+        for (int p = threadIdx.x; p < G.n_ap; p += blockDim.x) {
+            const int a = G.ap_off + p;
+            double *r = b.rec + a * m.rec_len;
+            const bool gh = G.max_gh >= 0;
+            const double V = gh ? b.Vp[a] : 0.0, is = gh ? b.isp[a] : 1.0, s = 1.0 / is;
+            const int base = G.obs_off + p;
+            double q0 = 0.0, q1 = 0.0, q2 = 0.0;
+            if (G.k_mass >= 0) q0 += b.c[base + G.k_mass * G.n_ap];
+            if (G.k_v2 >= 0) {
+                const double c = b.c[base + G.k_v2 * G.n_ap];
+                q0 += c * V * V;
+                q1 += c * 2.0 * V * s;
+                q2 += c * s * s;
+            }
+            if (G.k_v1 >= 0) {
+                const double c = b.c[base + G.k_v1 * G.n_ap];
+                q0 += c * V;
+                q1 += c * s;
+            }
+            r[0] = V;
+            r[1] = is;
+            r[2] = q0;
+            r[3] = q1;
+            r[4] = q2;
+            double pc[7] = {0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+            for (int n = 0; n < 7; ++n) {
+                if (n <= G.max_gh && G.k_gh[n] >= 0) {
+                    const double c = b.c[base + G.k_gh[n] * G.n_ap] * gh_c(n);
+#pragma unroll
+                    for (int q = 0; q <= n; ++q) pc[q] += c * kHerm[n][q];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+                if (5 + q < m.rec_len) r[5 + q] = pc[q];
         }
-        if (push) leapfrog(m, x, y, z, vx, vy, vz);
-        T Y, vlos;
-        project(m, y, z, vy, vz, Y, vlos);
-        if (w != T(0)) {
-            for_each_kernel(m, edges_s, vp_s, isp_s, x, Y, vlos, [&](int j, int kind, T K) {
-                double sc_ = kind == kKindMass ? m.fx_w : (kind == kKindV2 ? m.fx_v2 : m.fx_gh);
-                if (kind == kKindV2 && K > T(m.v2max)) err |= kErrOverflow;
-                if (kind == kKindV1) sc_ = m.fx_v2;
-                deposit<T, WPS>(h, j, w * K, sc_);
-            });
-            deposit<T, WPS>(h, m.J, w, m.fx_w);
-            wdep += double(w);
-        }
-        if (prior_step) {
-            const int c = prior_cell(m, b.lcE, x, y, z, vx, vy, vz);
-            if (w != T(0)) deposit<T, WPS>(h, m.J + 1 + c, w, m.fx_w);
-            atomicAdd(reinterpret_cast<unsigned long long *>(h + m.off_count + c), 1ull);
-            P.cell[i] = static_cast<uint16_t>(c);
-        }
-        P.x[i] = x;
-        P.y[i] = y;
-        P.z[i] = z;
-        P.vx[i] = vx;
-        P.vy[i] = vy;
-        P.vz[i] = vz;
-        P.w[i] = w;
-    }
-    if (err) atomicOr(&b.sc->err, err);
-    // the check sum only guards the fixed-point range, so its summation order does not matter
-    for (int o = 16; o > 0; o >>= 1) wdep += __shfl_xor_sync(0xffffffffu, wdep, o);
-    if ((threadIdx.x & 31) == 0 && wdep != 0.0) atomicAdd(&b.sc->Wcheck, wdep);
-    __syncthreads();
-    const int words = prior_step ? m.hist_words : m.off_grid;
-    for (int k = threadIdx.x; k < words; k += blockDim.x) {
-        const long long v = h[k];
-        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + k), static_cast<unsigned long long>(v));
     }
 }
 
-// ---------------------------------------------------------------- finalize kernel
+// ---------------------------------------------------------------- finalize (last block)
 //
-// One block: converts the fixed-point sums, renormalises, smooths (eq. myts),
-// forms Delta_j, chi^2 (eqs. delta, chi) and the force-of-change coefficients,
-// the prior means on update steps, and clears the sums for the next step.
+// Run by the last block of the step kernel once every block has added its sums:
+// converts the fixed-point sums, renormalises, smooths (eq. myts), forms Delta_j,
+// chi^2 (eqs. delta, chi) and the force-of-change coefficients, the prior means on
+// update steps, and clears the sums for the next step. red: blockDim doubles.
 template <int WPS>
-__global__ void __launch_bounds__(1024) k_finalize(const Model m, const Buffers b, long long n, int init)
+__device__ void finalize_block(const Model &m, const Buffers &b, long long n, int init, int prior_step,
+                               double *red)
 {
-    __shared__ double red[1024];
-    __shared__ double s_ren_s;
-    __shared__ int prior_step_s;
+    // other blocks updated the sums and scalars with atomics: read them from L2
     Scalars &sc = *b.sc;
-    const long long t = init ? 0 : sc.t + 1;
-    if (threadIdx.x == 0) {
-        const double U = fx_read<WPS>(b.hist, m.J) / m.fx_w;
-        double s_ren = 1.0;
-        if (init) {
+    const long long t = init ? 0 : __ldcg(&sc.t) + 1;
+    const double U = fx_read<WPS>(b.hist, m.J) / m.fx_w;
+    double s_ren = 1.0;
+    if (init) {
+        if (threadIdx.x == 0) {
             sc.W0 = U;
             sc.what_flat = n > 0 ? U / double(n) : 0.0;
-        } else if (m.renormalize && U > 0.0) {
-            s_ren = sc.W0 / U;
         }
-        // the integer sums wrap beyond the range: the floating-point check sum catches it
-        if (!(sc.Wcheck <= 0.5 * sc.Wrange)) atomicOr(&sc.err, kErrOverflow);
-        sc.Wcheck = 0.0;
-        sc.Wsum = U;
-        s_ren_s = s_ren;
-        prior_step_s = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
+    } else if (m.renormalize && U > 0.0) {
+        s_ren = __ldcg(&sc.W0) / U;
     }
-    __syncthreads();
-    const double s_ren = s_ren_s;
     double part = 0.0;
     for (int j = threadIdx.x; j < m.J; j += blockDim.x) {
         const double raw = fx_read<WPS>(b.hist, j) * b.obs_iscale[j] * s_ren * b.obs_post[j];
@@ -612,66 +915,184 @@ __global__ void __launch_bounds__(1024) k_finalize(const Model m, const Buffers 
     }
     red[threadIdx.x] = part;
     __syncthreads();
+    build_records(m, b);
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (prior_step_s) {
+    if (prior_step) {
         for (int c = threadIdx.x; c < m.ncell; c += blockDim.x) {
-            const long long cnt = b.hist[m.off_count + c];
+            const long long cnt = __ldcg(b.hist + m.off_count + c);
             const double sum = fx_read<WPS>(b.hist, m.J + 1 + c) / m.fx_w * s_ren;
-            b.prior[c] = cnt > 0 ? sum / double(cnt) : 0.0;
+            b.prior[c] = cnt > 0 ? sum / double(cnt) : 0.0;  // mean weight of the cell
             b.prior_count[c] = cnt;
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < m.hist_words; k += blockDim.x) b.hist[k] = 0;
+    const int words = prior_step ? m.hist_words : m.off_grid;
+    for (int k = threadIdx.x; k < words; k += blockDim.x) b.hist[k] = 0;
     if (threadIdx.x == 0) {
+        // the integer sums wrap beyond their range: the floating-point check sum catches it
+        if (!(__ldcg(&sc.Wcheck) <= 0.5 * __ldcg(&sc.Wrange))) atomicOr(&sc.err, kErrOverflow);
+        sc.Wcheck = 0.0;
+        sc.Wsum = U;
         sc.chi2 = red[0];
         if (!init) sc.t = t;
         sc.wscale = s_ren;
         sc.pending = init ? 0 : (t > m.n_relax ? 1 : 0);
+        sc.blocks_done = 0;
+    }
+}
+
+// ---------------------------------------------------------------- step kernel
+//
+// One M2M step over all particles, one read and one write of the particle state:
+// (a) the previous step's force of change at the current position, (b) the
+// kick-drift-kick push, (c) the deposit of w K_j into block-shared fixed-point
+// sums, (d) on prior-update steps the (E, x) cell of every particle with per-cell
+// weight sums and counts. Blocks add their sums to the global sums with integer
+// atomics (exact, so order-independent); the last block to finish runs the
+// finalize. Nothing waits on another block.
+template <class T, int WPS, int MINB, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+__global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
+                                                    const Buffers b, int push, int init)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Smem<T> S = carve<T>(m, smem, 1);
+    __shared__ bool am_last;
+
+    const Scalars sc = *b.sc;
+    const long long t = sc.t + 1;
+    const int pending = init ? 0 : sc.pending;
+    const int prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
+    const T wscale = init ? T(1) : T(sc.wscale);
+    const T what_flat = T(sc.what_flat);
+
+    {
+        int *z = static_cast<int *>(S.h);
+        const int nw = int(Acc<T>::bytes(m) / sizeof(int));
+        for (int q = threadIdx.x; q < nw; q += blockDim.x) z[q] = 0;
+    }
+    if (pending) {
+        for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
+        if (m.mode == 1)
+            for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.prior[q] = T(b.prior[q]);
+    }
+    load_tables(m, b, S);
+    __syncthreads();
+    const Tables<T> tb{S.edges, S.e2, S.lut, S.vp, S.isp};
+
+    unsigned err = 0;
+    Total<T> wtot;
+    T wdep = T(0);  // floating-point twin of wtot, for the fixed-point range check
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+        T x = P.x[i], y = P.y[i], z = P.z[i];
+        T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
+        T w = P.w[i] * wscale;
+        if (pending) {
+            const T pr = m.mode == 1 ? S.prior[P.cell[i]] : what_flat;
+            w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
+        }
+        if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
+        if (w != T(0)) {
+            T Y, vlos;
+            project(k, y, z, vy, vz, Y, vlos);
+            each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
+                constexpr unsigned M = decltype(Pl)::mask;
+                const GroupDesc &G = m.g[g];
+                const int p = aperture<M>(G, tb.edges, tb.e2, tb.lut, x, Y);
+                if (p >= 0) {
+                    // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
+                    if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
+                    group_kernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
+                        Acc<T>::add(S.h, m, j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
+                    });
+                }
+            });
+            wtot.add(w, k.fx_w);
+            wdep += w;
+        }
+        if (prior_step) {
+            const int c = prior_cell(m, k, b.lcE, x, y, z, vx, vy, vz);
+            Acc<T>::add(S.h, m, m.J + 1 + c, w, k.fx_w);
+            Acc<T>::count(S.h, m, c);
+            P.cell[i] = static_cast<uint16_t>(c);
+        }
+        P.x[i] = x; P.y[i] = y; P.z[i] = z;
+        P.vx[i] = vx; P.vy[i] = vy; P.vz[i] = vz;
+        P.w[i] = w;
+    }
+    if (err) atomicOr(&b.sc->err, err);
+    // the total weight went into registers: one global atomic per warp and word
+#pragma unroll
+    for (int q = 0; q < WPS; ++q) {
+        long long v = wtot.word(q, k.fx_w);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v != 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + WPS * m.J + q), static_cast<unsigned long long>(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) wdep += __shfl_xor_sync(0xffffffffu, wdep, o);
+    if ((threadIdx.x & 31) == 0 && wdep != T(0)) atomicAdd(&b.sc->Wcheck, double(wdep));
+    __syncthreads();
+    const int words = prior_step ? m.hist_words : m.off_grid;
+    for (int q = threadIdx.x; q < words; q += blockDim.x) {
+        if (q >= WPS * m.J && q < WPS * (m.J + 1)) continue;  // the total is already global
+        const long long v = Acc<T>::word(S.h, m, q);
+        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + q), static_cast<unsigned long long>(v));
+    }
+    // last block to finish runs the finalize
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (am_last) {
+        __threadfence();
+        finalize_block<WPS>(m, b, P.n, init, prior_step, reinterpret_cast<double *>(smem));
     }
 }
 
 // ---------------------------------------------------------------- helpers
 
 // Weights as of the end of the last step: the pending force of change applied
-// (without renormalisation) into out[], and the total added to acc (one sum).
-template <class T, int WPS>
-__global__ void k_materialize(const Model m, const State<T> P, const Buffers b, double *out,
+// (without renormalisation) into out[], and the total added to acc (two words).
+template <class T>
+__global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, const Buffers b, double *out,
                               long long *acc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *c_s = reinterpret_cast<T *>(smem);
-    T *pri_s = c_s + m.J;
-    T *edges_s = pri_s + m.ncell;
-    T *vp_s = edges_s + m.n_edges_total;
-    T *isp_s = vp_s + m.n_ap_total;
+    const Smem<T> S = carve<T>(m, smem, 0);
     const Scalars sc = *b.sc;
-    for (int k = threadIdx.x; k < m.J; k += blockDim.x) c_s[k] = T(b.c[k]);
+    for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
     if (m.mode == 1)
-        for (int k = threadIdx.x; k < m.ncell; k += blockDim.x) pri_s[k] = T(b.prior[k]);
-    load_tables(m, b, edges_s, vp_s, isp_s);
+        for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.prior[q] = T(b.prior[q]);
+    load_tables(m, b, S);
     __syncthreads();
+    const Tables<T> tb{S.edges, S.e2, S.lut, S.vp, S.isp};
     unsigned err = 0;
+    Total<double> tot;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
         T w = P.w[i] * T(sc.wscale);
         if (sc.pending) {
-            const T pr = (m.mode == 1) ? pri_s[P.cell[i]] : T(sc.what_flat);
-            w = foc_update(m, edges_s, vp_s, isp_s, c_s, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i],
-                           P.vz[i], err);
-            if (w != T(0)) fx_add<2>(acc, 0, double(w), m.fx_w);
+            const T pr = (m.mode == 1) ? S.prior[P.cell[i]] : T(sc.what_flat);
+            w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i], P.vz[i], err);
+            if (w != T(0)) tot.add(double(w), m.fx_w);
         }
         out[i] = double(w);
     }
     if (err) atomicOr(&b.sc->err, err);
+    for (int q = 0; q < 2; ++q) {
+        long long s = tot.word(q, m.fx_w);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s != 0)
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc + q), static_cast<unsigned long long>(s));
+    }
 }
 
 __global__ void k_scale(double *out, long long n, const long long *acc, const Model m, const Scalars *sc)
 {
-    const double U = fx_read<2>(acc, 0) / m.fx_w;
+    const double U = (double(acc[0]) + double(acc[1]) * (1.0 / 4294967296.0)) / m.fx_w;
     if (!sc->pending || !m.renormalize || !(U > 0.0)) return;
     const double s = sc->W0 / U;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -692,18 +1113,26 @@ __global__ void k_convert_out(const T *src, double *dst, long long n)
         dst[i] = double(src[i]);
 }
 
-// Largest v^2 a particle can reach in the fixed potential (2 (E - phi_min)),
-// and the total weight and smallest weight, for the fixed-point ranges.
-__global__ void k_load_stats(const Model m, const double *x, const double *y, const double *z,
-                             const double *vx, const double *vy, const double *vz, const double *w,
-                             long long n, unsigned long long *v2max_bits, unsigned *bad)
+// Largest v^2 a particle can reach in the fixed potential (2 (E - phi_min)), and a
+// flag for non-finite input or negative weights.
+__global__ void k_load_stats(const Model m, const Cst<double> k, const double *x, const double *y,
+                             const double *z, const double *vx, const double *vy, const double *vz,
+                             const double *w, long long n, unsigned long long *v2max_bits, unsigned *bad)
 {
+    double best = 0.0;
+    unsigned flag = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
-        const double e = v2 + 2.0 * (potential<double>(m, x[i], y[i], z[i]) - m.phi_min);
+        const double e = v2 + 2.0 * (potential<double>(m, k, x[i], y[i], z[i]) - m.phi_min);
         const double val = e > v2 ? e : v2;
-        if (!isfinite(val) || !isfinite(x[i] + y[i] + z[i]) || !isfinite(w[i]) || w[i] < 0.0) atomicOr(bad, 1u);
-        else atomicMax(v2max_bits, static_cast<unsigned long long>(__double_as_longlong(val)));
+        if (!isfinite(val) || !isfinite(x[i] + y[i] + z[i]) || !isfinite(w[i]) || w[i] < 0.0) flag = 1;
+        else if (val > best) best = val;
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    flag = __reduce_or_sync(0xffffffffu, flag);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(v2max_bits, static_cast<unsigned long long>(__double_as_longlong(best)));
+        if (flag) atomicOr(bad, 1u);
     }
 }
 
