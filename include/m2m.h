@@ -227,6 +227,30 @@ m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double
                              const double *noise, double *Y, double *sigY, double *Vp,
                              double *sp, int32_t *iterations);
 
+/* Observables without device allocation. The paper has no counterpart: this call
+ * exists for callers that cannot call cudaMalloc, for example code running inside
+ * another runtime's memory pool, under a policy that forbids allocation after
+ * start-up, or next to a framework whose allocator owns the device. It computes
+ * the raw observables y_j = sum_i w_i K_j(z_i) of n particles given as device FP64
+ * arrays (pos, vel: 3n values each, x then y then z; w: n values) for the
+ * observable set obs (obs->Y and obs->sigY are ignored), and writes the J values to
+ * the device array y_dev, on `stream` (a cudaStream_t, NULL for the default
+ * stream). Results agree with m2m_load_particles_device followed by the raw
+ * observables of m2m_get_observables to FP64 rounding.
+ *
+ * It allocates nothing: all scratch lives in one static device array of about
+ * 320 KiB that every GPU loading this library holds until the process exits. The
+ * array limits J to 8192 observables, the apertures to 8192 and the annulus edges
+ * to 8192 in total; larger sets are rejected with M2M_ERR_ARG. The first call on a
+ * device looks up the array's device address, so make that first call before any
+ * stream capture. Every call reuses the array (its sums are cleared at the start
+ * of each call), so calls that overlap on the GPU, on any streams, race: issue
+ * them one after another. The call synchronises `stream` before returning.
+ * Errors go to m2m_last_error(NULL): M2M_ERR_ARG for invalid input, M2M_ERR_CUDA,
+ * M2M_ERR_OVERFLOW if a deposit left the fixed-point range. */
+m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, const double *pos_dev,
+                              const double *vel_dev, const double *w_dev, double *y_dev, void *stream);
+
 /* One-line description of the last error on this context ("" if none); valid
  * until the next call on the context. ctx may be NULL for creation errors. */
 const char *m2m_last_error(const m2m_ctx *ctx);

@@ -106,6 +106,8 @@ def lib():
         L.m2m_load_state.argtypes = [vp, C.c_char_p]
         L.m2m_build_targets.argtypes = [C.POINTER(Observables), C.c_int64, _DP, _DP, _DP, _DP, _DP,
                                         _DP, _DP, _DP, _DP, C.POINTER(C.c_int32)]
+        L.m2m_observe_static.argtypes = [C.POINTER(Observables), C.c_int64, vp, vp, vp, vp, vp]
+        L.m2m_observe_static.restype = C.c_int
         L.m2m_last_error.restype = C.c_char_p
         L.m2m_last_error.argtypes = [vp]
         L.m2m_destroy.argtypes = [vp]
@@ -197,6 +199,15 @@ def build_targets(groups, incl_deg, particles: dict, err, noise=None):
     _check(lib().m2m_build_targets(C.byref(d.o), n, _dp(pos), _dp(vel), _dp(w), _dp(err), _dp(nz), _dp(Y),
                                    _dp(sig), _dp(Vp), _dp(sp), C.byref(it)))
     return Y, sig, Vp, sp, it.value
+
+
+def observe_static(groups, incl_deg, n: int, pos_ptr: int, vel_ptr: int, w_ptr: int, y_ptr: int,
+                   Vp=None, sp=None, stream=None):
+    """Raw observables of device particles into device memory, without allocation
+    (m2m_observe_static)."""
+    d = ObsDesc(groups, incl_deg, Vp=Vp, sp=sp)
+    _check(lib().m2m_observe_static(C.byref(d.o), n, pos_ptr, vel_ptr, w_ptr, y_ptr, stream))
+    return d.J
 
 
 class Fit:

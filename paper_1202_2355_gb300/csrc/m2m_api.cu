@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1275,4 +1276,294 @@ extern "C" void m2m_destroy(m2m_ctx *ctx)
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+}
+
+// ------------------------------------------------------------------ observables without allocation
+//
+// m2m_observe_static serves callers that cannot allocate device memory: code
+// running where cudaMalloc is unavailable or forbidden (inside a memory pool
+// owned by another runtime, between captures that must not allocate, in
+// processes whose allocator is reserved by a host framework). It computes the
+// raw observables y_j = sum_i w_i K_j(z_i) of caller-provided device particles in
+// FP64 with the same device code as a context's deposit, and keeps all its
+// scratch (the fixed-point sums, the aperture tables, a few counters) in one
+// file-scope device array of kStaticScratchBytes. Every GPU that loads this
+// library holds that array until the process exits.
+
+namespace {
+constexpr int kStaticMaxObs = 8192;        // J
+constexpr int kStaticMaxApertures = 8192;  // sum of n_ap over the groups
+constexpr int kStaticMaxEdges = 8192;      // sum of n_ap + 1 over the annulus groups
+constexpr size_t kOffHist = 0;             // 2 J int64 words
+constexpr size_t kOffEdges = kOffHist + sizeof(long long) * 2 * kStaticMaxObs;
+constexpr size_t kOffVp = kOffEdges + sizeof(double) * kStaticMaxEdges;
+constexpr size_t kOffIsp = kOffVp + sizeof(double) * kStaticMaxApertures;
+constexpr size_t kOffStats = kOffIsp + sizeof(double) * kStaticMaxApertures;
+// stats: sum of weights (double), max v^2 (bits), input flag, error word, blocks done
+constexpr size_t kStaticScratchBytes = kOffStats + 64;
+
+struct StaticStats {
+    double wsum;
+    unsigned long long v2bits;
+    unsigned bad, err, done;
+};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_m2m_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void *g_static_addr[256];
+
+// Device address of the scratch array for the current device. The first call on a
+// device asks the runtime for it (cudaGetSymbolAddress), so that call should not
+// happen inside a stream capture.
+static m2m_status static_scratch(unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 256) return fail(nullptr, M2M_ERR_ARG, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_m2m_scratch);
+        if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_static_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_static_addr[dev]);
+    return M2M_OK;
+}
+
+// Sum of weights, largest |v|^2, finiteness of the input, and 1/sigma_p in place.
+__global__ void k_static_stats(const double *x, const double *y, const double *z, const double *vx,
+                               const double *vy, const double *vz, const double *w, long long n, double *isp,
+                               int nap, StaticStats *st)
+{
+    if (blockIdx.x == 0)
+        for (int a = threadIdx.x; a < nap; a += blockDim.x) isp[a] = 1.0 / isp[a];
+    double s = 0.0, best = 0.0;
+    unsigned flag = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
+        if (!isfinite(v2) || !isfinite(x[i] + y[i] + z[i]) || !isfinite(w[i]) || w[i] < 0.0) {
+            flag = 1;
+        } else {
+            s += w[i];
+            best = fmax(best, v2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    }
+    flag = __reduce_or_sync(0xffffffffu, flag);
+    if ((threadIdx.x & 31) == 0) {
+        if (s != 0.0) atomicAdd(&st->wsum, s);
+        atomicMax(&st->v2bits, static_cast<unsigned long long>(__double_as_longlong(best)));
+        if (flag) atomicOr(&st->bad, 1u);
+    }
+}
+
+// The deposit of the step kernel (FP64, generic shape), without push or force of
+// change, into block sums flushed to the scratch sums; the last block writes y.
+__global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst<double> k, const double *x,
+                                                        const double *y, const double *z, const double *vy,
+                                                        const double *vz, const double *w, long long n,
+                                                        const double *edges, const double *vp, const double *isp,
+                                                        long long *hist, StaticStats *st, double *out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    long long *h = reinterpret_cast<long long *>(smem);
+    __shared__ bool am_last;
+    for (int q = threadIdx.x; q < 2 * m.J; q += blockDim.x) h[q] = 0;
+    __syncthreads();
+    const Tables<double> tb{edges, nullptr, nullptr, vp, isp};
+    unsigned err = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+        if (wi == 0.0) continue;
+        double Y, vlos;
+        project(k, y[i], z[i], vy[i], vz[i], Y, vlos);
+        each_group<0, kDyn, kDyn, kDyn, kDyn>(m, [&](auto, int g) {
+            const GroupDesc &G = m.g[g];
+            const int p = aperture<kDyn>(G, tb.edges, nullptr, nullptr, x[i], Y);
+            if (p >= 0) {
+                if (G.has_v2 && vlos * vlos > k.v2max) err |= kErrOverflow;
+                group_kernels<kDyn>(G, tb, p, vlos, wi, [&](int j, double v, int cls) {
+                    Acc<double>::add(h, m, j, v, cls == kClassMass ? m.fx_w : (cls == kClassVel ? m.fx_v2 : m.fx_gh));
+                });
+            }
+        });
+    }
+    if (err) atomicOr(&st->err, err);
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * m.J; q += blockDim.x)
+        if (h[q] != 0) atomicAdd(reinterpret_cast<unsigned long long *>(hist + q), static_cast<unsigned long long>(h[q]));
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = atomicAdd(&st->done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < m.J; j += blockDim.x) {
+        int g = 0;
+        while (g + 1 < m.n_groups && j >= m.g[g + 1].obs_off) ++g;
+        const GroupDesc &G = m.g[g];
+        const int q = (j - G.obs_off) / G.n_ap, p = (j - G.obs_off) % G.n_ap;
+        const int kind = G.kinds[q];
+        const double scale = kind == kKindMass ? m.fx_w : (kind == kKindV2 ? m.fx_v2 : m.fx_gh);
+        double post = 1.0;
+        if (kind == kKindMass) {
+            double area;
+            if (G.geometry == 0) {
+                const double e0 = edges[G.edge_off + p], e1 = edges[G.edge_off + p + 1];
+                area = __dmul_rn(3.14159265358979323846, __dsub_rn(__dmul_rn(e1, e1), __dmul_rn(e0, e0)));
+            } else {
+                area = __dmul_rn(__ddiv_rn(G.xw, double(G.nx)), __ddiv_rn(G.yw, double(G.ny)));
+            }
+            post = 1.0 / area;
+        }
+        out[j] = fx_read<2>(hist, j) * (1.0 / scale) * post;
+    }
+}
+
+extern "C" m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, const double *pos_dev,
+                                         const double *vel_dev, const double *w_dev, double *y_dev, void *stream)
+{
+    // errors are reported through m2m_last_error(NULL)
+    if (!obs || n < 0 || (n > 0 && (!pos_dev || !vel_dev || !w_dev)) || !y_dev)
+        return fail(nullptr, M2M_ERR_ARG, "m2m_observe_static: null argument or n < 0");
+    if (obs->n_groups < 1 || obs->n_groups > kMaxGroups)
+        return fail(nullptr, M2M_ERR_ARG, "n_groups must be 1..%d", kMaxGroups);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *scr = nullptr;
+    m2m_status status = static_scratch(&scr);
+    if (status != M2M_OK) return status;
+    double *d_edges = reinterpret_cast<double *>(scr + kOffEdges);
+    double *d_vp = reinterpret_cast<double *>(scr + kOffVp);
+    double *d_isp = reinterpret_cast<double *>(scr + kOffIsp);
+    long long *d_hist = reinterpret_cast<long long *>(scr + kOffHist);
+    StaticStats *d_st = reinterpret_cast<StaticStats *>(scr + kOffStats);
+
+    // the model of the observable set (the fields the deposit reads), validated as m2m_create does
+    Model m{};
+    const double inc = obs->incl_deg * 3.14159265358979323846 / 180.0;
+    m.sin_i = std::sin(inc);
+    m.cos_i = std::cos(inc);
+    m.n_groups = obs->n_groups;
+    int J = 0, nap = 0, ned = 0;
+    for (int g = 0; g < m.n_groups; ++g) {
+        const m2m_obs_group &S = obs->groups[g];
+        GroupDesc &G = m.g[g];
+        G.geometry = S.geometry;
+        G.n_ap = S.n_ap;
+        G.n_kinds = S.n_kinds;
+        G.obs_off = J;
+        G.ap_off = nap;
+        G.edge_off = ned;
+        G.max_gh = -1;
+        G.k_mass = G.k_v2 = G.k_v1 = -1;
+        for (int q = 0; q < 7; ++q) G.k_gh[q] = -1;
+        if (S.n_ap < 1 || S.n_kinds < 1 || S.n_kinds > kMaxKinds)
+            return fail(nullptr, M2M_ERR_ARG, "group %d: n_ap >= 1 and 1 <= n_kinds <= %d required", g, kMaxKinds);
+        if (S.geometry == M2M_GEOM_ANNULI) {
+            if (!S.edges) return fail(nullptr, M2M_ERR_ARG, "group %d: annuli need edges", g);
+            for (int p = 0; p <= S.n_ap; ++p)
+                if (!std::isfinite(S.edges[p]) || S.edges[p] < 0 || (p > 0 && !(S.edges[p] > S.edges[p - 1])))
+                    return fail(nullptr, M2M_ERR_ARG, "group %d: edges must be finite, >= 0 and increasing", g);
+            ned += S.n_ap + 1;
+        } else if (S.geometry == M2M_GEOM_PIXELS) {
+            if (S.nx < 1 || S.ny < 1 || (long long)S.nx * S.ny != S.n_ap || !(S.xhi > S.xlo) || !(S.yhi > S.ylo))
+                return fail(nullptr, M2M_ERR_ARG, "group %d: pixels need nx*ny == n_ap and a non-empty box", g);
+            G.nx = S.nx; G.ny = S.ny;
+            G.xlo = S.xlo; G.ylo = S.ylo; G.xw = S.xhi - S.xlo; G.yw = S.yhi - S.ylo;
+        } else {
+            return fail(nullptr, M2M_ERR_ARG, "group %d: unknown geometry %d", g, S.geometry);
+        }
+        for (int q = 0; q < S.n_kinds; ++q) {
+            const int kind = S.kinds[q];
+            if (!(kind == kKindMass || kind == kKindV2 || is_gh(kind)))
+                return fail(nullptr, M2M_ERR_ARG, "group %d: unknown observable kind %d", g, kind);
+            for (int q2 = 0; q2 < q; ++q2)
+                if (S.kinds[q2] == kind) return fail(nullptr, M2M_ERR_ARG, "group %d: kind %d listed twice", g, kind);
+            G.kinds[q] = kind;
+            if (kind == kKindMass) G.k_mass = q;
+            if (kind == kKindV2) G.k_v2 = q, G.has_v2 = 1;
+            if (is_gh(kind)) G.k_gh[kind - kKindGH0] = q, G.max_gh = std::max(G.max_gh, kind - kKindGH0);
+        }
+        if (G.max_gh >= 0) {
+            if (!S.Vp || !S.sp) return fail(nullptr, M2M_ERR_ARG, "group %d: GH kinds need Vp and sp", g);
+            for (int p = 0; p < S.n_ap; ++p)
+                if (!std::isfinite(S.Vp[p]) || !(S.sp[p] > 0) || !std::isfinite(S.sp[p]))
+                    return fail(nullptr, M2M_ERR_ARG, "group %d: sp must be finite and > 0", g);
+        }
+        J += S.n_kinds * S.n_ap;
+        nap += S.n_ap;
+    }
+    if (J > kStaticMaxObs || nap > kStaticMaxApertures || ned > kStaticMaxEdges)
+        return fail(nullptr, M2M_ERR_ARG,
+                    "m2m_observe_static holds at most %d observables, %d apertures and %d annulus edges "
+                    "(got %d, %d, %d)", kStaticMaxObs, kStaticMaxApertures, kStaticMaxEdges, J, nap, ned);
+    m.J = J;
+    m.n_ap_total = nap;
+    m.n_edges_total = ned;
+
+#define CS(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+    // tables into the scratch array; the sums and counters must start at zero
+    for (int g = 0; g < m.n_groups; ++g) {
+        const m2m_obs_group &S = obs->groups[g];
+        const GroupDesc &G = m.g[g];
+        if (G.geometry == 0)
+            CS(cudaMemcpyAsync(d_edges + G.edge_off, S.edges, sizeof(double) * (S.n_ap + 1), cudaMemcpyHostToDevice, st));
+        if (G.max_gh >= 0) {
+            CS(cudaMemcpyAsync(d_vp + G.ap_off, S.Vp, sizeof(double) * S.n_ap, cudaMemcpyHostToDevice, st));
+            CS(cudaMemcpyAsync(d_isp + G.ap_off, S.sp, sizeof(double) * S.n_ap, cudaMemcpyHostToDevice, st));
+        } else {
+            CS(cudaMemsetAsync(d_vp + G.ap_off, 0, sizeof(double) * S.n_ap, st));
+            CS(cudaMemsetAsync(d_isp + G.ap_off, 0, sizeof(double) * S.n_ap, st));  // unused for such groups
+        }
+    }
+    CS(cudaMemsetAsync(d_hist, 0, sizeof(long long) * 2 * J, st));
+    CS(cudaMemsetAsync(d_st, 0, sizeof(StaticStats), st));
+    int nsm = 0;
+    int dev = 0;
+    CS(cudaGetDevice(&dev));
+    CS(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const double *px = pos_dev, *py = pos_dev + n, *pz = pos_dev + 2 * n;
+    const double *vx = vel_dev, *vy = vel_dev + n, *vz = vel_dev + 2 * n;
+    k_static_stats<<<nsm * 4, 256, 0, st>>>(px, py, pz, vx, vy, vz, w_dev, n, d_isp, nap, d_st);
+    CS(cudaGetLastError());
+    StaticStats hs{};
+    CS(cudaMemcpyAsync(&hs, d_st, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CS(cudaStreamSynchronize(st));
+    if (hs.bad) return fail(nullptr, M2M_ERR_ARG, "particles must be finite with weights >= 0");
+    // groups without Gauss-Hermite kernels never read 1/sigma_p (zeros became inf above)
+    double v2max;
+    std::memcpy(&v2max, &hs.v2bits, sizeof v2max);
+    const double W = hs.wsum > 0 ? hs.wsum : 1.0;
+    const double Wb = 16777216.0 * W;  // the FP64-mode range of a context
+    const double two62 = 4611686018427387904.0;
+    m.v2max = 2.0 * (v2max > 0 ? v2max : 1.0);
+    m.fx_w = pow2_floor(two62 / Wb);
+    m.fx_v2 = pow2_floor(two62 / (Wb * (m.v2max > 1.0 ? m.v2max : 1.0)));
+    m.fx_gh = pow2_floor(two62 / (Wb * 1.5));
+    const size_t smem = sizeof(long long) * 2 * size_t(J);
+    CS(cudaFuncSetAttribute(k_static_observe, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    int occ = 0;
+    CS(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_static_observe, 256, smem));
+    long long grid = std::min<long long>((n + 255) / 256, (long long)nsm * std::max(occ, 1));
+    if (grid < 1) grid = 1;
+    k_static_observe<<<int(grid), 256, smem, st>>>(m, make_cst<double>(m), px, py, pz, vy, vz, w_dev, n, d_edges, d_vp,
+                                                    d_isp, d_hist, d_st, y_dev);
+    CS(cudaGetLastError());
+    CS(cudaMemcpyAsync(&hs, d_st, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CS(cudaStreamSynchronize(st));
+#undef CS
+    if (hs.err & kErrOverflow) return fail(nullptr, M2M_ERR_OVERFLOW, "a deposit left the fixed-point range");
+    return M2M_OK;
 }
