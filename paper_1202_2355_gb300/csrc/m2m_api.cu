@@ -47,7 +47,7 @@ struct m2m_ctx {
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
     int *d_kind = nullptr;
     double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
-    double *d_rec = nullptr;
+    double *d_rec = nullptr, *d_iprior = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
     Scalars *d_sc = nullptr;
     double *d_wout = nullptr;
@@ -455,6 +455,8 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMalloc(&ctx->d_yraw, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_delta, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_prior, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMalloc(&ctx->d_iprior, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMemset(ctx->d_iprior, 0, sizeof(double) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_prior_count, sizeof(long long) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * m.hist_words));
     CU(cudaMalloc(&ctx->d_acc, sizeof(long long) * 2));
@@ -537,7 +539,7 @@ static Buffers buffers(m2m_ctx *c)
     Buffers b;
     b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
-    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.iprior = c->d_iprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
 }
@@ -649,6 +651,7 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     sc0.Wrange = 9.2233720368547758e18 / m.fx_w;
     CU(cudaMemcpyAsync(ctx->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_iprior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_prior_count, 0, sizeof(long long) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->cell, 0, sizeof(uint16_t) * (ctx->n > 0 ? ctx->n : 1), ctx->stream));
     launch_one(ctx, 0, 1);
@@ -965,7 +968,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.ncell = m.ncell;
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + m.ncell) +
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     char *p = buf.data();
     for (int k = 0; k < 7; ++k) {
@@ -983,6 +986,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     p += sizeof(double) * m.n_ap_total * m.rec_len;
     if (m.ncell) {
         CU(cudaMemcpy(p, ctx->d_prior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(p, ctx->d_iprior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(p, ctx->d_prior_count, 8 * m.ncell, cudaMemcpyDeviceToHost));
         p += 8 * m.ncell;
@@ -1012,7 +1017,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         return fail(ctx, M2M_ERR_ARG, "%s was written for different descriptors", path);
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + m.ncell) +
+    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
@@ -1045,6 +1050,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     p += sizeof(double) * m.n_ap_total * m.rec_len;
     if (m.ncell) {
         CU(cudaMemcpy(ctx->d_prior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
+        p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(ctx->d_iprior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(ctx->d_prior_count, p, 8 * m.ncell, cudaMemcpyHostToDevice));
         p += 8 * m.ncell;
@@ -1271,7 +1278,8 @@ extern "C" void m2m_destroy(m2m_ctx *ctx)
     free_state(ctx);
     free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
-    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_ytil);
+    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_iprior);
+    free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1337,10 +1345,12 @@ static m2m_status static_scratch(unsigned char **out)
 // Sum of weights, largest |v|^2, finiteness of the input, and 1/sigma_p in place.
 __global__ void k_static_stats(const double *x, const double *y, const double *z, const double *vx,
                                const double *vy, const double *vz, const double *w, long long n, double *isp,
-                               int nap, StaticStats *st)
+                               int nap, double *edges, int nedges, StaticStats *st)
 {
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int a = threadIdx.x; a < nap; a += blockDim.x) isp[a] = 1.0 / isp[a];
+        for (int a = threadIdx.x; a < nedges; a += blockDim.x) edges[a] = edges[a] * edges[a];  // squared
+    }
     double s = 0.0, best = 0.0;
     unsigned flag = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1377,7 +1387,7 @@ __global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst
     __shared__ bool am_last;
     for (int q = threadIdx.x; q < 2 * m.J; q += blockDim.x) h[q] = 0;
     __syncthreads();
-    const Tables<double> tb{edges, nullptr, nullptr, vp, isp};
+    const Tables<double> tb{edges, nullptr, vp, isp};  // edges: squared
     unsigned err = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double wi = w[i];
@@ -1386,7 +1396,7 @@ __global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst
         project(k, y[i], z[i], vy[i], vz[i], Y, vlos);
         each_group<0, kDyn, kDyn, kDyn, kDyn>(m, [&](auto, int g) {
             const GroupDesc &G = m.g[g];
-            const int p = aperture<kDyn>(G, tb.edges, nullptr, nullptr, x[i], Y);
+            const int p = aperture<kDyn>(G, tb.esq, nullptr, x[i], Y);
             if (p >= 0) {
                 if (G.has_v2 && vlos * vlos > k.v2max) err |= kErrOverflow;
                 group_kernels<kDyn>(G, tb, p, vlos, wi, [&](int j, double v, int cls) {
@@ -1415,9 +1425,9 @@ __global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst
         double post = 1.0;
         if (kind == kKindMass) {
             double area;
-            if (G.geometry == 0) {
-                const double e0 = edges[G.edge_off + p], e1 = edges[G.edge_off + p + 1];
-                area = __dmul_rn(3.14159265358979323846, __dsub_rn(__dmul_rn(e1, e1), __dmul_rn(e0, e0)));
+            if (G.geometry == 0) {  // edges holds the squared edges
+                const double e0s = edges[G.edge_off + p], e1s = edges[G.edge_off + p + 1];
+                area = __dmul_rn(3.14159265358979323846, __dsub_rn(e1s, e0s));
             } else {
                 area = __dmul_rn(__ddiv_rn(G.xw, double(G.nx)), __ddiv_rn(G.yw, double(G.ny)));
             }
@@ -1536,7 +1546,7 @@ extern "C" m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, 
     CS(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     const double *px = pos_dev, *py = pos_dev + n, *pz = pos_dev + 2 * n;
     const double *vx = vel_dev, *vy = vel_dev + n, *vz = vel_dev + 2 * n;
-    k_static_stats<<<nsm * 4, 256, 0, st>>>(px, py, pz, vx, vy, vz, w_dev, n, d_isp, nap, d_st);
+    k_static_stats<<<nsm * 4, 256, 0, st>>>(px, py, pz, vx, vy, vz, w_dev, n, d_isp, nap, d_edges, ned, d_st);
     CS(cudaGetLastError());
     StaticStats hs{};
     CS(cudaMemcpyAsync(&hs, d_st, sizeof hs, cudaMemcpyDeviceToHost, st));

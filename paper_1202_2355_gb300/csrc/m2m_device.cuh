@@ -195,6 +195,7 @@ struct Buffers {
     double *c;                       // per observable: coefficient of the force of change
     double *rec;                     // per aperture: the data term of eq. modFOC as polynomials in nu
     double *prior;                   // per cell: prior (cell mean weight)
+    double *iprior;                  // per cell: 1/prior (0 when the prior reads as 0)
     long long *prior_count;          // per cell: particle count at the last update
     long long *hist;                 // global fixed-point sums
     double *ytil, *yraw, *delta;
@@ -353,24 +354,42 @@ __device__ __forceinline__ void project(const Cst<T> &k, T y, T z, T vy, T vz, T
     vlos = vy * k.sin_i + vz * k.cos_i;
 }
 
-// Aperture of sky point (X, Y) in group G, or -1. FP64 evaluates the definition:
-// half-open annuli [edge_p, edge_p+1) in R = sqrt(X^2 + Y^2) (binary search), pixel
-// p = py nx + px with px = floor((X - xlo) nx / (xhi - xlo)).
+// Aperture of sky point (X, Y) in group G, or -1: half-open annuli
+// [edge_p, edge_p+1) in R = sqrt(X^2 + Y^2), decided on R^2 against squared edges
+// (so the decision can differ from one made on R only within a few ulp of an
+// edge), or pixel p = py nx + px with px = floor((X - xlo) nx / (xhi - xlo)).
+// Annuli start from a candidate found from log2 R^2 in FP32 (the annulus itself
+// for log-uniform edges, else a lookup table) and are corrected by exact
+// comparisons; without a table (lut_n = 0) a binary search is used.
+//
+// FP64: for R^2 >= 0 the IEEE bit pattern orders like the value, so the
+// comparisons run on the integer pipe.
 template <unsigned M>
-__device__ __forceinline__ int aperture(const GroupDesc &G, const double *edges, const float *,
-                                        const unsigned short *, double X, double Y)
+__device__ __forceinline__ int aperture(const GroupDesc &G, const double *esq, const unsigned short *lut,
+                                        double X, double Y)
 {
     if (!GP<M>::pixels(G)) {
-        const double R = sqrt(X * X + Y * Y);
-        const double *e = edges + G.edge_off;
-        if (!(R >= e[0]) || !(R < e[G.n_ap])) return -1;
-        int lo = 0, hi = G.n_ap;  // e[lo] <= R < e[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (e[mid] <= R) lo = mid;
-            else hi = mid;
+        const double R2 = X * X + Y * Y;
+        const long long r = __double_as_longlong(R2);
+        const double *e = esq + G.edge_off;
+        if (r < __double_as_longlong(e[0]) || r >= __double_as_longlong(e[G.n_ap])) return -1;
+        int p;
+        if (G.lut_n > 0) {
+            int b = __float2int_rd((__log2f(__double2float_rn(R2)) - G.l0) * G.lscale);
+            b = b < 0 ? 0 : (b >= G.lut_n ? G.lut_n - 1 : b);
+            p = G.lut_identity ? b : int(lut[G.lut_off + b]);
+            while (p > 0 && r < __double_as_longlong(e[p])) --p;
+            while (r >= __double_as_longlong(e[p + 1])) ++p;
+        } else {
+            int lo = 0, hi = G.n_ap;  // e[lo] <= R^2 < e[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__double_as_longlong(e[mid]) <= r) lo = mid;
+                else hi = mid;
+            }
+            p = lo;
         }
-        return lo;
+        return p;
     }
     const double fx = floor((X - G.xlo) * G.nx / G.xw);
     const double fy = floor((Y - G.ylo) * G.ny / G.yw);
@@ -378,12 +397,9 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const double *edges,
     return int(fy) * G.nx + int(fx);
 }
 
-// FP32: the squared radius against squared edges, starting from a candidate found
-// from log2 R^2 (the annulus itself for log-uniform edges, else a lookup table) and
-// corrected by exact comparisons.
 template <unsigned M>
-__device__ __forceinline__ int aperture(const GroupDesc &G, const float *, const float *e2s,
-                                        const unsigned short *lut, float X, float Y)
+__device__ __forceinline__ int aperture(const GroupDesc &G, const float *e2s, const unsigned short *lut, float X,
+                                        float Y)
 {
     if (!GP<M>::pixels(G)) {
         const float R2 = X * X + Y * Y;
@@ -420,8 +436,7 @@ enum { kClassMass = 0, kClassVel = 1, kClassGH = 2 };  // fixed-point scale clas
 
 template <class T>
 struct Tables {
-    const T *edges;       // per group edges (FP64 path)
-    const float *e2;      // squared edges (FP32 path)
+    const T *esq;         // per group squared edges
     const unsigned short *lut;
     const T *vp, *isp;
 };
@@ -470,7 +485,7 @@ __device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, cons
     each_group<0, Ms...>(m, [&](auto P, int g) {
         constexpr unsigned M = decltype(P)::mask;
         const GroupDesc &G = m.g[g];
-        const int p = aperture<M>(G, tb.edges, tb.e2, tb.lut, X, Y);
+        const int p = aperture<M>(G, tb.esq, tb.lut, X, Y);
         if (p >= 0) {
             const T *r = rec + (G.ap_off + p) * m.rec_len;
             const T nu = (vlos - r[0]) * r[1];
@@ -588,12 +603,44 @@ __device__ __forceinline__ int prior_cell(const Model &m, const Cst<T> &k, const
 // next 32 fraction bits of v*scale), mixed mode one (round(v*scale)). Integer
 // sums are exact, so the result does not depend on the order of the additions.
 
+// FP64: v*scale = hi + lo 2^-32 with hi = floor and lo in [0, 2^32), computed with
+// integer operations on the IEEE fields (scale is a power of two): the 53-bit
+// significand m and exponent give T = round(v*scale*2^32) = m 2^k, split into its
+// high and low 32-bit parts. |v*scale| < 2^62 keeps k <= 42, so m 2^(k-32) < 2^63.
 __device__ __forceinline__ void fx2(double v, double scale, long long &hi, long long &lo)
 {
-    const double s = v * scale;
-    const double h = floor(s);
-    hi = static_cast<long long>(h);
-    lo = __double2ll_rn((s - h) * 4294967296.0);
+    const long long bits = __double_as_longlong(v);
+    const int e = int((bits >> 52) & 0x7FF);
+    if (e == 0) {  // zero (and subnormals, below any resolution used here)
+        hi = 0;
+        lo = 0;
+        return;
+    }
+    const int se = int((__double_as_longlong(scale) >> 52) & 0x7FF) - 1023;
+    const unsigned long long m = (static_cast<unsigned long long>(bits) & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int k = e - 1075 + se + 32;
+    unsigned long long th, tl;
+    if (k >= 32) {
+        th = m << (k - 32);
+        tl = 0;
+    } else if (k >= 0) {
+        th = m >> (32 - k);
+        tl = (m << k) & 0xFFFFFFFFull;
+    } else if (k > -63) {
+        const unsigned long long r = (m + (1ull << (-k - 1))) >> (-k);
+        th = r >> 32;
+        tl = r & 0xFFFFFFFFull;
+    } else {
+        th = 0;
+        tl = 0;
+    }
+    if (bits < 0) {
+        hi = tl ? -static_cast<long long>(th) - 1 : -static_cast<long long>(th);
+        lo = tl ? 4294967296ll - static_cast<long long>(tl) : 0;
+    } else {
+        hi = static_cast<long long>(th);
+        lo = static_cast<long long>(tl);
+    }
 }
 
 // Mixed mode: round(v*scale) as three signed 32-bit limbs, computed with FP32 and
@@ -738,16 +785,17 @@ __device__ __forceinline__ double fx_read(const long long *h, int slot)
 // F = mu dS/dw - sum_j K_j c_j, c_j = Delta_j/sigma_j (times 1/area for mass),
 // dS/dw = -ln(w/what) (eq. S+) or -ln(w/what) - 1 (eq. entropy).
 template <unsigned... Ms, class T>
-__device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec, T prior,
+__device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec, T iprior,
                                         T w, T x, T y, T z, T vy, T vz, unsigned &err)
 {
     if (w == T(0)) return w;  // w = 0 is a fixed point
     T Y, vlos;
     project(k, y, z, vy, vz, Y, vlos);
     const T data = data_term<Ms...>(m, tb, rec, x, Y, vlos);
-    // A cell mean below the resolution of the fixed-point cell sums reads as 0;
-    // the particle's weight is then unresolved too and the entropy term is dropped.
-    T dS = prior > T(0) ? -d_log(d_div(w, prior)) : T(0);
+    // A cell mean below the resolution of the fixed-point cell sums reads as 0
+    // (iprior = 0); the particle's weight is then unresolved too and the entropy
+    // term is dropped.
+    T dS = iprior > T(0) ? -d_log(w * iprior) : T(0);
     if (m.mode == 0) dS -= T(1);
     const T h = k.dteps * (k.mu * dS - data);
     T wn;
@@ -763,8 +811,7 @@ __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const T
 template <class T>
 struct Smem {
     void *h;               // fixed-point sums of the block (layout of Acc<T>)
-    T *c, *prior, *edges, *vp, *isp;  // c: the force-of-change records
-    float *e2;
+    T *c, *iprior, *esq, *vp, *isp;  // c: the force-of-change records
     unsigned short *lut;
 };
 
@@ -779,7 +826,6 @@ __host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist)
 {
     size_t b = with_hist ? acc_bytes_padded<T>(m) : 0;
     b += sizeof(T) * size_t(m.n_ap_total * m.rec_len + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
-    b += sizeof(float) * size_t(m.n_edges_total);
     b += sizeof(unsigned short) * size_t(m.n_lut) + 16;
     return b;
 }
@@ -791,22 +837,18 @@ __device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, in
     s.h = base;
     T *t = reinterpret_cast<T *>(base + (with_hist ? acc_bytes_padded<T>(m) : 0));
     s.c = t;
-    s.prior = s.c + m.n_ap_total * m.rec_len;
-    s.edges = s.prior + m.ncell;
-    s.vp = s.edges + m.n_edges_total;
+    s.iprior = s.c + m.n_ap_total * m.rec_len;
+    s.esq = s.iprior + m.ncell;
+    s.vp = s.esq + m.n_edges_total;
     s.isp = s.vp + m.n_ap_total;
-    s.e2 = reinterpret_cast<float *>(s.isp + m.n_ap_total);
-    s.lut = reinterpret_cast<unsigned short *>(s.e2 + m.n_edges_total);
+    s.lut = reinterpret_cast<unsigned short *>(s.isp + m.n_ap_total);
     return s;
 }
 
 template <class T>
 __device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, const Smem<T> &s)
 {
-    for (int k = threadIdx.x; k < m.n_edges_total; k += blockDim.x) {
-        s.edges[k] = T(b.edges[k]);
-        s.e2[k] = float(b.edges[k] * b.edges[k]);
-    }
+    for (int k = threadIdx.x; k < m.n_edges_total; k += blockDim.x) s.esq[k] = T(b.edges[k] * b.edges[k]);
     for (int k = threadIdx.x; k < m.n_ap_total; k += blockDim.x) {
         s.vp[k] = T(b.Vp[k]);
         s.isp[k] = T(b.isp[k]);
@@ -924,7 +966,9 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
         for (int c = threadIdx.x; c < m.ncell; c += blockDim.x) {
             const long long cnt = __ldcg(b.hist + m.off_count + c);
             const double sum = fx_read<WPS>(b.hist, m.J + 1 + c) / m.fx_w * s_ren;
-            b.prior[c] = cnt > 0 ? sum / double(cnt) : 0.0;  // mean weight of the cell
+            const double pr = cnt > 0 ? sum / double(cnt) : 0.0;  // mean weight of the cell
+            b.prior[c] = pr;
+            b.iprior[c] = pr > 0.0 ? 1.0 / pr : 0.0;
             b.prior_count[c] = cnt;
         }
     }
@@ -966,7 +1010,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     const int pending = init ? 0 : sc.pending;
     const int prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
     const T wscale = init ? T(1) : T(sc.wscale);
-    const T what_flat = T(sc.what_flat);
+    const T iwhat_flat = sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0);
 
     {
         int *z = static_cast<int *>(S.h);
@@ -976,11 +1020,11 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     if (pending) {
         for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
         if (m.mode == 1)
-            for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.prior[q] = T(b.prior[q]);
+            for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(b.iprior[q]);
     }
     load_tables(m, b, S);
     __syncthreads();
-    const Tables<T> tb{S.edges, S.e2, S.lut, S.vp, S.isp};
+    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp};
 
     unsigned err = 0;
     Total<T> wtot;
@@ -991,7 +1035,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
         T w = P.w[i] * wscale;
         if (pending) {
-            const T pr = m.mode == 1 ? S.prior[P.cell[i]] : what_flat;
+            const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
             w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
         }
         if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
@@ -1001,7 +1045,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
             each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
                 constexpr unsigned M = decltype(Pl)::mask;
                 const GroupDesc &G = m.g[g];
-                const int p = aperture<M>(G, tb.edges, tb.e2, tb.lut, x, Y);
+                const int p = aperture<M>(G, tb.esq, tb.lut, x, Y);
                 if (p >= 0) {
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
                     if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
@@ -1065,17 +1109,17 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
     const Scalars sc = *b.sc;
     for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
     if (m.mode == 1)
-        for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.prior[q] = T(b.prior[q]);
+        for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(b.iprior[q]);
     load_tables(m, b, S);
     __syncthreads();
-    const Tables<T> tb{S.edges, S.e2, S.lut, S.vp, S.isp};
+    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp};
     unsigned err = 0;
     Total<double> tot;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
         T w = P.w[i] * T(sc.wscale);
         if (sc.pending) {
-            const T pr = (m.mode == 1) ? S.prior[P.cell[i]] : T(sc.what_flat);
+            const T pr = (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
             w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i], P.vz[i], err);
             if (w != T(0)) tot.add(double(w), m.fx_w);
         }
