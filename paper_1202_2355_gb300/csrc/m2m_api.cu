@@ -40,7 +40,7 @@ struct m2m_ctx {
     // device buffers
     long long n = 0;
     long long capacity = 0;
-    void *st[7] = {nullptr};
+    void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and in FP64 mode ax, ay, az
     uint16_t *cell = nullptr;
     double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
     unsigned short *d_lut = nullptr;
@@ -550,6 +550,7 @@ static State<T> state(m2m_ctx *c)
     State<T> s;
     s.x = (T *)c->st[0]; s.y = (T *)c->st[1]; s.z = (T *)c->st[2];
     s.vx = (T *)c->st[3]; s.vy = (T *)c->st[4]; s.vz = (T *)c->st[5]; s.w = (T *)c->st[6];
+    s.ax = (T *)c->st[7]; s.ay = (T *)c->st[8]; s.az = (T *)c->st[9];
     s.cell = c->cell;
     s.n = c->n;
     return s;
@@ -598,7 +599,8 @@ static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
     if (n <= ctx->capacity && ctx->st[0]) return M2M_OK;
     free_state(ctx);
     const long long cap = n > 0 ? n : 1;
-    for (auto &p : ctx->st) CU(cudaMalloc(&p, cap * elem_size(ctx)));
+    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    for (int k = 0; k < narr; ++k) CU(cudaMalloc(&ctx->st[k], cap * elem_size(ctx)));
     CU(cudaMalloc(&ctx->cell, cap * sizeof(uint16_t)));
     ctx->capacity = cap;
     return M2M_OK;
@@ -968,10 +970,11 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.ncell = m.ncell;
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
+    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     char *p = buf.data();
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < narr; ++k) {
         if (n) CU(cudaMemcpy(p, ctx->st[k], es * n, cudaMemcpyDeviceToHost));
         p += es * n;
     }
@@ -1017,7 +1020,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         return fail(ctx, M2M_ERR_ARG, "%s was written for different descriptors", path);
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
-    std::vector<char> buf(es * n * 7 + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
+    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
@@ -1035,7 +1039,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     }
     CU(cudaMemcpy(ctx->d_iscale, ctx->obs_iscale.data(), sizeof(double) * m.J, cudaMemcpyHostToDevice));
     const char *p = buf.data();
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < narr; ++k) {
         if (n) CU(cudaMemcpy(ctx->st[k], p, es * n, cudaMemcpyHostToDevice));
         p += es * n;
     }

@@ -180,9 +180,17 @@ struct Scalars {
 template <class T>
 struct State {
     T *x, *y, *z, *vx, *vy, *vz, *w;
+    T *ax, *ay, *az;  // FP64 mode: acceleration at the current positions (null in mixed mode)
     uint16_t *cell;
     long long n;
 };
+
+// FP64 mode keeps a(x_t) from the closing half-kick of one step for the opening
+// half-kick of the next (the same function of the same positions, so bit-identical
+// to recomputing it): 48 more bytes of state traffic instead of one FP64 force
+// evaluation, worth it because that mode is bound by the FP64 pipe, not by HBM.
+template <class T>
+constexpr bool kCacheAccel = sizeof(T) == 8;
 
 struct Buffers {
     const double *edges, *Vp, *isp;  // per group edges, per aperture V_p and 1/sigma_p
@@ -323,6 +331,24 @@ __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, 
     ax = -f * x;
     ay = -f * y;
     az = -f * z;
+}
+
+// One kick-drift-kick leap-frog step from a known acceleration at the start
+// position; returns the acceleration at the end position in (ax, ay, az).
+template <class T>
+__device__ __forceinline__ void leapfrog_from(const Model &m, const Cst<T> &k, T &x, T &y, T &z, T &vx, T &vy, T &vz,
+                                              T &ax, T &ay, T &az)
+{
+    vx += k.hdt * ax;
+    vy += k.hdt * ay;
+    vz += k.hdt * az;
+    x += k.dt * vx;
+    y += k.dt * vy;
+    z += k.dt * vz;
+    accel(m, k, x, y, z, ax, ay, az);
+    vx += k.hdt * ax;
+    vy += k.hdt * ay;
+    vz += k.hdt * az;
 }
 
 // One kick-drift-kick leap-frog step.
@@ -1038,7 +1064,18 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
             const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
             w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
         }
-        if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
+        if constexpr (kCacheAccel<T>) {
+            T ax, ay, az;
+            if (push) {
+                ax = P.ax[i]; ay = P.ay[i]; az = P.az[i];
+                leapfrog_from(m, k, x, y, z, vx, vy, vz, ax, ay, az);
+            } else {
+                accel(m, k, x, y, z, ax, ay, az);
+            }
+            P.ax[i] = ax; P.ay[i] = ay; P.az[i] = az;
+        } else {
+            if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
+        }
         if (w != T(0)) {
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
