@@ -33,13 +33,33 @@ UNIT = "particle-steps/s"
 WORKLOADS = {"c1": 0, "c2": 1, "c3": 2, "c4": 3}
 
 
-def _peaks():
+def _hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 4 FP64 flop per
+# clock per SM (2 DFMA lanes) x 2.07 GHz = 1.2586 TFLOP/s (nominal 1.25). An FMA
+# loop reaches 1.162 TFLOP/s on this part.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+# Per particle-step figures of the step kernel, by precision:
+#   bytes  algorithmic state traffic (read + write);
+#   flops  FP64 flops the FP64 kernel executes (DFMA = 2, DADD/DMUL = 1: ncu
+#          sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over one
+#          step launch / N), including the iterative sqrt, division, log and exp;
+#   dram   dram__bytes_read.sum + dram__bytes_write.sum of one launch / N, from an
+#          ncu capture of the kernel as it stands (None when not captured).
+KERNEL_FIGURES = {
+    # read x, y, z, vx, vy, vz, w, ax, ay, az (80 B) + prior cell (2 B); write 80 B
+    "fp64": {"bytes": 162, "flops": None, "dram": None, "dram_n": None},
+    # read 6 coordinates + w (28 B) + prior cell (2 B); write 28 B
+    "mixed": {"bytes": 58, "flops": None, "dram": 402.6e6 / 8e6, "dram_n": 8_000_000},
+}
 
 
 class ClockSampler:
@@ -99,9 +119,32 @@ def _dist():
     return ws, rank, local
 
 
-def bytes_per_particle_step(precision: str) -> int:
-    # state read (6 coordinates + weight + 2-byte prior cell) and written (6 + weight)
-    return (6 * 8 + 8 + 2 + 7 * 8) if precision == "fp64" else (6 * 4 + 4 + 2 + 7 * 4)
+def roofline(precision: str, n: int, ms_per_launch: float) -> dict:
+    """Roofline of the step kernel (the only kernel of the timed region).
+
+    The FP64 kernel is bound by the FP64 pipe (HBM stays mostly idle); the mixed
+    kernel streams 58 B per particle-step and is compared with HBM."""
+    f = KERNEL_FIGURES[precision]
+    sec = ms_per_launch / 1e3
+    gbs = f["bytes"] * n / sec / 1e9
+    hbm, hbm_src = _hbm_peak()
+    traffic = None if f["dram"] is None else f["dram"] * n
+    common = {"kernel": "k_step", "units_per_launch": n, "unit_of_work": "particle-step",
+              "ms_per_launch": ms_per_launch, "algorithmic_bytes_per_unit": f["bytes"],
+              "traffic_per_unit_measured_at_n": f["dram_n"]}
+    if precision == "fp64":
+        out = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
+               "traffic": traffic, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+               "fp64_flops_per_unit": f["flops"],
+               "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": hbm_src}}
+        if f["flops"] is not None:
+            out["achieved"] = f["flops"] * n / sec / 1e12
+            out["frac"] = out["achieved"] / FP64_PEAK_TFLOPS
+    else:
+        out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+               "traffic": traffic, "peak_source": hbm_src}
+    out.update(common)
+    return out
 
 
 def cpu_baseline(wl_name: str, n_sample: int, steps: int):
@@ -223,25 +266,22 @@ def run_ours(args):
                 flush.fill_(1)
         fit.synchronize()
         torch.cuda.synchronize()
-    step_ms, fin_ms, nt = fit.timing()
+    step_ms, nt = fit.timing()
     fit.set_timing(False)
     assert nt == K
-    total_ms = step_ms + fin_ms
     chi2 = fit.chi2()
     if ws > 1:
-        t = torch.tensor([total_ms, step_ms], dtype=torch.float64, device="cuda")
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, step_ms = float(t[0]), float(t[1])
+        step_ms = float(t[0])
         dist.barrier()
     fit.close()
-    value = ws * n * K / (total_ms / 1e3)
+    value = ws * n * K / (step_ms / 1e3)
 
     # end to end through the public API from pinned host buffers
     e2e_s = None if args.no_e2e else _e2e(B, wl, Y, sig, Vp, sp, stream, n, K, ws)
 
-    peak, peak_src = _peaks()
-    bpp = bytes_per_particle_step(wl.precision)
-    achieved = bpp * n / (step_ms / K / 1e3) / 1e9
+    roof = roofline(wl.precision, n, step_ms / K)
     line = None
     if rank == 0:
         cpu = None
@@ -254,7 +294,7 @@ def run_ours(args):
                              f"{dt:.1f} s single-threaded FP64"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32+i64",
             "data": "synthetic",
             "config": {"workload": wl.name, "n_particles": n, "observables": wl.J,
@@ -262,16 +302,13 @@ def run_ours(args):
                        "dt": wl.params["dt"], "precision": wl.precision,
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "parallelism": f"{ws} independent fit(s), one per GPU", "chi2_per_J_end": chi2 / wl.J},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                         "kernel": "k_step", "bytes_per_particle_step": bpp,
-                         "kernel_ms_per_step": step_ms / K, "finalize_ms_per_step": fin_ms / K},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": None if e2e_s is None else {
                 "value": ws * n * K / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 7 * 8 * n / K, "d2h_bytes_per_step": 8 + 8 * n / K,
                 "note": "load from pinned host memory once, K x (step + chi^2 read), weights read"},
-            "gpu_launches": 2 * K,
+            "gpu_launches": K,  # one step kernel per step (the finalize runs in its last block)
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -195,13 +195,13 @@ m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t);
 /* Number of particles currently loaded (0 before the first load). */
 m2m_status m2m_get_particle_count(m2m_ctx *ctx, int64_t *n);
 
-/* Kernel timing. While on, every step kernel and finalize kernel launch is
- * bracketed by CUDA events recorded on the context stream (graph replay is
- * off), and m2m_get_timing returns their summed device time in milliseconds
- * and the number of steps timed since timing was switched on. */
+/* Kernel timing. While on, every step-kernel launch (one per step: the
+ * finalize runs inside it) is bracketed by CUDA events recorded on the
+ * context stream (graph replay is off), and m2m_get_timing returns their
+ * summed device time in milliseconds and the number of steps timed since
+ * timing was switched on. Either output pointer may be NULL. */
 m2m_status m2m_set_timing(m2m_ctx *ctx, int32_t on);
-m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_kernel_ms, double *finalize_kernel_ms,
-                          int64_t *steps);
+m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_kernel_ms, int64_t *steps);
 
 /* Write / read the full fit state (particles, weights, priors, smoothed
  * observables, step counter, pending update) to / from a file. A context

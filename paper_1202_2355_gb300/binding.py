@@ -101,7 +101,7 @@ def lib():
         L.m2m_get_step_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.m2m_get_particle_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.m2m_set_timing.argtypes = [vp, C.c_int32]
-        L.m2m_get_timing.argtypes = [vp, _DP, _DP, C.POINTER(C.c_int64)]
+        L.m2m_get_timing.argtypes = [vp, _DP, C.POINTER(C.c_int64)]
         L.m2m_save_state.argtypes = [vp, C.c_char_p]
         L.m2m_load_state.argtypes = [vp, C.c_char_p]
         L.m2m_build_targets.argtypes = [C.POINTER(Observables), C.c_int64, _DP, _DP, _DP, _DP, _DP,
@@ -300,9 +300,10 @@ class Fit:
         self._ck(lib().m2m_set_timing(self.h, 1 if on else 0))
 
     def timing(self):
-        a, b, k = C.c_double(), C.c_double(), C.c_int64()
-        self._ck(lib().m2m_get_timing(self.h, C.byref(a), C.byref(b), C.byref(k)))
-        return a.value, b.value, k.value
+        """(summed step-kernel device time in ms, steps timed)."""
+        a, k = C.c_double(), C.c_int64()
+        self._ck(lib().m2m_get_timing(self.h, C.byref(a), C.byref(k)))
+        return a.value, k.value
 
     def save(self, path: str):
         self._ck(lib().m2m_save_state(self.h, path.encode()))

@@ -47,7 +47,7 @@ struct m2m_ctx {
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
     int *d_kind = nullptr;
     double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
-    double *d_rec = nullptr, *d_iprior = nullptr;
+    double *d_rec = nullptr, *d_iprior = nullptr, *d_lprior = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
     Scalars *d_sc = nullptr;
     double *d_wout = nullptr;
@@ -457,6 +457,8 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMalloc(&ctx->d_prior, sizeof(double) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_iprior, sizeof(double) * (m.ncell + 1)));
     CU(cudaMemset(ctx->d_iprior, 0, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMalloc(&ctx->d_lprior, sizeof(double) * (m.ncell + 1)));
+    CU(cudaMemset(ctx->d_lprior, 0, sizeof(double) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_prior_count, sizeof(long long) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * m.hist_words));
     CU(cudaMalloc(&ctx->d_acc, sizeof(long long) * 2));
@@ -515,6 +517,12 @@ static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *o
         cudaError_t e = cudaMemcpyToSymbol(kHerm, h, sizeof h);
         if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "Hermite table: %s", cudaGetErrorString(e));
     }
+    if (s == M2M_OK) {
+        double t[32];
+        exp2_table(t);
+        cudaError_t e = cudaMemcpyToSymbol(kExp2j, t, sizeof t);
+        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "exp table: %s", cudaGetErrorString(e));
+    }
     if (s == M2M_OK) s = upload_tables(ctx);
     if (s != M2M_OK) {
         g_create_error = ctx->err;
@@ -539,7 +547,7 @@ static Buffers buffers(m2m_ctx *c)
     Buffers b;
     b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
-    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.iprior = c->d_iprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.iprior = c->d_iprior; b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
 }
@@ -587,7 +595,6 @@ static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
     step_kernel<T>(c)<<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c),
                                                                               buffers(c), 1, 0);
     cudaEventRecord(ev[1], c->stream);
-    cudaEventRecord(ev[2], c->stream);
 }
 
 // ------------------------------------------------------------------ particles
@@ -654,6 +661,7 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     CU(cudaMemcpyAsync(ctx->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_iprior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_lprior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_prior_count, 0, sizeof(long long) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->cell, 0, sizeof(uint16_t) * (ctx->n > 0 ? ctx->n : 1), ctx->stream));
     launch_one(ctx, 0, 1);
@@ -703,8 +711,9 @@ static m2m_status load_common(m2m_ctx *ctx, int64_t n, const double *pos, const 
     }
     if (n > 0) {
         if (ctx->precision == M2M_PREC_FP64) {
-            for (int k = 0; k < 7; ++k)
+            for (int k = 0; k < 6; ++k)
                 CU(cudaMemcpyAsync(ctx->st[k], stage + k * n, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            k_log_in<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(stage + 6 * n, (double *)ctx->st[6], n);
         } else {
             for (int k = 0; k < 7; ++k)
                 k_convert_in<float><<<ctx->nsm * 4, 256, 0, ctx->stream>>>(stage + k * n, (float *)ctx->st[k], n);
@@ -756,12 +765,12 @@ extern "C" m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps)
     if (nsteps < 0) return fail(ctx, M2M_ERR_ARG, "nsteps must be >= 0");
     if (ctx->timing) {
         for (int64_t k = 0; k < nsteps; ++k) {
-            while (ctx->events.size() < 3 * (ctx->timed + 1)) {
+            while (ctx->events.size() < 2 * (ctx->timed + 1)) {
                 cudaEvent_t e;
                 CU(cudaEventCreate(&e));
                 ctx->events.push_back(e);
             }
-            cudaEvent_t *ev = &ctx->events[3 * ctx->timed];
+            cudaEvent_t *ev = &ctx->events[2 * ctx->timed];
             if (ctx->precision == M2M_PREC_FP64) launch_step_timed<double, 2>(ctx, ev);
             else launch_step_timed<float, 1>(ctx, ev);
             ++ctx->timed;
@@ -923,20 +932,17 @@ extern "C" m2m_status m2m_set_timing(m2m_ctx *ctx, int32_t on)
     return M2M_OK;
 }
 
-extern "C" m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_ms, double *fin_ms, int64_t *steps)
+extern "C" m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_ms, int64_t *steps)
 {
     if (!ctx) return M2M_ERR_ARG;
     CU(cudaStreamSynchronize(ctx->stream));
-    double a = 0.0, b = 0.0;
+    double a = 0.0;
     for (size_t k = 0; k < ctx->timed; ++k) {
-        float t1 = 0.f, t2 = 0.f;
-        CU(cudaEventElapsedTime(&t1, ctx->events[3 * k], ctx->events[3 * k + 1]));
-        CU(cudaEventElapsedTime(&t2, ctx->events[3 * k + 1], ctx->events[3 * k + 2]));
-        a += t1;
-        b += t2;
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, ctx->events[2 * k], ctx->events[2 * k + 1]));
+        a += t;
     }
     if (step_ms) *step_ms = a;
-    if (fin_ms) *fin_ms = b;
     if (steps) *steps = (int64_t)ctx->timed;
     return M2M_OK;
 }
@@ -962,7 +968,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const Model &m = ctx->m;
     CkptHeader hd{};
     std::memcpy(hd.magic, "M2MSTATE", 8);
-    hd.version = 1;
+    hd.version = 2;
     hd.precision = ctx->precision;
     hd.config_hash = ctx->config_hash;
     hd.n = ctx->n;
@@ -971,7 +977,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
-    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
+    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     char *p = buf.data();
     for (int k = 0; k < narr; ++k) {
@@ -992,6 +998,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(p, ctx->d_iprior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
         p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(p, ctx->d_lprior, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
+        p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(p, ctx->d_prior_count, 8 * m.ncell, cudaMemcpyDeviceToHost));
         p += 8 * m.ncell;
     }
@@ -1010,7 +1018,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 1) {
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 2) {
         std::fclose(f);
         return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
     }
@@ -1021,7 +1029,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
-    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 2 * m.ncell) +
+    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) +
                           8 * m.ncell + sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
@@ -1056,6 +1064,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         CU(cudaMemcpy(ctx->d_prior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(ctx->d_iprior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
+        p += sizeof(double) * m.ncell;
+        CU(cudaMemcpy(ctx->d_lprior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(ctx->d_prior_count, p, 8 * m.ncell, cudaMemcpyHostToDevice));
         p += 8 * m.ncell;
@@ -1282,7 +1292,7 @@ extern "C" void m2m_destroy(m2m_ctx *ctx)
     free_state(ctx);
     free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
-    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_iprior);
+    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
     free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
@@ -1327,8 +1337,8 @@ static std::mutex g_static_mu;
 static void *g_static_addr[256];
 
 // Device address of the scratch array for the current device. The first call on a
-// device asks the runtime for it (cudaGetSymbolAddress), so that call should not
-// happen inside a stream capture.
+// device asks the runtime for it (cudaGetSymbolAddress) and sets the exp table, so
+// that call should not happen inside a stream capture.
 static m2m_status static_scratch(unsigned char **out)
 {
     int dev = 0;
@@ -1340,6 +1350,10 @@ static m2m_status static_scratch(unsigned char **out)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_m2m_scratch);
         if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        double t[32];
+        exp2_table(t);
+        e = cudaMemcpyToSymbol(kExp2j, t, sizeof t);
+        if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "exp table: %s", cudaGetErrorString(e));
         g_static_addr[dev] = p;
     }
     *out = static_cast<unsigned char *>(g_static_addr[dev]);
@@ -1391,7 +1405,7 @@ __global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst
     __shared__ bool am_last;
     for (int q = threadIdx.x; q < 2 * m.J; q += blockDim.x) h[q] = 0;
     __syncthreads();
-    const Tables<double> tb{edges, nullptr, vp, isp};  // edges: squared
+    const Tables<double> tb{edges, nullptr, vp, isp, kExp2j};  // edges: squared
     unsigned err = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double wi = w[i];

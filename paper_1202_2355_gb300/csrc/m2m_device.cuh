@@ -13,6 +13,8 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+#include "fp64_exp.cuh"
+
 namespace m2m {
 
 constexpr int kMaxGroups = 4;
@@ -165,7 +167,9 @@ inline Cst<T> make_cst(const Model &m)
 // Per-fit scalars living in device memory, written by the finalize.
 struct Scalars {
     long long t;        // steps completed
-    double wscale;      // current weight = wscale * stored weight
+    double wscale;      // current weight = wscale * stored weight (mixed mode)
+    double lwscale;     // ln wscale: current ln w = stored ln w + lwscale (FP64 mode)
+    double lwhat_flat;  // ln of the flat prior (-inf when it reads 0)
     double W0;          // initial total weight
     double what_flat;   // flat prior W0/N (global entropy)
     double chi2;
@@ -184,6 +188,13 @@ struct State {
     uint16_t *cell;
     long long n;
 };
+
+// FP64 mode stores ln w instead of w: the exponential force-of-change update is
+// then an addition and the entropy term -ln(w/what) a subtraction, so the only
+// transcendental left per particle for the weight is the exp that recovers w for
+// the deposit (mixed mode keeps w: its FP32 ln w would lose ~1e-6 relative per step).
+template <class T>
+constexpr bool kLogWeights = sizeof(T) == 8;
 
 // FP64 mode keeps a(x_t) from the closing half-kick of one step for the opening
 // half-kick of the next (the same function of the same positions, so bit-identical
@@ -204,6 +215,7 @@ struct Buffers {
     double *rec;                     // per aperture: the data term of eq. modFOC as polynomials in nu
     double *prior;                   // per cell: prior (cell mean weight)
     double *iprior;                  // per cell: 1/prior (0 when the prior reads as 0)
+    double *lprior;                  // per cell: ln prior (-inf when the prior reads as 0)
     long long *prior_count;          // per cell: particle count at the last update
     long long *hist;                 // global fixed-point sums
     double *ytil, *yraw, *delta;
@@ -465,7 +477,13 @@ struct Tables {
     const T *esq;         // per group squared edges
     const unsigned short *lut;
     const T *vp, *isp;
+    const double *e2;     // FP64 mode: 2^(j/32), j < 32 (exp_tab)
 };
+
+// exp of the kernel values and weights: the ex2-based approximation in mixed mode,
+// the table-driven exp_tab in FP64 mode.
+__device__ __forceinline__ float kexp(const Tables<float> &, float x) { return __expf(x); }
+__device__ __forceinline__ double kexp(const Tables<double> &tb, double x) { return exp_tab(x, tb.e2); }
 
 // Emits emit(slot, w K_slot, class) for every kernel of group G at aperture p:
 // surface mass (K = 1), v_los^2, v_los, and the Gauss-Hermite b_n with H_n from the
@@ -482,7 +500,7 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
     const int nmax = P::max_gh(G);
     if (nmax >= 0) {
         const T nu = (vlos - tb.vp[G.ap_off + p]) * tb.isp[G.ap_off + p];
-        const T we = w * d_exp(T(-0.5) * nu * nu);
+        const T we = w * kexp(tb, T(-0.5) * nu * nu);
         T hm1 = T(1), h = T(2) * nu;
         if (P::gh(G, 0)) emit(base + G.k_gh[0] * G.n_ap, T(gh_c(0)) * we, kClassGH);
         if (P::gh(G, 1)) emit(base + G.k_gh[1] * G.n_ap, h * we, kClassGH);
@@ -522,7 +540,7 @@ __device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, cons
 #pragma unroll
                 for (int n = 6; n >= 0; --n)
                     if (n <= nmax) poly = poly * nu + r[5 + n];
-                d += d_exp(T(-0.5) * nu * nu) * poly;
+                d += kexp(tb, T(-0.5) * nu * nu) * poly;
             }
             data += d;
         }
@@ -832,12 +850,42 @@ __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const T
     return wn;
 }
 
+// The same update on u = ln w (FP64 mode): u + eps dt F for the exponential rule,
+// u + ln(1 + eps dt F) for explicit Euler, with dS/dw = ln(what) - u.
+template <unsigned... Ms, class T>
+__device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
+                                            T lprior, T u, T x, T y, T z, T vy, T vz, unsigned &err)
+{
+    if (u == -HUGE_VAL) return u;  // w = 0 is a fixed point
+    T Y, vlos;
+    project(k, y, z, vy, vz, Y, vlos);
+    const T data = data_term<Ms...>(m, tb, rec, x, Y, vlos);
+    // a prior that reads 0 (below the resolution of the cell sums) drops the entropy term
+    T dS = lprior > -HUGE_VAL ? lprior - u : T(0);
+    if (m.mode == 0) dS -= T(1);
+    const T h = k.dteps * (k.mu * dS - data);
+    T un;
+    if (m.update_rule == 0) {
+        un = u + h;
+    } else {
+        if (!(h > T(-1))) {
+            err |= (h != h) ? kErrNonFinite : kErrNegWeight;
+            return u;
+        }
+        un = u + log1p(h);
+    }
+    // exp_tab overflows above 709
+    if (!(un <= T(709))) err |= kErrNonFinite;
+    return un;
+}
+
 // ---------------------------------------------------------------- shared-memory layout
 
 template <class T>
 struct Smem {
     void *h;               // fixed-point sums of the block (layout of Acc<T>)
-    T *c, *iprior, *esq, *vp, *isp;  // c: the force-of-change records
+    T *c, *iprior, *esq, *vp, *isp;  // c: the force-of-change records; iprior: 1/prior, or ln prior (FP64)
+    double *e2;            // 2^(j/32) for exp_tab
     unsigned short *lut;
 };
 
@@ -852,6 +900,7 @@ __host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist)
 {
     size_t b = with_hist ? acc_bytes_padded<T>(m) : 0;
     b += sizeof(T) * size_t(m.n_ap_total * m.rec_len + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
+    b = (b + 7) / 8 * 8 + sizeof(double) * 32;
     b += sizeof(unsigned short) * size_t(m.n_lut) + 16;
     return b;
 }
@@ -867,7 +916,9 @@ __device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, in
     s.esq = s.iprior + m.ncell;
     s.vp = s.esq + m.n_edges_total;
     s.isp = s.vp + m.n_ap_total;
-    s.lut = reinterpret_cast<unsigned short *>(s.isp + m.n_ap_total);
+    unsigned char *e = reinterpret_cast<unsigned char *>(s.isp + m.n_ap_total);
+    s.e2 = reinterpret_cast<double *>(base + (e - base + 7) / 8 * 8);
+    s.lut = reinterpret_cast<unsigned short *>(s.e2 + 32);
     return s;
 }
 
@@ -880,6 +931,7 @@ __device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, co
         s.isp[k] = T(b.isp[k]);
     }
     for (int k = threadIdx.x; k < m.n_lut; k += blockDim.x) s.lut[k] = b.lut[k];
+    for (int k = threadIdx.x; k < 32; k += blockDim.x) s.e2[k] = kExp2j[k];
 }
 
 // ---------------------------------------------------------------- force-of-change records
@@ -966,6 +1018,7 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
         if (threadIdx.x == 0) {
             sc.W0 = U;
             sc.what_flat = n > 0 ? U / double(n) : 0.0;
+            sc.lwhat_flat = sc.what_flat > 0.0 ? log(sc.what_flat) : -HUGE_VAL;
         }
     } else if (m.renormalize && U > 0.0) {
         s_ren = __ldcg(&sc.W0) / U;
@@ -995,6 +1048,7 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
             const double pr = cnt > 0 ? sum / double(cnt) : 0.0;  // mean weight of the cell
             b.prior[c] = pr;
             b.iprior[c] = pr > 0.0 ? 1.0 / pr : 0.0;
+            b.lprior[c] = pr > 0.0 ? log(pr) : -HUGE_VAL;
             b.prior_count[c] = cnt;
         }
     }
@@ -1009,6 +1063,7 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
         sc.chi2 = red[0];
         if (!init) sc.t = t;
         sc.wscale = s_ren;
+        sc.lwscale = log(s_ren);
         sc.pending = init ? 0 : (t > m.n_relax ? 1 : 0);
         sc.blocks_done = 0;
     }
@@ -1036,7 +1091,8 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     const int pending = init ? 0 : sc.pending;
     const int prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
     const T wscale = init ? T(1) : T(sc.wscale);
-    const T iwhat_flat = sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0);
+    const T lwscale = init ? T(0) : T(sc.lwscale);
+    const T iwhat_flat = kLogWeights<T> ? T(sc.lwhat_flat) : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
 
     {
         int *z = static_cast<int *>(S.h);
@@ -1045,12 +1101,14 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     }
     if (pending) {
         for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
-        if (m.mode == 1)
-            for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(b.iprior[q]);
+        if (m.mode == 1) {
+            const double *pr = kLogWeights<T> ? b.lprior : b.iprior;
+            for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(pr[q]);
+        }
     }
     load_tables(m, b, S);
     __syncthreads();
-    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp};
+    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp, S.e2};
 
     unsigned err = 0;
     Total<T> wtot;
@@ -1059,10 +1117,21 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
         T x = P.x[i], y = P.y[i], z = P.z[i];
         T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
-        T w = P.w[i] * wscale;
-        if (pending) {
-            const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
-            w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
+        T w, u;
+        if constexpr (kLogWeights<T>) {
+            u = P.w[i] + lwscale;
+            if (pending) {
+                const T lp = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
+                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, S.c, lp, u, x, y, z, vy, vz, err);
+            }
+            w = kexp(tb, u);
+        } else {
+            w = P.w[i] * wscale;
+            if (pending) {
+                const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
+                w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
+            }
+            u = w;
         }
         if constexpr (kCacheAccel<T>) {
             T ax, ay, az;
@@ -1102,7 +1171,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         }
         P.x[i] = x; P.y[i] = y; P.z[i] = z;
         P.vx[i] = vx; P.vy[i] = vy; P.vz[i] = vz;
-        P.w[i] = w;
+        P.w[i] = u;
     }
     if (err) atomicOr(&b.sc->err, err);
     // the total weight went into registers: one global atomic per warp and word
@@ -1145,21 +1214,36 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
     const Smem<T> S = carve<T>(m, smem, 0);
     const Scalars sc = *b.sc;
     for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
-    if (m.mode == 1)
-        for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(b.iprior[q]);
+    if (m.mode == 1) {
+        const double *pr = kLogWeights<T> ? b.lprior : b.iprior;
+        for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(pr[q]);
+    }
     load_tables(m, b, S);
     __syncthreads();
-    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp};
+    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp, S.e2};
     unsigned err = 0;
     Total<double> tot;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-        T w = P.w[i] * T(sc.wscale);
-        if (sc.pending) {
-            const T pr = (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
-            w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i], P.vz[i], err);
-            if (w != T(0)) tot.add(double(w), m.fx_w);
+        T w;
+        if constexpr (kLogWeights<T>) {
+            T u = P.w[i] + T(sc.lwscale);
+            if (sc.pending) {
+                const T lp = (m.mode == 1) ? S.iprior[P.cell[i]] : T(sc.lwhat_flat);
+                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, lp, u, P.x[i], P.y[i], P.z[i], P.vy[i],
+                                                           P.vz[i], err);
+            }
+            w = kexp(tb, u);
+        } else {
+            w = P.w[i] * T(sc.wscale);
+            if (sc.pending) {
+                const T pr =
+                    (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
+                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i], P.vz[i],
+                                                       err);
+            }
         }
+        if (sc.pending && w != T(0)) tot.add(double(w), m.fx_w);
         out[i] = double(w);
     }
     if (err) atomicOr(&b.sc->err, err);
@@ -1185,6 +1269,13 @@ __global__ void k_convert_in(const double *src, T *dst, long long n)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = T(src[i]);
+}
+
+// FP64 mode stores ln w (w = 0 gives -inf; load rejects negative weights first).
+__global__ void k_log_in(const double *src, double *dst, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = log(src[i]);
 }
 
 template <class T>
