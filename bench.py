@@ -52,14 +52,16 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 #   flops  FP64 flops the FP64 kernel executes (DFMA = 2, DADD/DMUL = 1: ncu
 #          sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over one
 #          step launch / N), including the iterative sqrt, division, log and exp;
-#   dram   dram__bytes_read.sum + dram__bytes_write.sum of one launch / N, from an
-#          ncu capture of the kernel as it stands (None when not captured).
 KERNEL_FIGURES = {
-    # read x, y, z, vx, vy, vz, w, ax, ay, az (80 B) + prior cell (2 B); write 80 B
-    "fp64": {"bytes": 162, "flops": None, "dram": None, "dram_n": None},
+    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B) + prior cell (2 B); write 80 B
+    "fp64": {"bytes": 162, "flops": None},
     # read 6 coordinates + w (28 B) + prior cell (2 B); write 28 B
-    "mixed": {"bytes": 58, "flops": None, "dram": 402.6e6 / 8e6, "dram_n": 8_000_000},
+    "mixed": {"bytes": 58, "flops": None},
 }
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one step launch / N, from an ncu
+# capture of the kernel as it stands, by (workload, precision); absent: not captured.
+DRAM_PER_UNIT = {}
 
 
 class ClockSampler:
@@ -119,7 +121,7 @@ def _dist():
     return ws, rank, local
 
 
-def roofline(precision: str, n: int, ms_per_launch: float) -> dict:
+def roofline(workload: str, precision: str, n: int, ms_per_launch: float) -> dict:
     """Roofline of the step kernel (the only kernel of the timed region).
 
     The FP64 kernel is bound by the FP64 pipe (HBM stays mostly idle); the mixed
@@ -128,10 +130,11 @@ def roofline(precision: str, n: int, ms_per_launch: float) -> dict:
     sec = ms_per_launch / 1e3
     gbs = f["bytes"] * n / sec / 1e9
     hbm, hbm_src = _hbm_peak()
-    traffic = None if f["dram"] is None else f["dram"] * n
+    dram = DRAM_PER_UNIT.get((workload, precision))
+    traffic = None if dram is None else dram[0] * n
     common = {"kernel": "k_step", "units_per_launch": n, "unit_of_work": "particle-step",
               "ms_per_launch": ms_per_launch, "algorithmic_bytes_per_unit": f["bytes"],
-              "traffic_per_unit_measured_at_n": f["dram_n"]}
+              "traffic_per_unit_measured_at_n": None if dram is None else dram[1]}
     if precision == "fp64":
         out = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
                "traffic": traffic, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
@@ -281,7 +284,7 @@ def run_ours(args):
     # end to end through the public API from pinned host buffers
     e2e_s = None if args.no_e2e else _e2e(B, wl, Y, sig, Vp, sp, stream, n, K, ws)
 
-    roof = roofline(wl.precision, n, step_ms / K)
+    roof = roofline(args.workload, wl.precision, n, step_ms / K)
     line = None
     if rank == 0:
         cpu = None

@@ -77,6 +77,12 @@ enum { M2M_REG_GWR = 0, M2M_REG_MPR = 1 };            /* eq. entropy / eq. S+ wi
 enum { M2M_E_LOGNEG = 0, M2M_E_EXP = 1, M2M_E_LINEAR = 2 }; /* E-axis bins uniform in ln(-E), exp(E), E */
 enum { M2M_PREC_FP64 = 0, M2M_PREC_MIXED = 1 };
 enum { M2M_UPDATE_EXP = 0, M2M_UPDATE_EULER = 1 };
+/* Deposit strategy of the step kernel. SHARED: per-block fixed-point sums in
+ * shared memory, flushed once per block; GLOBAL: every deposit added to the
+ * global fixed-point sums (for observable sets too large for shared memory,
+ * e.g. 64 x 64 maps of five moments). Both add the same integers, so results
+ * are bit-identical. AUTO: SHARED when it fits. */
+enum { M2M_DEPOSIT_AUTO = 0, M2M_DEPOSIT_SHARED = 1, M2M_DEPOSIT_GLOBAL = 2 };
 
 #define M2M_MAX_GROUPS 4
 #define M2M_MAX_KINDS 8
@@ -141,6 +147,7 @@ typedef struct {
     void *stream;                  /* cudaStream_t to run on; NULL: the library creates one */
     int32_t block;                 /* threads per block of the step kernel; 0: tuned */
     int32_t blocks_per_sm;         /* resident blocks per SM; 0: tuned */
+    int32_t deposit;               /* M2M_DEPOSIT_*: where the step kernel accumulates y_j */
 } m2m_options;
 
 /* Create a fit context on the current CUDA device. eps, mu and alpha are the

@@ -70,10 +70,13 @@ class PriorGrid(C.Structure):
                 ("Emax", C.c_double)]
 
 
+DEPOSIT = {"auto": 0, "shared": 1, "global": 2}
+
+
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("dt", C.c_double), ("renormalize", C.c_int32),
                 ("update_rule", C.c_int32), ("n_relax", C.c_int64), ("stream", C.c_void_p),
-                ("block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("deposit", C.c_int32)]
 
 
 def library_path() -> str:
@@ -215,14 +218,14 @@ class Fit:
 
     def __init__(self, potential_desc: dict, groups, incl_deg, Y, sig, Vp, sp, prior: dict,
                  params: dict, precision: str = "fp64", stream=None, block: int = 0,
-                 blocks_per_sm: int = 0):
+                 blocks_per_sm: int = 0, deposit: str = "auto"):
         self.desc = ObsDesc(groups, incl_deg, Y, sig, Vp, sp)
         self.J = self.desc.J
         self.ncell = prior["nE"] * prior["nx"] if prior["mode"] == "mpr" else 0
         P = potential(potential_desc)
         G = prior_grid(prior)
         opt = Options(PREC[precision], params["dt"], params["renormalize"], RULE[params["update_rule"]],
-                      params["n_relax"], stream, block, blocks_per_sm)
+                      params["n_relax"], stream, block, blocks_per_sm, DEPOSIT[deposit])
         h = C.c_void_p()
         _check(lib().m2m_create(C.byref(P), C.byref(self.desc.o), C.byref(G), params["eps"], params["mu"],
                                 params["alpha"], C.byref(opt), C.byref(h)))

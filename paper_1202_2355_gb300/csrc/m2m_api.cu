@@ -29,6 +29,8 @@ struct m2m_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int block = 256, bps = 0, nsm = 0, grid = 0;
+    int deposit = M2M_DEPOSIT_AUTO;  // requested; global_dep: the strategy in use
+    bool global_dep = false;
     size_t smem_step = 0, smem_mat = 0;
 
     // host copies of the descriptors
@@ -48,6 +50,7 @@ struct m2m_ctx {
     int *d_kind = nullptr;
     double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
     double *d_rec = nullptr, *d_iprior = nullptr, *d_lprior = nullptr;
+    float *d_recf = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
     Scalars *d_sc = nullptr;
     double *d_wout = nullptr;
@@ -367,8 +370,8 @@ struct StepKernel {
 template <class T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
 
-template <class T, int WPS, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-static typename StepKernel<T>::Fn step_fn() { return k_step<T, WPS, kMinBlocks<T>, M0, M1, M2, M3>; }
+template <class T, int WPS, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+static typename StepKernel<T>::Fn step_fn() { return k_step<T, WPS, kMinBlocks<T>, GA, M0, M1, M2, M3>; }
 
 static unsigned group_mask(const GroupDesc &G)
 {
@@ -382,17 +385,17 @@ static unsigned group_mask(const GroupDesc &G)
     return mk;
 }
 
-template <class T, int WPS>
+template <class T, int WPS, bool GA>
 static typename StepKernel<T>::Fn pick_step(const Model &m)
 {
     unsigned mk[4] = {0, 0, 0, 0};
     for (int g = 0; g < m.n_groups; ++g) mk[g] = group_mask(m.g[g]);
     constexpr unsigned kin1 = kBitV2 | bit_gh(4), kin2 = kBitV2 | bit_gh(3) | bit_gh(4);
     constexpr unsigned map = kBitPix | kBitMass | bit_gh(1) | bit_gh(2) | bit_gh(3) | bit_gh(4);
-    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin1) return step_fn<T, WPS, kBitMass, kin1, 0u, 0u>();
-    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin2) return step_fn<T, WPS, kBitMass, kin2, 0u, 0u>();
-    if (m.n_groups == 1 && mk[0] == map) return step_fn<T, WPS, map, 0u, 0u, 0u>();
-    return step_fn<T, WPS, kDyn, kDyn, kDyn, kDyn>();
+    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin1) return step_fn<T, WPS, GA, kBitMass, kin1, 0u, 0u>();
+    if (m.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin2) return step_fn<T, WPS, GA, kBitMass, kin2, 0u, 0u>();
+    if (m.n_groups == 1 && mk[0] == map) return step_fn<T, WPS, GA, map, 0u, 0u, 0u>();
+    return step_fn<T, WPS, GA, kDyn, kDyn, kDyn, kDyn>();
 }
 
 template <class T>
@@ -405,14 +408,23 @@ template <class T, int WPS>
 static m2m_status configure_kernels(m2m_ctx *ctx)
 {
     // the finalize reuses the start of the dynamic shared memory for a block reduction
-    ctx->smem_step = std::max(smem_bytes<T>(ctx->m, 1), size_t(256) * sizeof(double));
-    ctx->smem_mat = smem_bytes<T>(ctx->m, 0);
+    const size_t red = size_t(256) * sizeof(double);
+    const size_t smem_shared = std::max(smem_bytes<T>(ctx->m, 1, 1), red);
+    const size_t smem_global = std::max(smem_bytes<T>(ctx->m, 0, 0), red);
+    ctx->smem_mat = smem_bytes<T>(ctx->m, 0, 0);
     int maxsm = 0;
     CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    // block-shared sums while the sums and records fit in shared memory, else global deposits
+    if (ctx->deposit == M2M_DEPOSIT_SHARED && smem_shared > size_t(maxsm))
+        return fail(ctx, M2M_ERR_ARG, "shared deposit needs %zu B of shared memory (limit %d)", smem_shared, maxsm);
+    ctx->global_dep = ctx->deposit == M2M_DEPOSIT_GLOBAL ||
+                      (ctx->deposit == M2M_DEPOSIT_AUTO && smem_shared > size_t(maxsm));
+    ctx->smem_step = ctx->global_dep ? smem_global : smem_shared;
     if (ctx->smem_step > size_t(maxsm))
-        return fail(ctx, M2M_ERR_ARG, "observable set and prior grid need %zu B of shared memory (limit %d)",
+        return fail(ctx, M2M_ERR_ARG, "observable tables and prior grid need %zu B of shared memory (limit %d)",
                     ctx->smem_step, maxsm);
-    ctx->kstep = reinterpret_cast<void *>(pick_step<T, WPS>(ctx->m));
+    ctx->kstep = reinterpret_cast<void *>(ctx->global_dep ? pick_step<T, WPS, true>(ctx->m)
+                                                           : pick_step<T, WPS, false>(ctx->m));
     CU(cudaFuncSetAttribute(step_kernel<T>(ctx), cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_step)));
     CU(cudaFuncSetAttribute(k_materialize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_mat)));
     int occ = 0;
@@ -451,6 +463,8 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMalloc(&ctx->d_c, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_rec, sizeof(double) * m.n_ap_total * m.rec_len));
     CU(cudaMemset(ctx->d_rec, 0, sizeof(double) * m.n_ap_total * m.rec_len));
+    CU(cudaMalloc(&ctx->d_recf, sizeof(float) * m.n_ap_total * m.rec_len));
+    CU(cudaMemset(ctx->d_recf, 0, sizeof(float) * m.n_ap_total * m.rec_len));
     CU(cudaMalloc(&ctx->d_ytil, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_yraw, sizeof(double) * m.J));
     CU(cudaMalloc(&ctx->d_delta, sizeof(double) * m.J));
@@ -498,6 +512,9 @@ static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *o
         ctx->block = (opt->block > 0) ? opt->block : 256;
         if (ctx->block % 32 != 0 || ctx->block > 256) s = fail(ctx, M2M_ERR_ARG, "block must be a multiple of 32, <= 256");
         ctx->bps = opt->blocks_per_sm;
+        ctx->deposit = opt->deposit;
+        if (ctx->deposit < M2M_DEPOSIT_AUTO || ctx->deposit > M2M_DEPOSIT_GLOBAL)
+            s = fail(ctx, M2M_ERR_ARG, "deposit must be M2M_DEPOSIT_AUTO, _SHARED or _GLOBAL");
     }
     if (s == M2M_OK) {
         s = ctx->precision == M2M_PREC_FP64 ? configure_kernels<double, 2>(ctx) : configure_kernels<float, 1>(ctx);
@@ -547,7 +564,7 @@ static Buffers buffers(m2m_ctx *c)
     Buffers b;
     b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
-    b.c = c->d_c; b.rec = c->d_rec; b.prior = c->d_prior; b.iprior = c->d_iprior; b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior; b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
 }
@@ -1059,6 +1076,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         p += sizeof(double) * m.J;
     }
     CU(cudaMemcpy(ctx->d_rec, p, sizeof(double) * m.n_ap_total * m.rec_len, cudaMemcpyHostToDevice));
+    k_convert_in<float><<<ctx->nsm, 256, 0, ctx->stream>>>(ctx->d_rec, ctx->d_recf, m.n_ap_total * m.rec_len);
+    CU(cudaStreamSynchronize(ctx->stream));
     p += sizeof(double) * m.n_ap_total * m.rec_len;
     if (m.ncell) {
         CU(cudaMemcpy(ctx->d_prior, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
@@ -1292,7 +1311,7 @@ extern "C" void m2m_destroy(m2m_ctx *ctx)
     free_state(ctx);
     free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
-    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
+    free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_recf); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
     free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);

@@ -213,6 +213,7 @@ struct Buffers {
     const double *obs_iscale;        // per observable: 1/fixed-point scale
     double *c;                       // per observable: coefficient of the force of change
     double *rec;                     // per aperture: the data term of eq. modFOC as polynomials in nu
+    float *recf;                     // FP32 copy of rec (mixed mode reads it from global memory)
     double *prior;                   // per cell: prior (cell mean weight)
     double *iprior;                  // per cell: 1/prior (0 when the prior reads as 0)
     double *lprior;                  // per cell: ln prior (-inf when the prior reads as 0)
@@ -895,24 +896,27 @@ __host__ __device__ inline size_t acc_bytes_padded(const Model &m)
     return (Acc<T>::bytes(m) + 15) / 16 * 16;
 }
 
+// Dynamic shared memory of a kernel holding the block sums (with_hist) and the
+// force-of-change records (with_rec) in shared memory; the global-deposit step
+// kernel keeps both in global memory.
 template <class T>
-__host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist)
+__host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist, int with_rec = 1)
 {
     size_t b = with_hist ? acc_bytes_padded<T>(m) : 0;
-    b += sizeof(T) * size_t(m.n_ap_total * m.rec_len + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
+    b += sizeof(T) * size_t((with_rec ? m.n_ap_total * m.rec_len : 0) + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
     b = (b + 7) / 8 * 8 + sizeof(double) * 32;
     b += sizeof(unsigned short) * size_t(m.n_lut) + 16;
     return b;
 }
 
 template <class T>
-__device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, int with_hist)
+__device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, int with_hist, int with_rec = 1)
 {
     Smem<T> s;
     s.h = base;
     T *t = reinterpret_cast<T *>(base + (with_hist ? acc_bytes_padded<T>(m) : 0));
     s.c = t;
-    s.iprior = s.c + m.n_ap_total * m.rec_len;
+    s.iprior = s.c + (with_rec ? m.n_ap_total * m.rec_len : 0);
     s.esq = s.iprior + m.ncell;
     s.vp = s.esq + m.n_edges_total;
     s.isp = s.vp + m.n_ap_total;
@@ -995,6 +999,8 @@ __device__ void build_records(const Model &m, const Buffers &b)
 #pragma unroll
             for (int q = 0; q < 7; ++q)
                 if (5 + q < m.rec_len) r[5 + q] = pc[q];
+            float *rf = b.recf + a * m.rec_len;
+            for (int q = 0; q < m.rec_len; ++q) rf[q] = float(r[q]);
         }
     }
 }
@@ -1078,12 +1084,43 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
 // weight sums and counts. Blocks add their sums to the global sums with integer
 // atomics (exact, so order-independent); the last block to finish runs the
 // finalize. Nothing waits on another block.
-template <class T, int WPS, int MINB, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+//
+// GA (global deposit): for observable sets whose block sums or force-of-change
+// records do not fit in shared memory (e.g. 64 x 64 pixel maps of five moments),
+// every deposit goes straight to the global int64 sums with 64-bit atomics and the
+// records are read from global memory (L1/L2 resident). The sums are the same
+// integers in either mode, so both give bit-identical results.
+template <class T>
+__device__ __forceinline__ const T *global_records(const Buffers &b);
+template <>
+__device__ __forceinline__ const double *global_records<double>(const Buffers &b) { return b.rec; }
+template <>
+__device__ __forceinline__ const float *global_records<float>(const Buffers &b) { return b.recf; }
+
+// One deposit into the global sums (global-deposit mode): the fixed-point words of
+// the block-shared path, added directly.
+__device__ __forceinline__ void global_add(long long *hist, int slot, double v, double scale)
+{
+    if (v == 0.0) return;
+    long long hi, lo;
+    fx2(v, scale, hi, lo);
+    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * slot), static_cast<unsigned long long>(hi));
+    if (lo) atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * slot + 1), static_cast<unsigned long long>(lo));
+}
+__device__ __forceinline__ void global_add(long long *hist, int slot, float v, float scale)
+{
+    if (v == 0.f) return;
+    const Limbs l = split(v, scale);
+    atomicAdd(reinterpret_cast<unsigned long long *>(hist + slot),
+              static_cast<unsigned long long>(limbs_value(l.hi, l.mid, l.lo)));
+}
+
+template <class T, int WPS, int MINB, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
 __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
                                                     const Buffers b, int push, int init)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Smem<T> S = carve<T>(m, smem, 1);
+    const Smem<T> S = carve<T>(m, smem, GA ? 0 : 1, GA ? 0 : 1);
     __shared__ bool am_last;
 
     const Scalars sc = *b.sc;
@@ -1094,13 +1131,14 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     const T lwscale = init ? T(0) : T(sc.lwscale);
     const T iwhat_flat = kLogWeights<T> ? T(sc.lwhat_flat) : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
 
-    {
+    if (!GA) {
         int *z = static_cast<int *>(S.h);
         const int nw = int(Acc<T>::bytes(m) / sizeof(int));
         for (int q = threadIdx.x; q < nw; q += blockDim.x) z[q] = 0;
     }
     if (pending) {
-        for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
+        if (!GA)
+            for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = global_records<T>(b)[q];
         if (m.mode == 1) {
             const double *pr = kLogWeights<T> ? b.lprior : b.iprior;
             for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(pr[q]);
@@ -1109,6 +1147,11 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     load_tables(m, b, S);
     __syncthreads();
     const Tables<T> tb{S.esq, S.lut, S.vp, S.isp, S.e2};
+    const T *rec = GA ? global_records<T>(b) : S.c;
+    auto deposit = [&](int slot, T v, T scale) {
+        if constexpr (GA) global_add(b.hist, slot, v, scale);
+        else Acc<T>::add(S.h, m, slot, v, scale);
+    };
 
     unsigned err = 0;
     Total<T> wtot;
@@ -1122,14 +1165,14 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
             u = P.w[i] + lwscale;
             if (pending) {
                 const T lp = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
-                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, S.c, lp, u, x, y, z, vy, vz, err);
+                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, lp, u, x, y, z, vy, vz, err);
             }
             w = kexp(tb, u);
         } else {
             w = P.w[i] * wscale;
             if (pending) {
                 const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
-                w = foc_update<M0, M1, M2, M3>(m, k, tb, S.c, pr, w, x, y, z, vy, vz, err);
+                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, pr, w, x, y, z, vy, vz, err);
             }
             u = w;
         }
@@ -1156,7 +1199,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
                     if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
                     group_kernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
-                        Acc<T>::add(S.h, m, j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
+                        deposit(j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
                     });
                 }
             });
@@ -1165,8 +1208,9 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         }
         if (prior_step) {
             const int c = prior_cell(m, k, b.lcE, x, y, z, vx, vy, vz);
-            Acc<T>::add(S.h, m, m.J + 1 + c, w, k.fx_w);
-            Acc<T>::count(S.h, m, c);
+            deposit(m.J + 1 + c, w, k.fx_w);
+            if constexpr (GA) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + m.off_count + c), 1ull);
+            else Acc<T>::count(S.h, m, c);
             P.cell[i] = static_cast<uint16_t>(c);
         }
         P.x[i] = x; P.y[i] = y; P.z[i] = z;
@@ -1185,7 +1229,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
     for (int o = 16; o > 0; o >>= 1) wdep += __shfl_xor_sync(0xffffffffu, wdep, o);
     if ((threadIdx.x & 31) == 0 && wdep != T(0)) atomicAdd(&b.sc->Wcheck, double(wdep));
     __syncthreads();
-    const int words = prior_step ? m.hist_words : m.off_grid;
+    const int words = GA ? 0 : (prior_step ? m.hist_words : m.off_grid);
     for (int q = threadIdx.x; q < words; q += blockDim.x) {
         if (q >= WPS * m.J && q < WPS * (m.J + 1)) continue;  // the total is already global
         const long long v = Acc<T>::word(S.h, m, q);
@@ -1211,9 +1255,8 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
                               long long *acc)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Smem<T> S = carve<T>(m, smem, 0);
+    const Smem<T> S = carve<T>(m, smem, 0, 0);
     const Scalars sc = *b.sc;
-    for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = T(b.rec[q]);
     if (m.mode == 1) {
         const double *pr = kLogWeights<T> ? b.lprior : b.iprior;
         for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(pr[q]);
@@ -1230,8 +1273,8 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             T u = P.w[i] + T(sc.lwscale);
             if (sc.pending) {
                 const T lp = (m.mode == 1) ? S.iprior[P.cell[i]] : T(sc.lwhat_flat);
-                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, lp, u, P.x[i], P.y[i], P.z[i], P.vy[i],
-                                                           P.vz[i], err);
+                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), lp, u, P.x[i], P.y[i],
+                                                           P.z[i], P.vy[i], P.vz[i], err);
             }
             w = kexp(tb, u);
         } else {
@@ -1239,8 +1282,8 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             if (sc.pending) {
                 const T pr =
                     (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
-                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, S.c, pr, w, P.x[i], P.y[i], P.z[i], P.vy[i], P.vz[i],
-                                                       err);
+                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), pr, w, P.x[i], P.y[i],
+                                                       P.z[i], P.vy[i], P.vz[i], err);
             }
         }
         if (sc.pending && w != T(0)) tot.add(double(w), m.fx_w);
