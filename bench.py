@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "M2M particle-steps/s (push+observe+MPR weight update) at stated chi2 error, 1 GB300"
 UNIT = "particle-steps/s"
-WORKLOADS = {"c1": 0, "c2": 1, "c3": 2, "c4": 3}
+WORKLOADS = {"c1": 0, "c2": 1, "c3": 2, "c4": 3, "c5": 4}
 
 
 def _hbm_peak():
@@ -150,18 +150,29 @@ def roofline(workload: str, precision: str, n: int, ms_per_launch: float) -> dic
     return out
 
 
+def _sample_workload(wl_name: str, n_sample: int):
+    """The first n_sample particles of a workload (of the first fit for the c5 batch)."""
+    from paper_1202_2355_gb300 import workloads as W
+    if wl_name == "c5":
+        wl = W.make_batch(fits=[0])[0]
+        wl.model = W.subset(wl.model, min(n_sample, wl.n))
+        wl.n = len(wl.model["x"])
+        return wl
+    return W.make(wl_name, n=n_sample)
+
+
 def cpu_baseline(wl_name: str, n_sample: int, steps: int):
     """The oracle as it stands, single-threaded, on the first n_sample particles of the workload."""
     import oracle as O
-    from paper_1202_2355_gb300 import workloads as W
-    wl = W.make(wl_name, n=n_sample)
+    wl = _sample_workload(wl_name, n_sample)
+    n_sample = wl.n
     obs, Y, sig = O.from_workload(wl)
     run = O.Run(wl.potential, obs, Y, sig, wl.prior, wl.params, wl.model)
     t0 = time.perf_counter()
     rc = run.step(steps)
     dt = time.perf_counter() - t0
     assert rc == 0
-    return n_sample * steps / dt, dt
+    return n_sample * steps / dt, dt, n_sample
 
 
 def run_reference(args):
@@ -171,8 +182,8 @@ def run_reference(args):
     import oracle as O
     from paper_1202_2355_gb300 import workloads as W
     O.build()
-    n_sample = args.ref_sample
-    wl = W.make(args.workload, n=n_sample)
+    wl = _sample_workload(args.workload, args.ref_sample)
+    n_sample = wl.n
     obs, Y, sig = O.from_workload(wl)
     run = O.Run(wl.potential, obs, Y, sig, wl.prior, wl.params, wl.model)
     assert run.step(args.warmup) == 0
@@ -226,6 +237,134 @@ def _e2e(B, wl, Y, sig, Vp, sp, stream, n, K, ws):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dt = float(t[0])
     return dt
+
+
+def run_batch(args):
+    """The c5 batch: 96 independent mixed-precision fits of uneven size advanced by one
+    launch per step (m2m_create_batch), launch shape from the library's autotuner."""
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1202_2355_gb300 import binding as B
+    from paper_1202_2355_gb300 import build as BUILD
+    from paper_1202_2355_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    BUILD.build()
+    K, Wm = args.steps, args.warmup
+    n_all = W.batch_draws()[0]
+    scale = 1.0 if args.n is None else args.n / float(n_all.sum())
+    # every rank runs its own copy of the batch: weak scaling, no collective on the data path
+    wls = W.make_batch(n_scale=scale)
+    descs = []
+    for wl in wls:
+        Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
+        descs.append(dict(potential=wl.potential, groups=wl.groups, incl_deg=wl.incl_deg, Y=Y, sig=sig, Vp=Vp,
+                          sp=sp, prior=wl.prior, params=wl.params))
+        wl.target = None
+    ntot = sum(wl.n for wl in wls)
+    stream = torch.cuda.Stream()
+    batch = B.Batch(descs, precision="mixed", stream=stream.cuda_stream)
+    for wl, f in zip(wls, batch.fits):
+        f.load(wl.model)
+    shape = batch.autotune(steps=2)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(Wm):
+            batch.step(1)
+            flush.fill_(1)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    batch.set_timing(True)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                batch.step(1)
+                flush.fill_(1)
+        batch.synchronize()
+        torch.cuda.synchronize()
+    step_ms, nt = batch.timing()
+    batch.set_timing(False)
+    assert nt == K
+    chi2_per_J = float(np.mean([f.chi2() / f.J for f in batch.fits]))
+    if ws > 1:
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t[0])
+        dist.barrier()
+    value = ws * ntot * K / (step_ms / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the public API: load every fit from pinned host buffers,
+        # K x (one batched step, read every fit's chi^2), read every fit's weights
+        pinned = []
+        for wl in wls:
+            pinned.append((torch.from_numpy(np.concatenate([wl.model[k] for k in ("x", "y", "z")])).pin_memory(),
+                           torch.from_numpy(np.concatenate([wl.model[k] for k in ("vx", "vy", "vz")])).pin_memory(),
+                           torch.from_numpy(np.ascontiguousarray(wl.model["w"])).pin_memory(),
+                           torch.empty(wl.n, dtype=torch.float64).pin_memory()))
+        lib = B.lib()
+        c2, J = C.c_double(), C.c_int32()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for wl, f, (pos, vel, wts, _) in zip(wls, batch.fits, pinned):
+            B._check(lib.m2m_load_particles(f.h, wl.n, C.cast(pos.data_ptr(), B._DP), C.cast(vel.data_ptr(), B._DP),
+                                            C.cast(wts.data_ptr(), B._DP)), f.h)
+        for _ in range(K):
+            B._check(lib.m2m_step(batch.h, 1), batch.h)
+            for f in batch.fits:
+                B._check(lib.m2m_get_chi2(f.h, C.byref(c2), C.byref(J), None), f.h)
+        for wl, f, (_, _, _, wout) in zip(wls, batch.fits, pinned):
+            B._check(lib.m2m_get_weights(f.h, C.cast(wout.data_ptr(), B._DP), wl.n), f.h)
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t[0])
+        e2e = {"value": ws * ntot * K / dt, "unit": UNIT, "h2d_bytes_per_step": 7 * 8 * ntot / K,
+               "d2h_bytes_per_step": 8 * len(wls) + 8 * ntot / K,
+               "note": "every fit loaded from pinned host memory once, K x (batched step + every fit's chi^2 "
+                       "read), every fit's weights read"}
+    batch.close()
+    roof = roofline("c5", "mixed", ntot, step_ms / K)
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            import oracle as O
+            O.build()
+            v, dt, ns = cpu_baseline("c5", args.cpu_sample, args.cpu_steps)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"first {ns} particles of fit 0 of the c5 batch, {args.cpu_steps} steps, "
+                             f"{dt:.1f} s single-threaded FP64"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+i64", "data": "synthetic",
+            "config": {"workload": "c5_batch96_hernquist_nfw_mixed", "fits": len(wls), "n_particles": ntot,
+                       "observables_per_fit": wls[0].J, "prior_grid": "50x20 every 25", "dt": 0.01,
+                       "precision": "mixed", "launch_shape": {"block": shape[0], "blocks_per_sm": shape[1],
+                                                              "segment": shape[2]},
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"{ws} independent batch(es) of {len(wls)} fits, one per GPU",
+                       "chi2_per_J_end_mean": chi2_per_J},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K,  # one batched step kernel per step for all fits
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_ours(args):
@@ -291,7 +430,7 @@ def run_ours(args):
         if ws == 1 and not args.no_cpu_baseline:
             import oracle as O
             O.build()
-            v, dt = cpu_baseline(args.workload, args.cpu_sample, args.cpu_steps)
+            v, dt, _ = cpu_baseline(args.workload, args.cpu_sample, args.cpu_steps)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {args.cpu_sample} particles of {wl.name}, {args.cpu_steps} steps, "
                              f"{dt:.1f} s single-threaded FP64"}
@@ -339,6 +478,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -210,6 +210,43 @@ m2m_status m2m_get_particle_count(m2m_ctx *ctx, int64_t *n);
 m2m_status m2m_set_timing(m2m_ctx *ctx, int32_t on);
 m2m_status m2m_get_timing(m2m_ctx *ctx, double *step_kernel_ms, int64_t *steps);
 
+/* ---- Batches of independent fits ----
+ *
+ * A batch advances many independent fits (each with its own potential,
+ * observable set and targets, prior grid, eps, mu, alpha and particle count)
+ * with one kernel launch per step. Every fit of a batch is a full context: its
+ * particles are loaded, and its weights, observables, chi^2, priors and state
+ * read or checkpointed, through the fit handle m2m_batch_model returns, with the
+ * single-fit calls above. m2m_step, m2m_synchronize and the timing calls take the
+ * batch handle and act on all fits; the other single-fit calls reject it with
+ * M2M_ERR_STATE. All fits share the precision and stream of `opt` and the
+ * block-shared deposit (M2M_DEPOSIT_GLOBAL is rejected); a fit advanced in a batch
+ * gives bit-identical results to the same fit advanced alone. */
+
+/* Create a batch of nmodels >= 1 fits from arrays of nmodels descriptors and
+ * parameters (copied; see m2m_create). Errors: M2M_ERR_ARG naming the first
+ * invalid fit, M2M_ERR_CUDA / M2M_ERR_OOM. m2m_destroy(batch) releases every fit. */
+m2m_status m2m_create_batch(int32_t nmodels, const m2m_potential *pots, const m2m_observables *obs,
+                            const m2m_prior_grid *priors, const double *eps, const double *mu,
+                            const double *alpha, const m2m_options *opt, m2m_ctx **out);
+
+/* Number of fits in a batch. */
+m2m_status m2m_batch_size(m2m_ctx *batch, int32_t *nmodels);
+
+/* Handle of fit i (0 <= i < nmodels), owned by the batch (m2m_destroy on it does
+ * nothing). Stepping it alone advances only that fit. */
+m2m_status m2m_batch_model(m2m_ctx *batch, int32_t i, m2m_ctx **model);
+
+/* Times the batched step for a set of launch shapes (threads per block, resident
+ * blocks per SM, particles per segment; a segment is a contiguous run of one
+ * fit's particles that a block processes before flushing its sums), each over
+ * `steps` steps after one warm-up step, and keeps the fastest, returned in the
+ * optional outputs. The trial steps are real steps: every fit advances by
+ * (steps + 1) times the number of shapes tried (at most 12). The sums are exact
+ * integers, so results do not depend on the shape. Requires every fit loaded. */
+m2m_status m2m_batch_autotune(m2m_ctx *batch, int32_t steps, int32_t *block, int32_t *blocks_per_sm,
+                              int64_t *segment);
+
 /* Write / read the full fit state (particles, weights, priors, smoothed
  * observables, step counter, pending update) to / from a file. A context
  * resumed from a file continues bit-identically to an uninterrupted run with

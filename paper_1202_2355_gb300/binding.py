@@ -114,11 +114,18 @@ def lib():
         L.m2m_last_error.restype = C.c_char_p
         L.m2m_last_error.argtypes = [vp]
         L.m2m_destroy.argtypes = [vp]
+        L.m2m_create_batch.argtypes = [C.c_int32, C.POINTER(Potential), C.POINTER(Observables),
+                                       C.POINTER(PriorGrid), _DP, _DP, _DP, C.POINTER(Options), C.POINTER(vp)]
+        L.m2m_batch_size.argtypes = [vp, C.POINTER(C.c_int32)]
+        L.m2m_batch_model.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+        L.m2m_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int64)]
         for name in ("m2m_create", "m2m_load_particles", "m2m_load_particles_device", "m2m_step",
                      "m2m_synchronize", "m2m_get_weights", "m2m_get_state", "m2m_get_observables",
                      "m2m_get_chi2", "m2m_get_priors", "m2m_get_step_count", "m2m_get_particle_count",
                      "m2m_save_state", "m2m_set_timing", "m2m_get_timing",
-                     "m2m_load_state", "m2m_build_targets"):
+                     "m2m_load_state", "m2m_build_targets", "m2m_create_batch", "m2m_batch_size",
+                     "m2m_batch_model", "m2m_batch_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -218,10 +225,15 @@ class Fit:
 
     def __init__(self, potential_desc: dict, groups, incl_deg, Y, sig, Vp, sp, prior: dict,
                  params: dict, precision: str = "fp64", stream=None, block: int = 0,
-                 blocks_per_sm: int = 0, deposit: str = "auto"):
+                 blocks_per_sm: int = 0, deposit: str = "auto", handle=None):
         self.desc = ObsDesc(groups, incl_deg, Y, sig, Vp, sp)
         self.J = self.desc.J
         self.ncell = prior["nE"] * prior["nx"] if prior["mode"] == "mpr" else 0
+        self.n = 0
+        self.owned = handle is None
+        if handle is not None:  # a fit of a batch (m2m_batch_model), owned by the batch
+            self.h = handle
+            return
         P = potential(potential_desc)
         G = prior_grid(prior)
         opt = Options(PREC[precision], params["dt"], params["renormalize"], RULE[params["update_rule"]],
@@ -230,11 +242,11 @@ class Fit:
         _check(lib().m2m_create(C.byref(P), C.byref(self.desc.o), C.byref(G), params["eps"], params["mu"],
                                 params["alpha"], C.byref(opt), C.byref(h)))
         self.h = h
-        self.n = 0
 
     def close(self):
         if getattr(self, "h", None):
-            lib().m2m_destroy(self.h)
+            if self.owned:
+                lib().m2m_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -322,3 +334,74 @@ def fit_from_workload(wl, Y, sig, Vp, sp, precision: str | None = None, params: 
                       prior: dict | None = None, **kw) -> Fit:
     return Fit(wl.potential, wl.groups, wl.incl_deg, Y, sig, Vp, sp, prior or wl.prior,
                params or wl.params, precision or wl.precision, **kw)
+
+
+class Batch:
+    """Many independent fits advanced together (m2m_create_batch). `fits` is a list
+    of dicts with the keys of Fit's arguments: potential, groups, incl_deg, Y, sig,
+    Vp, sp, prior, params. Per-fit calls go through batch.fit(i), a Fit."""
+
+    def __init__(self, fits, precision: str = "fp64", stream=None, block: int = 0, blocks_per_sm: int = 0):
+        M = len(fits)
+        self.descs = [ObsDesc(f["groups"], f["incl_deg"], f["Y"], f["sig"], f["Vp"], f["sp"]) for f in fits]
+        pots = (Potential * M)(*[potential(f["potential"]) for f in fits])
+        obs = (Observables * M)(*[d.o for d in self.descs])
+        pri = (PriorGrid * M)(*[prior_grid(f["prior"]) for f in fits])
+        eps = np.array([f["params"]["eps"] for f in fits], np.float64)
+        mu = np.array([f["params"]["mu"] for f in fits], np.float64)
+        alpha = np.array([f["params"]["alpha"] for f in fits], np.float64)
+        p0 = fits[0]["params"]
+        opt = Options(PREC[precision], p0["dt"], p0["renormalize"], RULE[p0["update_rule"]], p0["n_relax"],
+                      stream, block, blocks_per_sm, 0)
+        h = C.c_void_p()
+        _check(lib().m2m_create_batch(M, pots, obs, pri, _dp(eps), _dp(mu), _dp(alpha), C.byref(opt),
+                                      C.byref(h)))
+        self.h = h
+        self.fits = []
+        for i, f in enumerate(fits):
+            sub = C.c_void_p()
+            self._ck(lib().m2m_batch_model(self.h, i, C.byref(sub)))
+            self.fits.append(Fit(f["potential"], f["groups"], f["incl_deg"], f["Y"], f["sig"], f["Vp"], f["sp"],
+                                 f["prior"], f["params"], precision, handle=sub))
+
+    def __len__(self):
+        return len(self.fits)
+
+    def fit(self, i: int) -> Fit:
+        return self.fits[i]
+
+    def _ck(self, s):
+        _check(s, self.h)
+
+    def step(self, nsteps: int = 1):
+        self._ck(lib().m2m_step(self.h, nsteps))
+
+    def synchronize(self):
+        self._ck(lib().m2m_synchronize(self.h))
+
+    def autotune(self, steps: int = 3):
+        """(threads per block, blocks per SM, particles per segment) kept by the autotuner."""
+        b, k, seg = C.c_int32(), C.c_int32(), C.c_int64()
+        self._ck(lib().m2m_batch_autotune(self.h, steps, C.byref(b), C.byref(k), C.byref(seg)))
+        return b.value, k.value, seg.value
+
+    def set_timing(self, on: bool):
+        self._ck(lib().m2m_set_timing(self.h, 1 if on else 0))
+
+    def timing(self):
+        a, k = C.c_double(), C.c_int64()
+        self._ck(lib().m2m_get_timing(self.h, C.byref(a), C.byref(k)))
+        return a.value, k.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            for f in self.fits:
+                f.h = None
+            lib().m2m_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

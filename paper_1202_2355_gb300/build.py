@@ -7,9 +7,13 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "_build", "libm2m.so")
-SOURCES = [os.path.join(HERE, "csrc", f) for f in ("m2m_api.cu",)]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "m2m_device.cuh"), os.path.join(ROOT, "include", "m2m.h")]
+CSRC = os.path.join(HERE, "csrc")
+SOURCES = [os.path.join(CSRC, f) for f in ("m2m_api.cu", "m2m_batch.cu")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+
+
+def _deps():
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(ROOT, "include", "m2m.h")]
 
 
 def nvcc() -> str:
@@ -20,20 +24,33 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile csrc/ into _build/libm2m.so unless it is newer than every source."""
-    if not force and os.path.exists(SO) and os.path.getmtime(SO) >= max(os.path.getmtime(d) for d in DEPS):
+    """Compile csrc/ into _build/libm2m.so unless it is newer than every source.
+    The translation units compile in parallel, then link."""
+    if not force and os.path.exists(SO) and os.path.getmtime(SO) >= max(os.path.getmtime(d) for d in _deps()):
         return SO
-    os.makedirs(os.path.dirname(SO), exist_ok=True)
-    tmp = SO + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp] + SOURCES
+    bdir = os.path.dirname(SO)
+    os.makedirs(bdir, exist_ok=True)
+    tag = f".tmp{os.getpid()}"
+    flags = ["-O3", "-std=c++17", ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        flags.append("-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + tag + ".o")
+        objs.append(obj)
+        procs.append(subprocess.Popen([nvcc()] + flags + ["-c", "-o", obj, src], stdout=subprocess.PIPE,
+                                      stderr=subprocess.STDOUT, text=True))
+    outs = [p.communicate()[0] for p in procs]
+    if any(p.returncode for p in procs):
+        raise RuntimeError("nvcc failed:\n" + "\n".join(outs))
+    tmp = SO + tag
+    r = subprocess.run([nvcc(), "-shared", ARCH, "-o", tmp] + objs, capture_output=True, text=True)
+    for o in objs:
+        os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     if verbose:
-        print(r.stdout + r.stderr)
+        print("\n".join(outs))
     os.replace(tmp, SO)
     return SO
 

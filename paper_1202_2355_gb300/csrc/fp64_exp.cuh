@@ -20,8 +20,9 @@
 
 namespace m2m {
 
-// 2^(j/32), j = 0 .. 31, rounded to double (set by exp2_table on the host).
-__constant__ double kExp2j[32];
+// 2^(j/32), j = 0 .. 31, rounded to double (set by exp2_table on the host). Each
+// translation unit holds its own copy.
+static __constant__ double kExp2j[32];
 
 inline void exp2_table(double t[32])
 {

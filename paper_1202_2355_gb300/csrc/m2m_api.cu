@@ -6,8 +6,7 @@
 // over the particles, whose last block to finish runs the finalize over the
 // observables and prior cells. Every per-step decision is read from device
 // memory, so a chunk of steps is captured once in a CUDA graph and replayed.
-#include "m2m.h"
-#include "m2m_device.cuh"
+#include "m2m_ctx.h"
 
 #include <algorithm>
 #include <cmath>
@@ -20,57 +19,9 @@
 
 using namespace m2m;
 
-struct m2m_ctx {
-    Model m{};
-    int precision = 0;
-    int internal = 0;  // allows the internal first-moment kind (target construction)
-    double eps = 0, mu = 0, alpha = 0;
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int block = 256, bps = 0, nsm = 0, grid = 0;
-    int deposit = M2M_DEPOSIT_AUTO;  // requested; global_dep: the strategy in use
-    bool global_dep = false;
-    size_t smem_step = 0, smem_mat = 0;
+thread_local std::string g_create_error;
 
-    // host copies of the descriptors
-    std::vector<double> edges, Vp, isp, Y, sig, obs_post, obs_iscale, area_of_obs, lcE;
-    std::vector<int> obs_kind;
-    std::vector<unsigned short> lut;
-    uint64_t config_hash = 0;
-
-    // device buffers
-    long long n = 0;
-    long long capacity = 0;
-    void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and in FP64 mode ax, ay, az
-    uint16_t *cell = nullptr;
-    double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
-    unsigned short *d_lut = nullptr;
-    double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
-    int *d_kind = nullptr;
-    double *d_c = nullptr, *d_prior = nullptr, *d_ytil = nullptr, *d_yraw = nullptr, *d_delta = nullptr;
-    double *d_rec = nullptr, *d_iprior = nullptr, *d_lprior = nullptr;
-    float *d_recf = nullptr;
-    long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
-    Scalars *d_sc = nullptr;
-    double *d_wout = nullptr;
-    long long wout_cap = 0;
-    bool loaded = false;
-
-    cudaGraphExec_t graph = nullptr;
-    int graph_steps = 0;
-    std::string err;
-    void *kstep = nullptr;  // the step kernel picked for the observable shape
-
-    // kernel timing (m2m_set_timing)
-    bool timing = false;
-    std::vector<cudaEvent_t> events;  // three per timed step
-    size_t timed = 0;
-};
-
-static thread_local std::string g_create_error;
-
-static m2m_status fail(m2m_ctx *c, m2m_status s, const char *fmt, ...)
+m2m_status fail(m2m_ctx *c, m2m_status s, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -82,13 +33,10 @@ static m2m_status fail(m2m_ctx *c, m2m_status s, const char *fmt, ...)
     return s;
 }
 
-#define CU(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess)                                                                     \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? M2M_ERR_OOM : M2M_ERR_CUDA,       \
-                        "%s: %s", #call, cudaGetErrorString(e_));                                  \
-    } while (0)
+static m2m_status not_a_fit(m2m_ctx *ctx)
+{
+    return fail(ctx, M2M_ERR_STATE, "a batch context: per-fit calls take a fit handle from m2m_batch_model");
+}
 
 static double pow2_floor(double x)
 {
@@ -108,13 +56,6 @@ static uint64_t fnv(uint64_t h, const void *p, size_t n)
 }
 
 static bool is_gh(int kind) { return kind >= kKindGH0 && kind <= kKindGH0 + 6; }
-
-template <class T>
-static void free_dev(T *&p)
-{
-    if (p) cudaFree(p);
-    p = nullptr;
-}
 
 static void free_state(m2m_ctx *c)
 {
@@ -366,24 +307,9 @@ struct StepKernel {
     using Fn = void (*)(const Model, const Cst<T>, const State<T>, const Buffers, int, int);
 };
 
-// Resident blocks per SM the kernels are compiled for (register budget).
-template <class T>
-constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
 
 template <class T, int WPS, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
 static typename StepKernel<T>::Fn step_fn() { return k_step<T, WPS, kMinBlocks<T>, GA, M0, M1, M2, M3>; }
-
-static unsigned group_mask(const GroupDesc &G)
-{
-    unsigned mk = 0;
-    if (G.k_mass >= 0) mk |= kBitMass;
-    if (G.k_v2 >= 0) mk |= kBitV2;
-    if (G.k_v1 >= 0) mk |= kBitV1;
-    for (int n = 0; n < 7; ++n)
-        if (G.k_gh[n] >= 0) mk |= bit_gh(n);
-    if (G.geometry == 1) mk |= kBitPix;
-    return mk;
-}
 
 template <class T, int WPS, bool GA>
 static typename StepKernel<T>::Fn pick_step(const Model &m)
@@ -488,8 +414,8 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     return M2M_OK;
 }
 
-static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs,
-                              const m2m_prior_grid *pg, double eps, double mu, double alpha,
+m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs,
+                       const m2m_prior_grid *pg, double eps, double mu, double alpha,
                               const m2m_options *opt, int internal, m2m_ctx **out)
 {
     if (!out) return fail(nullptr, M2M_ERR_ARG, "out is null");
@@ -529,16 +455,8 @@ static m2m_status create_impl(const m2m_potential *pot, const m2m_observables *o
         }
     }
     if (s == M2M_OK) {
-        double h[7][7];
-        herm_table(h);
-        cudaError_t e = cudaMemcpyToSymbol(kHerm, h, sizeof h);
-        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "Hermite table: %s", cudaGetErrorString(e));
-    }
-    if (s == M2M_OK) {
-        double t[32];
-        exp2_table(t);
-        cudaError_t e = cudaMemcpyToSymbol(kExp2j, t, sizeof t);
-        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "exp table: %s", cudaGetErrorString(e));
+        cudaError_t e = upload_constants();
+        if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "constant tables: %s", cudaGetErrorString(e));
     }
     if (s == M2M_OK) s = upload_tables(ctx);
     if (s != M2M_OK) {
@@ -559,26 +477,15 @@ extern "C" m2m_status m2m_create(const m2m_potential *pot, const m2m_observables
 
 // ------------------------------------------------------------------ launches
 
-static Buffers buffers(m2m_ctx *c)
+Buffers buffers(m2m_ctx *c)
 {
     Buffers b;
     b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
-    b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior; b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior;
+    b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
-}
-
-template <class T>
-static State<T> state(m2m_ctx *c)
-{
-    State<T> s;
-    s.x = (T *)c->st[0]; s.y = (T *)c->st[1]; s.z = (T *)c->st[2];
-    s.vx = (T *)c->st[3]; s.vy = (T *)c->st[4]; s.vz = (T *)c->st[5]; s.w = (T *)c->st[6];
-    s.ax = (T *)c->st[7]; s.ay = (T *)c->st[8]; s.az = (T *)c->st[9];
-    s.cell = c->cell;
-    s.n = c->n;
-    return s;
 }
 
 static int grid_for(m2m_ctx *c)
@@ -696,7 +603,9 @@ static m2m_status load_common(m2m_ctx *ctx, int64_t n, const double *pos, const 
                               const double *w, bool device)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (n < 0 || (n > 0 && (!pos || !vel || !w))) return fail(ctx, M2M_ERR_ARG, "n >= 0 and non-null arrays required");
+    ++ctx->load_gen;
     if (n > 0x7fffffffll * 64) return fail(ctx, M2M_ERR_ARG, "too many particles");
     ctx->loaded = false;
     m2m_status s = ensure_capacity(ctx, n);
@@ -778,6 +687,7 @@ static m2m_status build_graph(m2m_ctx *ctx)
 extern "C" m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return batch_step(ctx, nsteps);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (nsteps < 0) return fail(ctx, M2M_ERR_ARG, "nsteps must be >= 0");
     if (ctx->timing) {
@@ -809,7 +719,7 @@ extern "C" m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps)
     return M2M_OK;
 }
 
-static m2m_status check_device_errors(m2m_ctx *ctx)
+m2m_status check_device_errors(m2m_ctx *ctx)
 {
     Scalars sc;
     CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
@@ -824,6 +734,7 @@ static m2m_status check_device_errors(m2m_ctx *ctx)
 extern "C" m2m_status m2m_synchronize(m2m_ctx *ctx)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return batch_synchronize(ctx);
     CU(cudaStreamSynchronize(ctx->stream));
     if (!ctx->loaded) return M2M_OK;
     return check_device_errors(ctx);
@@ -844,6 +755,7 @@ static void launch_materialize(m2m_ctx *c)
 extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (n != ctx->n || (n > 0 && !w)) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count (%lld)", ctx->n);
     if (n == 0) return m2m_synchronize(ctx);
@@ -862,6 +774,7 @@ extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
 extern "C" m2m_status m2m_get_state(m2m_ctx *ctx, double *pos, double *vel, int64_t n)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (n != ctx->n) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count");
     if (n == 0) return m2m_synchronize(ctx);
@@ -886,6 +799,7 @@ extern "C" m2m_status m2m_get_state(m2m_ctx *ctx, double *pos, double *vel, int6
 extern "C" m2m_status m2m_get_observables(m2m_ctx *ctx, double *ytil, double *y, int32_t J)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (J != ctx->m.J) return fail(ctx, M2M_ERR_ARG, "J must be %d", ctx->m.J);
     if (ytil) CU(cudaMemcpyAsync(ytil, ctx->d_ytil, sizeof(double) * J, cudaMemcpyDeviceToHost, ctx->stream));
@@ -896,6 +810,7 @@ extern "C" m2m_status m2m_get_observables(m2m_ctx *ctx, double *ytil, double *y,
 extern "C" m2m_status m2m_get_chi2(m2m_ctx *ctx, double *chi2, int32_t *J, double *delta)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     Scalars sc;
     CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
@@ -909,6 +824,7 @@ extern "C" m2m_status m2m_get_chi2(m2m_ctx *ctx, double *chi2, int32_t *J, doubl
 extern "C" m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *counts, int32_t *cells, int64_t n)
 {
     if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     const int nc = ctx->m.ncell;
     if (grid_mean && nc) CU(cudaMemcpyAsync(grid_mean, ctx->d_prior, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
@@ -926,6 +842,7 @@ extern "C" m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *c
 extern "C" m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t)
 {
     if (!ctx || !t) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     Scalars sc;
     CU(cudaMemcpyAsync(&sc, ctx->d_sc, sizeof sc, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -936,6 +853,7 @@ extern "C" m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t)
 extern "C" m2m_status m2m_get_particle_count(m2m_ctx *ctx, int64_t *n)
 {
     if (!ctx || !n) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     *n = ctx->n;
     return M2M_OK;
 }
@@ -979,6 +897,7 @@ struct CkptHeader {
 extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 {
     if (!ctx || !path) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     m2m_status s = m2m_synchronize(ctx);
     if (s != M2M_OK) return s;
@@ -1032,6 +951,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
 {
     if (!ctx || !path) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
@@ -1053,6 +973,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     if (!ok) return fail(ctx, M2M_ERR_ARG, "%s is truncated", path);
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->loaded = false;
+    ++ctx->load_gen;
     m2m_status s = ensure_capacity(ctx, hd.n);
     if (s != M2M_OK) return s;
     ctx->n = hd.n;
@@ -1304,7 +1225,13 @@ extern "C" const char *m2m_last_error(const m2m_ctx *ctx)
 
 extern "C" void m2m_destroy(m2m_ctx *ctx)
 {
-    if (!ctx) return;
+    if (!ctx || ctx->parent) return;  // a fit of a batch goes with its batch
+    if (!ctx->sub.empty()) batch_destroy(ctx);
+    destroy_impl(ctx);
+}
+
+void destroy_impl(m2m_ctx *ctx)
+{
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
@@ -1369,10 +1296,8 @@ static m2m_status static_scratch(unsigned char **out)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_m2m_scratch);
         if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        double t[32];
-        exp2_table(t);
-        e = cudaMemcpyToSymbol(kExp2j, t, sizeof t);
-        if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "exp table: %s", cudaGetErrorString(e));
+        e = upload_constants();
+        if (e != cudaSuccess) return fail(nullptr, M2M_ERR_CUDA, "constant tables: %s", cudaGetErrorString(e));
         g_static_addr[dev] = p;
     }
     *out = static_cast<unsigned char *>(g_static_addr[dev]);

@@ -797,23 +797,20 @@ struct Total<double> {
     __device__ long long word(int q, double) const { return q == 0 ? hi : lo; }
 };
 
-// Mixed mode: a compensated (Kahan) FP32 sum of the thread's weights, converted to
-// the fixed point once per thread; the order is fixed, so the result is reproducible.
+// Mixed mode: the limbs of every weight summed in registers (each thread handles far
+// fewer than kMaxParticlesPerBlock particles), so the total is the exact integer sum
+// and does not depend on how the particles are spread over threads and blocks.
 template <>
 struct Total<float> {
-    float s = 0.f, c = 0.f;
-    __device__ void add(float v, float)
+    int hi = 0, mid = 0, lo = 0;
+    __device__ void add(float v, float scale)
     {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+        const Limbs l = split(v, scale);
+        hi += l.hi;
+        mid += l.mid;
+        lo += l.lo;
     }
-    __device__ long long word(int, float scale) const
-    {
-        const Limbs l = split(s, scale);
-        return limbs_value(l.hi, l.mid, l.lo);
-    }
+    __device__ long long word(int, float) const { return limbs_value(hi, mid, lo); }
 };
 
 template <int WPS>
@@ -947,7 +944,7 @@ __device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, co
 // recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}. Called by every thread of one block.
 // Coefficient of nu^q in the physicists' H_n, set on the host from the recurrence
 // H_{n+1} = 2 nu H_n - 2 n H_{n-1} (see herm_table).
-__constant__ double kHerm[7][7];
+static __constant__ double kHerm[7][7];  // one copy per translation unit
 
 inline void herm_table(double h[7][7])
 {
@@ -959,7 +956,19 @@ inline void herm_table(double h[7][7])
         for (int q = 0; q < 7; ++q) h[n + 1][q] = (q > 0 ? 2.0 * h[n][q - 1] : 0.0) - 2.0 * n * h[n - 1][q];
 }
 
-__device__ void build_records(const Model &m, const Buffers &b)
+// Sets this translation unit's constant tables (kHerm, kExp2j) on the current device.
+static inline cudaError_t upload_constants()
+{
+    double h[7][7];
+    herm_table(h);
+    cudaError_t e = cudaMemcpyToSymbol(kHerm, h, sizeof h);
+    if (e != cudaSuccess) return e;
+    double t[32];
+    exp2_table(t);
+    return cudaMemcpyToSymbol(kExp2j, t, sizeof t);
+}
+
+static __device__ void build_records(const Model &m, const Buffers &b)
 {
     for (int g = 0; g < m.n_groups; ++g) {
         const GroupDesc &G = m.g[g];
@@ -1115,27 +1124,40 @@ __device__ __forceinline__ void global_add(long long *hist, int slot, float v, f
               static_cast<unsigned long long>(limbs_value(l.hi, l.mid, l.lo)));
 }
 
-template <class T, int WPS, int MINB, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-__global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
-                                                    const Buffers b, int push, int init)
+// Per-step flags of one fit, read from its scalars at the start of the step.
+template <class T>
+struct StepFlags {
+    int pending, prior_step;
+    T wscale, lwscale, iwhat_flat;
+};
+
+template <class T>
+__device__ __forceinline__ StepFlags<T> step_flags(const Model &m, const Scalars &sc, int init)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const Smem<T> S = carve<T>(m, smem, GA ? 0 : 1, GA ? 0 : 1);
-    __shared__ bool am_last;
-
-    const Scalars sc = *b.sc;
+    StepFlags<T> f;
     const long long t = sc.t + 1;
-    const int pending = init ? 0 : sc.pending;
-    const int prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
-    const T wscale = init ? T(1) : T(sc.wscale);
-    const T lwscale = init ? T(0) : T(sc.lwscale);
-    const T iwhat_flat = kLogWeights<T> ? T(sc.lwhat_flat) : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
+    f.pending = init ? 0 : sc.pending;
+    f.prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
+    f.wscale = init ? T(1) : T(sc.wscale);
+    f.lwscale = init ? T(0) : T(sc.lwscale);
+    f.iwhat_flat = kLogWeights<T> ? T(sc.lwhat_flat) : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
+    return f;
+}
 
-    if (!GA) {
-        int *z = static_cast<int *>(S.h);
-        const int nw = int(Acc<T>::bytes(m) / sizeof(int));
-        for (int q = threadIdx.x; q < nw; q += blockDim.x) z[q] = 0;
-    }
+// Zeroes the block sums (block-shared deposit only).
+template <class T, bool GA>
+__device__ __forceinline__ void block_zero(const Model &m, const Smem<T> &S)
+{
+    if (GA) return;
+    int *z = static_cast<int *>(S.h);
+    const int nw = int(Acc<T>::bytes(m) / sizeof(int));
+    for (int q = threadIdx.x; q < nw; q += blockDim.x) z[q] = 0;
+}
+
+// Copies a fit's records, priors and aperture tables into shared memory.
+template <class T, bool GA>
+__device__ __forceinline__ void block_tables(const Model &m, const Buffers &b, const Smem<T> &S, int pending)
+{
     if (pending) {
         if (!GA)
             for (int q = threadIdx.x; q < m.n_ap_total * m.rec_len; q += blockDim.x) S.c[q] = global_records<T>(b)[q];
@@ -1145,33 +1167,37 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         }
     }
     load_tables(m, b, S);
-    __syncthreads();
+}
+
+// The per-particle part of one step for particles i0, i0 + stride, ... below i1:
+// the pending force of change, the push, the deposit, the prior binning, and the
+// write-back of the state.
+template <class T, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+__device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, const State<T> &P, const Buffers &b,
+                                               const Smem<T> &S, const StepFlags<T> &f, int push, long long i0,
+                                               long long i1, long long stride, unsigned &err, Total<T> &wtot, T &wdep)
+{
     const Tables<T> tb{S.esq, S.lut, S.vp, S.isp, S.e2};
     const T *rec = GA ? global_records<T>(b) : S.c;
     auto deposit = [&](int slot, T v, T scale) {
         if constexpr (GA) global_add(b.hist, slot, v, scale);
         else Acc<T>::add(S.h, m, slot, v, scale);
     };
-
-    unsigned err = 0;
-    Total<T> wtot;
-    T wdep = T(0);  // floating-point twin of wtot, for the fixed-point range check
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    for (long long i = i0; i < i1; i += stride) {
         T x = P.x[i], y = P.y[i], z = P.z[i];
         T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
         T w, u;
         if constexpr (kLogWeights<T>) {
-            u = P.w[i] + lwscale;
-            if (pending) {
-                const T lp = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
+            u = P.w[i] + f.lwscale;
+            if (f.pending) {
+                const T lp = m.mode == 1 ? S.iprior[P.cell[i]] : f.iwhat_flat;
                 u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, lp, u, x, y, z, vy, vz, err);
             }
             w = kexp(tb, u);
         } else {
-            w = P.w[i] * wscale;
-            if (pending) {
-                const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : iwhat_flat;
+            w = P.w[i] * f.wscale;
+            if (f.pending) {
+                const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : f.iwhat_flat;
                 w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, pr, w, x, y, z, vy, vz, err);
             }
             u = w;
@@ -1206,7 +1232,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
             wtot.add(w, k.fx_w);
             wdep += w;
         }
-        if (prior_step) {
+        if (f.prior_step) {
             const int c = prior_cell(m, k, b.lcE, x, y, z, vx, vy, vz);
             deposit(m.J + 1 + c, w, k.fx_w);
             if constexpr (GA) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + m.off_count + c), 1ull);
@@ -1217,6 +1243,14 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         P.vx[i] = vx; P.vy[i] = vy; P.vz[i] = vz;
         P.w[i] = u;
     }
+}
+
+// Adds the block's sums, its total weight and its error bits to the fit's global
+// sums and scalars. Called by every thread of the block.
+template <class T, int WPS, bool GA>
+__device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, const Buffers &b, const Smem<T> &S,
+                                            int prior_step, unsigned err, const Total<T> &wtot, T wdep)
+{
     if (err) atomicOr(&b.sc->err, err);
     // the total weight went into registers: one global atomic per warp and word
 #pragma unroll
@@ -1235,14 +1269,116 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
         const long long v = Acc<T>::word(S.h, m, q);
         if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + q), static_cast<unsigned long long>(v));
     }
-    // last block to finish runs the finalize
     __threadfence();
     __syncthreads();
+}
+
+template <class T, int WPS, int MINB, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+__global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
+                                                    const Buffers b, int push, int init)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Smem<T> S = carve<T>(m, smem, GA ? 0 : 1, GA ? 0 : 1);
+    __shared__ bool am_last;
+
+    const StepFlags<T> f = step_flags<T>(m, *b.sc, init);
+    block_zero<T, GA>(m, S);
+    block_tables<T, GA>(m, b, S, f.pending);
+    __syncthreads();
+
+    unsigned err = 0;
+    Total<T> wtot;
+    T wdep = T(0);  // floating-point twin of wtot, for the fixed-point range check
+    step_particles<T, GA, M0, M1, M2, M3>(m, k, P, b, S, f, push, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+                                          P.n, (long long)gridDim.x * blockDim.x, err, wtot, wdep);
+    block_flush<T, WPS, GA>(m, k, b, S, f.prior_step, err, wtot, wdep);
+    // last block to finish runs the finalize
     if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (am_last) {
         __threadfence();
-        finalize_block<WPS>(m, b, P.n, init, prior_step, reinterpret_cast<double *>(smem));
+        finalize_block<WPS>(m, b, P.n, init, f.prior_step, reinterpret_cast<double *>(smem));
+    }
+}
+
+// ---------------------------------------------------------------- batched step kernel
+//
+// Many independent fits (their own potential, targets, priors and particle counts)
+// advanced by one launch. The host cuts the fits' particles, taken in model order,
+// into equal contiguous shares, one per block, and each share into segments
+// (model, begin, end) of at most kMaxParticlesPerBlock particles. A block walks its
+// segments: on a new model it loads the model's descriptors and tables into shared
+// memory, it runs the per-particle step over the segment, and it flushes its sums
+// into the model's global sums. The block that flushes a model's last segment runs
+// that model's finalize. The sums are exact integers, so a fit advanced in a batch
+// gives bit-identical results to the same fit advanced alone.
+struct Segment {
+    int model;
+    int pad;
+    long long begin, end;
+};
+
+template <class T>
+struct BatchArgs {
+    const Model *models;
+    const Cst<T> *csts;
+    const State<T> *states;
+    const Buffers *bufs;
+    const Segment *seg;
+    const int *seg_off;      // block b walks seg[seg_off[b] .. seg_off[b+1])
+    const unsigned *nseg;    // per model: its number of segments
+};
+
+template <class T, int WPS, int MINB, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+__global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(16) unsigned long long mbuf[(sizeof(Model) + 7) / 8];
+    __shared__ __align__(16) unsigned long long kbuf[(sizeof(Cst<T>) + 7) / 8];
+    __shared__ Buffers sb;
+    __shared__ State<T> sP;
+    __shared__ bool am_last;
+    const Model &m = *reinterpret_cast<const Model *>(mbuf);
+    const Cst<T> &k = *reinterpret_cast<const Cst<T> *>(kbuf);
+
+    int cur = -1;
+    const int s1 = a.seg_off[blockIdx.x + 1];
+    for (int s = a.seg_off[blockIdx.x]; s < s1; ++s) {
+        const Segment sg = a.seg[s];
+        const bool fresh = sg.model != cur;
+        if (fresh) {
+            __syncthreads();
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(a.models + sg.model);
+            for (int q = threadIdx.x; q < int(sizeof(mbuf) / 8); q += blockDim.x) mbuf[q] = src[q];
+            const unsigned long long *ks = reinterpret_cast<const unsigned long long *>(a.csts + sg.model);
+            for (int q = threadIdx.x; q < int(sizeof(kbuf) / 8); q += blockDim.x) kbuf[q] = ks[q];
+            if (threadIdx.x == 0) {
+                sb = a.bufs[sg.model];
+                sP = a.states[sg.model];
+            }
+            __syncthreads();
+            cur = sg.model;
+        }
+        const Buffers &b = sb;
+        const State<T> P = sP;
+        const Smem<T> S = carve<T>(m, smem, 1, 1);
+        const StepFlags<T> f = step_flags<T>(m, *b.sc, 0);
+        block_zero<T, false>(m, S);
+        if (fresh) block_tables<T, false>(m, b, S, f.pending);
+        __syncthreads();
+        unsigned err = 0;
+        Total<T> wtot;
+        T wdep = T(0);
+        step_particles<T, false, M0, M1, M2, M3>(m, k, P, b, S, f, 1, sg.begin + threadIdx.x, sg.end, blockDim.x,
+                                                 err, wtot, wdep);
+        block_flush<T, WPS, false>(m, k, b, S, f.prior_step, err, wtot, wdep);
+        if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == a.nseg[cur] - 1;
+        __syncthreads();
+        if (am_last) {
+            __threadfence();
+            finalize_block<WPS>(m, b, P.n, 0, f.prior_step, reinterpret_cast<double *>(smem));
+            cur = -1;  // the finalize used the shared memory: reload before the next segment
+        }
     }
 }
 
@@ -1298,7 +1434,7 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
     }
 }
 
-__global__ void k_scale(double *out, long long n, const long long *acc, const Model m, const Scalars *sc)
+static __global__ void k_scale(double *out, long long n, const long long *acc, const Model m, const Scalars *sc)
 {
     const double U = (double(acc[0]) + double(acc[1]) * (1.0 / 4294967296.0)) / m.fx_w;
     if (!sc->pending || !m.renormalize || !(U > 0.0)) return;
@@ -1315,7 +1451,7 @@ __global__ void k_convert_in(const double *src, T *dst, long long n)
 }
 
 // FP64 mode stores ln w (w = 0 gives -inf; load rejects negative weights first).
-__global__ void k_log_in(const double *src, double *dst, long long n)
+static __global__ void k_log_in(const double *src, double *dst, long long n)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = log(src[i]);
@@ -1330,7 +1466,7 @@ __global__ void k_convert_out(const T *src, double *dst, long long n)
 
 // Largest v^2 a particle can reach in the fixed potential (2 (E - phi_min)), and a
 // flag for non-finite input or negative weights.
-__global__ void k_load_stats(const Model m, const Cst<double> k, const double *x, const double *y,
+static __global__ void k_load_stats(const Model m, const Cst<double> k, const double *x, const double *y,
                              const double *z, const double *vx, const double *vy, const double *vz,
                              const double *w, long long n, unsigned long long *v2max_bits, unsigned *bad)
 {

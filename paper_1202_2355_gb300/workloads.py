@@ -19,6 +19,14 @@ Workloads (G = M = a = 1 units):
   c4  mixed, flattened log potential (v0 = r0 = 1, q = 0.8) seen at i = 60 deg,
       N = 8,000,000; 64 x 64 pixel maps over [-4, 4]^2 of mass and h1..h4
       (2 %, 0.02); signed-Lz grid 40 x 20, linear in exp(E); eps 1e-6; 5,000 steps.
+  c5  mixed batch of 96 independent fits (make_batch): N log-uniform in
+      [50,000, 2,000,000]; each a Hernquist + NFW potential with r_s uniform in
+      [2, 20] and halo mass M200/M uniform in [1, 30] (c = 10); sigma_r/sigma_t
+      uniform in [0.7, 1.5]; target a 200,000-particle isotropic realisation in the
+      fit's own potential (seed 1000 + fit); the c2 observable set (J = 150) and
+      50 x 20 grid; dt 0.01, 3,000 steps. The per-fit draws come from stream 5 of
+      seed 1 (four uniforms per fit: N, r_s, M200/M, anisotropy); models use seed
+      2000 + fit.
 """
 from __future__ import annotations
 
@@ -177,4 +185,44 @@ def subset(p: dict, n: int) -> dict:
     """First n particles of a realisation, weights rescaled to keep the total."""
     out = {k: np.ascontiguousarray(v[:n]) for k, v in p.items()}
     out["w"] = out["w"] * (p["w"].sum() / out["w"].sum())
+    return out
+
+
+def _c2_groups():
+    return [Group("annuli", ["mass"], [0.01], edges=_logspace(0.05, 20.0, 60)),
+            Group("annuli", ["v2", "gh3", "gh4"], [0.01, 0.01, 0.01], edges=_logspace(0.1, 8.0, 30))]
+
+
+def batch_draws(nfits: int = 96, seed: int = 1):
+    """Per-fit (N, r_s, M200/M, sigma_r/sigma_t) of the c5 batch."""
+    u = synth.uniform(seed, 5, 4 * nfits).reshape(nfits, 4)
+    n = np.exp(math.log(5e4) + u[:, 0] * math.log(2e6 / 5e4)).astype(np.int64)
+    return n, 2.0 + 18.0 * u[:, 1], 1.0 + 29.0 * u[:, 2], 0.7 + 0.8 * u[:, 3]
+
+
+def make_batch(name: str = "c5", nfits: int = 96, n_scale: float = 1.0, n_target: int | None = None,
+               steps: int | None = None, fits=None) -> list:
+    """The fits of a batch workload (only c5), as Workloads. n_scale multiplies
+    every particle count (smaller test batches); fits selects a subset by index."""
+    if name.lower() != "c5":
+        raise ValueError(f"unknown batch workload {name!r}")
+    n_all, rs_all, mh_all, ani_all = batch_draws(nfits)
+    out = []
+    for i in (range(nfits) if fits is None else fits):
+        rs, mh = float(rs_all[i]), float(mh_all[i])
+        ms = synth.nfw_ms_from_m200(mh, 10.0)
+        pot = dict(kind="hernquist_nfw", G=1.0, M=1.0, a=1.0, Ms=ms, rs=rs, v0=0.0, r0=1.0, q=1.0)
+        wl = Workload(
+            name=f"c5_fit{i:02d}", precision="mixed", n=max(1, int(n_all[i] * n_scale)), steps=steps or 3_000,
+            potential=pot, incl_deg=0.0, groups=_c2_groups(),
+            prior=dict(mode="mpr", nE=50, nx=20, e_spacing="logneg", signed_lz=0,
+                       Emin=-1.0 - ms / rs, Emax=-1.0 / 51.0 - ms * math.log1p(50.0 / rs) / 50.0,
+                       update_every=25),
+            params=_params(0.01))
+        tab = synth.jeans_sigma2_table(synth.hernquist_density,
+                                       lambda r, ms=ms, rs=rs: synth.hernquist_mass(r) + synth.nfw_mass(r, ms, rs))
+        s2 = lambda r, tab=tab: synth.sigma2_from_table(tab, r)  # noqa: E731
+        wl.model = synth.realise_spherical(2000 + i, wl.n, s2, anisotropy=float(ani_all[i]))
+        wl.target = synth.realise_spherical(1000 + i, n_target or 200_000, s2)
+        out.append(wl)
     return out
