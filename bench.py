@@ -351,7 +351,7 @@ def run_batch(args):
             "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+i64", "data": "synthetic",
             "config": {"workload": "c5_batch96_hernquist_nfw_mixed", "fits": len(wls), "n_particles": ntot,
-                       "observables_per_fit": wls[0].J, "prior_grid": "50x20 every 25", "dt": 0.01,
+                       "observables_per_fit": wls[0].J, "prior_grid": "50x20 every 25", "dt": wls[0].params["dt"],
                        "precision": "mixed", "launch_shape": {"block": shape[0], "blocks_per_sm": shape[1],
                                                               "segment": shape[2]},
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
