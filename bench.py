@@ -53,21 +53,20 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 #          sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over one
 #          step launch / N), including the iterative sqrt, division, log and exp;
 KERNEL_FIGURES = {
-    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B) + prior cell (2 B); write 80 B
-    "fp64": {"bytes": 162, "flops": 180.65},
-    # read 6 coordinates + w (28 B) + prior cell (2 B); write 28 B
-    "mixed": {"bytes": 58, "flops": None},
+    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B), prior cell and cached
+    # apertures (2 + 2 B); write 80 B + 2 B of apertures
+    "fp64": {"bytes": 166, "flops": None},
+    # read 6 coordinates + w (28 B), prior cell and cached apertures (2 + 2 B);
+    # write 28 B + 2 B of apertures
+    "mixed": {"bytes": 62, "flops": None},
 }
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one step launch / N, from an ncu
 # capture of the kernel as it stands, by (workload, precision): (bytes per unit, N of
-# the capture); absent: not captured. Reads equal the algorithmic reads; most of a
-# step's writes are still in the 129 MB L2 when the kernel ends (written back during
-# the next launch or the L2 flush), so the write count is below the algorithmic one.
-DRAM_PER_UNIT = {
-    ("c2", "fp64"): (101.2, 1_000_000),
-    ("c2", "mixed"): (30.1, 1_000_000),
-}
+# the capture); absent: not captured. Most of a step's writes are still in the
+# 129 MB L2 when the kernel ends (written back during the next launch or the L2
+# flush), so the write count is below the algorithmic one.
+DRAM_PER_UNIT = {}
 
 
 class ClockSampler:

@@ -61,6 +61,7 @@ static void free_state(m2m_ctx *c)
 {
     for (auto &p : c->st) free_dev(p);
     free_dev(c->cell);
+    free_dev(c->ap);
     free_dev(c->d_wout);
     c->capacity = 0;
     c->wout_cap = 0;
@@ -283,6 +284,10 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.wps = ctx->precision == M2M_PREC_FP64 ? 2 : 1;
     m.off_total = m.J * m.wps;
     m.off_grid = (m.J + 1) * m.wps;
+    // aperture cache: one 16-bit code per particle (two small groups or one group)
+    m.ap_cache = 0;
+    if (m.n_groups == 1 && m.g[0].n_ap < int(kApNone16)) m.ap_cache = 2;
+    else if (m.n_groups == 2 && m.g[0].n_ap < int(kApNone8) && m.g[1].n_ap < int(kApNone8)) m.ap_cache = 1;
     m.off_count = (m.J + 1 + m.ncell) * m.wps;
     m.hist_words = m.off_count + m.ncell;
 
@@ -533,6 +538,7 @@ static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
     for (int k = 0; k < narr; ++k) CU(cudaMalloc(&ctx->st[k], cap * elem_size(ctx)));
     CU(cudaMalloc(&ctx->cell, cap * sizeof(uint16_t)));
+    if (ctx->m.ap_cache) CU(cudaMalloc(&ctx->ap, cap * sizeof(uint16_t)));
     ctx->capacity = cap;
     return M2M_OK;
 }
@@ -904,7 +910,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const Model &m = ctx->m;
     CkptHeader hd{};
     std::memcpy(hd.magic, "M2MSTATE", 8);
-    hd.version = 2;
+    hd.version = 3;
     hd.precision = ctx->precision;
     hd.config_hash = ctx->config_hash;
     hd.n = ctx->n;
@@ -913,8 +919,10 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
-    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) +
-                          8 * m.ncell + sizeof(Scalars));
+    const size_t apb = m.ap_cache ? 2 * n : 0;
+    std::vector<char> buf(es * n * narr + 2 * n + apb +
+                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
+                          sizeof(Scalars));
     char *p = buf.data();
     for (int k = 0; k < narr; ++k) {
         if (n) CU(cudaMemcpy(p, ctx->st[k], es * n, cudaMemcpyDeviceToHost));
@@ -922,6 +930,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     }
     if (n) CU(cudaMemcpy(p, ctx->cell, 2 * n, cudaMemcpyDeviceToHost));
     p += 2 * n;
+    if (n && apb) CU(cudaMemcpy(p, ctx->ap, apb, cudaMemcpyDeviceToHost));
+    p += apb;
     double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
     for (auto d : dv) {
         CU(cudaMemcpy(p, d, sizeof(double) * m.J, cudaMemcpyDeviceToHost));
@@ -955,7 +965,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 2) {
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 3) {
         std::fclose(f);
         return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
     }
@@ -966,8 +976,10 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
-    std::vector<char> buf(es * n * narr + 2 * n + sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) +
-                          8 * m.ncell + sizeof(Scalars));
+    const size_t apb = m.ap_cache ? 2 * n : 0;
+    std::vector<char> buf(es * n * narr + 2 * n + apb +
+                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
+                          sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
     if (!ok) return fail(ctx, M2M_ERR_ARG, "%s is truncated", path);
@@ -991,6 +1003,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     }
     if (n) CU(cudaMemcpy(ctx->cell, p, 2 * n, cudaMemcpyHostToDevice));
     p += 2 * n;
+    if (n && apb) CU(cudaMemcpy(ctx->ap, p, apb, cudaMemcpyHostToDevice));
+    p += apb;
     double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
     for (auto d : dv) {
         CU(cudaMemcpy(d, p, sizeof(double) * m.J, cudaMemcpyHostToDevice));

@@ -35,6 +35,7 @@ struct m2m_ctx {
     long long capacity = 0;
     void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and in FP64 mode ax, ay, az
     uint16_t *cell = nullptr;
+    uint16_t *ap = nullptr;  // cached apertures (Model::ap_cache)
     double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
     unsigned short *d_lut = nullptr;
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
@@ -103,13 +104,14 @@ inline m2m::State<T> state(m2m_ctx *c)
     s.vx = (T *)c->st[3]; s.vy = (T *)c->st[4]; s.vz = (T *)c->st[5]; s.w = (T *)c->st[6];
     s.ax = (T *)c->st[7]; s.ay = (T *)c->st[8]; s.az = (T *)c->st[9];
     s.cell = c->cell;
+    s.ap = c->ap;
     s.n = c->n;
     return s;
 }
 
 // Resident blocks per SM the step kernels are compiled for (register budget).
 template <class T>
-constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
+constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 5;
 
 // Compile-time shape bits of a group (see m2m::GP), for picking a specialised kernel.
 inline unsigned group_mask(const m2m::GroupDesc &G)

@@ -75,7 +75,14 @@ struct Model {
     int wps;                      // int64 words per sum in the global sums
     int hist_words, off_total, off_grid, off_count;
     int rec_len;                  // doubles per aperture record of the force of change
+    // aperture cache: the deposit of a step stores each particle's apertures for the
+    // force of change at the start of the next (same positions): 0 none, 1 two groups
+    // of at most 255 apertures (8 bits each), 2 one group (16 bits)
+    int ap_cache;
 };
+
+constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
+constexpr unsigned kApUncached = 0xFFFFFFFFu;  // no cached code: locate the apertures
 
 // Compile-time shape of an observable group, for step kernels specialised to a
 // configuration: bits for the kernels it deposits and its geometry. kDyn: read the
@@ -186,6 +193,7 @@ struct State {
     T *x, *y, *z, *vx, *vy, *vz, *w;
     T *ax, *ay, *az;  // FP64 mode: acceleration at the current positions (null in mixed mode)
     uint16_t *cell;
+    uint16_t *ap;     // cached apertures (Model::ap_cache), null without the cache
     long long n;
 };
 
@@ -523,6 +531,25 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
 // one record per aperture, r = [V_p, 1/sigma_p, q0, q1, q2, p0 .. p_nmax], and
 // sum_j K_j c_j = q0 + q1 nu + q2 nu^2 + exp(-nu^2/2) sum_n p_n nu^n
 // (groups without Gauss-Hermite kernels use V = 0, 1/sigma = 1, i.e. nu = v_los).
+template <unsigned M, class T>
+__device__ __forceinline__ T group_data(const Model &m, const GroupDesc &G, const Tables<T> &tb, const T *rec, int p,
+                                        T vlos)
+{
+    const T *r = rec + (G.ap_off + p) * m.rec_len;
+    const int nmax = GP<M>::max_gh(G);
+    if (!GP<M>::v2(G) && !GP<M>::v1(G) && nmax < 0) return r[2];  // surface mass only: a constant
+    const T nu = (vlos - r[0]) * r[1];
+    T d = r[2] + nu * (r[3] + nu * r[4]);
+    if (nmax >= 0) {
+        T poly = T(0);
+#pragma unroll
+        for (int n = 6; n >= 0; --n)
+            if (n <= nmax) poly = poly * nu + r[5 + n];
+        d += kexp(tb, T(-0.5) * nu * nu) * poly;
+    }
+    return d;
+}
+
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, const T *rec, T X, T Y, T vlos)
 {
@@ -531,20 +558,35 @@ __device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, cons
         constexpr unsigned M = decltype(P)::mask;
         const GroupDesc &G = m.g[g];
         const int p = aperture<M>(G, tb.esq, tb.lut, X, Y);
-        if (p >= 0) {
-            const T *r = rec + (G.ap_off + p) * m.rec_len;
-            const T nu = (vlos - r[0]) * r[1];
-            T d = r[2] + nu * (r[3] + nu * r[4]);
-            const int nmax = GP<M>::max_gh(G);
-            if (nmax >= 0) {
-                T poly = T(0);
-#pragma unroll
-                for (int n = 6; n >= 0; --n)
-                    if (n <= nmax) poly = poly * nu + r[5 + n];
-                d += kexp(tb, T(-0.5) * nu * nu) * poly;
-            }
-            data += d;
-        }
+        if (p >= 0) data += group_data<M>(m, G, tb, rec, p, vlos);
+    });
+    return data;
+}
+
+// Aperture of group g in a cached code (Model::ap_cache), -1 outside.
+__device__ __forceinline__ int ap_decode(const Model &m, unsigned code, int g)
+{
+    if (m.ap_cache == 2) return code == kApNone16 ? -1 : int(code);
+    const unsigned a = (code >> (8 * g)) & 0xFFu;
+    return a == kApNone8 ? -1 : int(a);
+}
+
+__device__ __forceinline__ unsigned ap_encode(const Model &m, unsigned code, int g, int p)
+{
+    if (m.ap_cache == 2) return p < 0 ? kApNone16 : unsigned(p);
+    return (code & ~(0xFFu << (8 * g))) | ((p < 0 ? kApNone8 : unsigned(p)) << (8 * g));
+}
+
+// data_term with the apertures taken from a cached code.
+template <unsigned... Ms, class T>
+__device__ __forceinline__ T data_term_cached(const Model &m, const Tables<T> &tb, const T *rec, unsigned code,
+                                              T vlos)
+{
+    T data = T(0);
+    each_group<0, Ms...>(m, [&](auto P, int g) {
+        constexpr unsigned M = decltype(P)::mask;
+        const int p = ap_decode(m, code, g);
+        if (p >= 0) data += group_data<M>(m, m.g[g], tb, rec, p, vlos);
     });
     return data;
 }
@@ -822,18 +864,28 @@ __device__ __forceinline__ double fx_read(const long long *h, int slot)
 
 // ---------------------------------------------------------------- force of change
 
+// The data term sum_j K_j c_j at the particle's position, with the apertures from
+// the cached code of the last deposit when there is one.
+template <unsigned... Ms, class T>
+__device__ __forceinline__ T foc_data(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
+                                      unsigned code, T x, T y, T z, T vy, T vz)
+{
+    T Y, vlos;
+    project(k, y, z, vy, vz, Y, vlos);
+    if (code != kApUncached) return data_term_cached<Ms...>(m, tb, rec, code, vlos);
+    return data_term<Ms...>(m, tb, rec, x, Y, vlos);
+}
+
 // Weight after the force of change of eq. modFOC over one step, the kernel
 // values taken at the particle's current position and the priors held fixed:
 // F = mu dS/dw - sum_j K_j c_j, c_j = Delta_j/sigma_j (times 1/area for mass),
 // dS/dw = -ln(w/what) (eq. S+) or -ln(w/what) - 1 (eq. entropy).
 template <unsigned... Ms, class T>
-__device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec, T iprior,
-                                        T w, T x, T y, T z, T vy, T vz, unsigned &err)
+__device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
+                                        unsigned code, T iprior, T w, T x, T y, T z, T vy, T vz, unsigned &err)
 {
     if (w == T(0)) return w;  // w = 0 is a fixed point
-    T Y, vlos;
-    project(k, y, z, vy, vz, Y, vlos);
-    const T data = data_term<Ms...>(m, tb, rec, x, Y, vlos);
+    const T data = foc_data<Ms...>(m, k, tb, rec, code, x, y, z, vy, vz);
     // A cell mean below the resolution of the fixed-point cell sums reads as 0
     // (iprior = 0); the particle's weight is then unresolved too and the entropy
     // term is dropped.
@@ -852,12 +904,10 @@ __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const T
 // u + ln(1 + eps dt F) for explicit Euler, with dS/dw = ln(what) - u.
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
-                                            T lprior, T u, T x, T y, T z, T vy, T vz, unsigned &err)
+                                            unsigned code, T lprior, T u, T x, T y, T z, T vy, T vz, unsigned &err)
 {
     if (u == -HUGE_VAL) return u;  // w = 0 is a fixed point
-    T Y, vlos;
-    project(k, y, z, vy, vz, Y, vlos);
-    const T data = data_term<Ms...>(m, tb, rec, x, Y, vlos);
+    const T data = foc_data<Ms...>(m, k, tb, rec, code, x, y, z, vy, vz);
     // a prior that reads 0 (below the resolution of the cell sums) drops the entropy term
     T dS = lprior > -HUGE_VAL ? lprior - u : T(0);
     if (m.mode == 0) dS -= T(1);
@@ -1183,22 +1233,41 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         if constexpr (GA) global_add(b.hist, slot, v, scale);
         else Acc<T>::add(S.h, m, slot, v, scale);
     };
+    // the next particle's state is loaded while the current one is processed
+    const bool need_cell = f.pending && m.mode == 1;
+    const bool cache = m.ap_cache != 0;
+    const bool need_ap = cache && f.pending;
+    T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0);
+    int ncell = 0;
+    unsigned nap = kApUncached;
+    auto fetch = [&](long long j) {
+        nx = P.x[j]; ny = P.y[j]; nz = P.z[j];
+        nvx = P.vx[j]; nvy = P.vy[j]; nvz = P.vz[j];
+        nw = P.w[j];
+        if (need_cell) ncell = P.cell[j];
+        if (need_ap) nap = P.ap[j];
+    };
+    if (i0 < i1) fetch(i0);
     for (long long i = i0; i < i1; i += stride) {
-        T x = P.x[i], y = P.y[i], z = P.z[i];
-        T vx = P.vx[i], vy = P.vy[i], vz = P.vz[i];
+        T x = nx, y = ny, z = nz;
+        T vx = nvx, vy = nvy, vz = nvz;
+        const T wst = nw;
+        const int cell = ncell;
+        const unsigned code = nap;
+        if (i + stride < i1) fetch(i + stride);
         T w, u;
         if constexpr (kLogWeights<T>) {
-            u = P.w[i] + f.lwscale;
+            u = wst + f.lwscale;
             if (f.pending) {
-                const T lp = m.mode == 1 ? S.iprior[P.cell[i]] : f.iwhat_flat;
-                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, lp, u, x, y, z, vy, vz, err);
+                const T lp = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
+                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, code, lp, u, x, y, z, vy, vz, err);
             }
             w = kexp(tb, u);
         } else {
-            w = P.w[i] * f.wscale;
+            w = wst * f.wscale;
             if (f.pending) {
-                const T pr = m.mode == 1 ? S.iprior[P.cell[i]] : f.iwhat_flat;
-                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, pr, w, x, y, z, vy, vz, err);
+                const T pr = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
+                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, code, pr, w, x, y, z, vy, vz, err);
             }
             u = w;
         }
@@ -1217,10 +1286,12 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         if (w != T(0)) {
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
+            unsigned code_out = 0;
             each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
                 constexpr unsigned M = decltype(Pl)::mask;
                 const GroupDesc &G = m.g[g];
                 const int p = aperture<M>(G, tb.esq, tb.lut, x, Y);
+                if (cache) code_out = ap_encode(m, code_out, g, p);
                 if (p >= 0) {
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
                     if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
@@ -1229,6 +1300,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                     });
                 }
             });
+            if (cache) P.ap[i] = static_cast<uint16_t>(code_out);
             wtot.add(w, k.fx_w);
             wdep += w;
         }
@@ -1409,8 +1481,8 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             T u = P.w[i] + T(sc.lwscale);
             if (sc.pending) {
                 const T lp = (m.mode == 1) ? S.iprior[P.cell[i]] : T(sc.lwhat_flat);
-                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), lp, u, P.x[i], P.y[i],
-                                                           P.z[i], P.vy[i], P.vz[i], err);
+                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached, lp, u, P.x[i],
+                                                           P.y[i], P.z[i], P.vy[i], P.vz[i], err);
             }
             w = kexp(tb, u);
         } else {
@@ -1418,8 +1490,8 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             if (sc.pending) {
                 const T pr =
                     (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
-                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), pr, w, P.x[i], P.y[i],
-                                                       P.z[i], P.vy[i], P.vz[i], err);
+                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached, pr, w, P.x[i],
+                                                       P.y[i], P.z[i], P.vy[i], P.vz[i], err);
             }
         }
         if (sc.pending && w != T(0)) tot.add(double(w), m.fx_w);
