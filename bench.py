@@ -53,9 +53,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 #          sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over one
 #          step launch / N), including the iterative sqrt, division, log and exp;
 KERNEL_FIGURES = {
-    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B), prior cell and cached
-    # apertures (2 + 2 B); write 80 B + 2 B of apertures
-    "fp64": {"bytes": 166, "flops": None},
+    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B), prior cell, cached apertures
+    # and cached exp(-nu^2/2) (2 + 2 + 8 B); write 80 + 2 + 8 B
+    "fp64": {"bytes": 182, "flops": None},
     # read 6 coordinates + w (28 B), prior cell and cached apertures (2 + 2 B);
     # write 28 B + 2 B of apertures
     "mixed": {"bytes": 62, "flops": None},

@@ -35,8 +35,12 @@ __device__ __forceinline__ double exp_tab(double x, const double *e2)
     constexpr double kL1 = 0.021660849392498290;         // ln2/32 rounded to double
     constexpr double kL2 = 7.2470212932696862984e-19;    // ln2/32 - kL1
     constexpr double kShift = 6755399441055744.0;        // 1.5 * 2^52
-    if (!(x > -707.0)) return x != x ? x : 0.0;
-    if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+    // |x| < 707 on the bit pattern (one integer compare); the rest, NaN included,
+    // takes the slow branch
+    if ((__double_as_longlong(x) & 0x7fffffffffffffffll) >= 0x4086180000000000ll) {
+        if (!(x > -707.0)) return x != x ? x : 0.0;
+        if (x > 709.0) return __longlong_as_double(0x7ff0000000000000ll);
+    }
     const double t = fma(x, kInvL, kShift);
     const int N = __double2loint(t);
     const double Nd = t - kShift;

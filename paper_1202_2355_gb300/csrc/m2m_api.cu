@@ -62,6 +62,7 @@ static void free_state(m2m_ctx *c)
     for (auto &p : c->st) free_dev(p);
     free_dev(c->cell);
     free_dev(c->ap);
+    free_dev(c->gx);
     free_dev(c->d_wout);
     c->capacity = 0;
     c->wout_cap = 0;
@@ -288,6 +289,9 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.ap_cache = 0;
     if (m.n_groups == 1 && m.g[0].n_ap < int(kApNone16)) m.ap_cache = 2;
     else if (m.n_groups == 2 && m.g[0].n_ap < int(kApNone8) && m.g[1].n_ap < int(kApNone8)) m.ap_cache = 1;
+    m.gx_group = -1;
+    for (int g = 0; m.ap_cache && m.gx_group < 0 && g < m.n_groups; ++g)
+        if (m.g[g].max_gh >= 0) m.gx_group = g;
     m.off_count = (m.J + 1 + m.ncell) * m.wps;
     m.hist_words = m.off_count + m.ncell;
 
@@ -539,6 +543,7 @@ static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
     for (int k = 0; k < narr; ++k) CU(cudaMalloc(&ctx->st[k], cap * elem_size(ctx)));
     CU(cudaMalloc(&ctx->cell, cap * sizeof(uint16_t)));
     if (ctx->m.ap_cache) CU(cudaMalloc(&ctx->ap, cap * sizeof(uint16_t)));
+    if (ctx->precision == M2M_PREC_FP64 && ctx->m.gx_group >= 0) CU(cudaMalloc(&ctx->gx, cap * sizeof(double)));
     ctx->capacity = cap;
     return M2M_OK;
 }
@@ -910,7 +915,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const Model &m = ctx->m;
     CkptHeader hd{};
     std::memcpy(hd.magic, "M2MSTATE", 8);
-    hd.version = 3;
+    hd.version = 4;
     hd.precision = ctx->precision;
     hd.config_hash = ctx->config_hash;
     hd.n = ctx->n;
@@ -919,8 +924,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
-    const size_t apb = m.ap_cache ? 2 * n : 0;
-    std::vector<char> buf(es * n * narr + 2 * n + apb +
+    const size_t apb = m.ap_cache ? 2 * n : 0, gxb = ctx->gx ? 8 * n : 0;
+    std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +
                           sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
                           sizeof(Scalars));
     char *p = buf.data();
@@ -932,6 +937,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     p += 2 * n;
     if (n && apb) CU(cudaMemcpy(p, ctx->ap, apb, cudaMemcpyDeviceToHost));
     p += apb;
+    if (n && gxb) CU(cudaMemcpy(p, ctx->gx, gxb, cudaMemcpyDeviceToHost));
+    p += gxb;
     double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
     for (auto d : dv) {
         CU(cudaMemcpy(p, d, sizeof(double) * m.J, cudaMemcpyDeviceToHost));
@@ -965,7 +972,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 3) {
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 4) {
         std::fclose(f);
         return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
     }
@@ -977,7 +984,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     const size_t es = elem_size(ctx), n = size_t(hd.n);
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
     const size_t apb = m.ap_cache ? 2 * n : 0;
-    std::vector<char> buf(es * n * narr + 2 * n + apb +
+    const size_t gxb = (ctx->precision == M2M_PREC_FP64 && m.gx_group >= 0) ? 8 * n : 0;
+    std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +
                           sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
                           sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
@@ -1005,6 +1013,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     p += 2 * n;
     if (n && apb) CU(cudaMemcpy(ctx->ap, p, apb, cudaMemcpyHostToDevice));
     p += apb;
+    if (n && gxb) CU(cudaMemcpy(ctx->gx, p, gxb, cudaMemcpyHostToDevice));
+    p += gxb;
     double *dv[4] = {ctx->d_c, ctx->d_ytil, ctx->d_yraw, ctx->d_delta};
     for (auto d : dv) {
         CU(cudaMemcpy(d, p, sizeof(double) * m.J, cudaMemcpyHostToDevice));

@@ -36,6 +36,7 @@ struct m2m_ctx {
     void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and in FP64 mode ax, ay, az
     uint16_t *cell = nullptr;
     uint16_t *ap = nullptr;  // cached apertures (Model::ap_cache)
+    double *gx = nullptr;    // cached exp(-nu^2/2) (Model::gx_group, FP64 mode)
     double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
     unsigned short *d_lut = nullptr;
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
@@ -105,6 +106,7 @@ inline m2m::State<T> state(m2m_ctx *c)
     s.ax = (T *)c->st[7]; s.ay = (T *)c->st[8]; s.az = (T *)c->st[9];
     s.cell = c->cell;
     s.ap = c->ap;
+    s.gx = sizeof(T) == 8 ? reinterpret_cast<T *>(c->gx) : nullptr;
     s.n = c->n;
     return s;
 }

@@ -79,6 +79,10 @@ struct Model {
     // force of change at the start of the next (same positions): 0 none, 1 two groups
     // of at most 255 apertures (8 bits each), 2 one group (16 bits)
     int ap_cache;
+    // FP64 mode with the aperture cache: exp(-nu^2/2) of this group's aperture (the
+    // first group with Gauss-Hermite kernels, -1 none) is also kept from the deposit
+    // for the next force of change (same nu, same value)
+    int gx_group;
 };
 
 constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
@@ -194,6 +198,7 @@ struct State {
     T *ax, *ay, *az;  // FP64 mode: acceleration at the current positions (null in mixed mode)
     uint16_t *cell;
     uint16_t *ap;     // cached apertures (Model::ap_cache), null without the cache
+    T *gx;            // cached exp(-nu^2/2) of Model::gx_group (FP64 mode), else null
     long long n;
 };
 
@@ -499,7 +504,8 @@ __device__ __forceinline__ double kexp(const Tables<double> &tb, double x) { ret
 // recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}, evaluated once up to the group's
 // highest order.
 template <unsigned M, class T, class F>
-__device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T> &tb, int p, T vlos, T w, F &&emit)
+__device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T> &tb, int p, T vlos, T w, F &&emit,
+                                              T *gexp_out = nullptr)
 {
     using P = GP<M>;
     const int base = G.obs_off + p;
@@ -509,7 +515,9 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
     const int nmax = P::max_gh(G);
     if (nmax >= 0) {
         const T nu = (vlos - tb.vp[G.ap_off + p]) * tb.isp[G.ap_off + p];
-        const T we = w * kexp(tb, T(-0.5) * nu * nu);
+        const T ge = kexp(tb, T(-0.5) * nu * nu);
+        if (gexp_out) *gexp_out = ge;
+        const T we = w * ge;
         T hm1 = T(1), h = T(2) * nu;
         if (P::gh(G, 0)) emit(base + G.k_gh[0] * G.n_ap, T(gh_c(0)) * we, kClassGH);
         if (P::gh(G, 1)) emit(base + G.k_gh[1] * G.n_ap, h * we, kClassGH);
@@ -533,7 +541,7 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
 // (groups without Gauss-Hermite kernels use V = 0, 1/sigma = 1, i.e. nu = v_los).
 template <unsigned M, class T>
 __device__ __forceinline__ T group_data(const Model &m, const GroupDesc &G, const Tables<T> &tb, const T *rec, int p,
-                                        T vlos)
+                                        T vlos, const T *gexp = nullptr)
 {
     const T *r = rec + (G.ap_off + p) * m.rec_len;
     const int nmax = GP<M>::max_gh(G);
@@ -545,7 +553,7 @@ __device__ __forceinline__ T group_data(const Model &m, const GroupDesc &G, cons
 #pragma unroll
         for (int n = 6; n >= 0; --n)
             if (n <= nmax) poly = poly * nu + r[5 + n];
-        d += kexp(tb, T(-0.5) * nu * nu) * poly;
+        d += (gexp ? *gexp : kexp(tb, T(-0.5) * nu * nu)) * poly;
     }
     return d;
 }
@@ -580,13 +588,13 @@ __device__ __forceinline__ unsigned ap_encode(const Model &m, unsigned code, int
 // data_term with the apertures taken from a cached code.
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T data_term_cached(const Model &m, const Tables<T> &tb, const T *rec, unsigned code,
-                                              T vlos)
+                                              T vlos, const T *gexp)
 {
     T data = T(0);
     each_group<0, Ms...>(m, [&](auto P, int g) {
         constexpr unsigned M = decltype(P)::mask;
         const int p = ap_decode(m, code, g);
-        if (p >= 0) data += group_data<M>(m, m.g[g], tb, rec, p, vlos);
+        if (p >= 0) data += group_data<M>(m, m.g[g], tb, rec, p, vlos, g == m.gx_group ? gexp : nullptr);
     });
     return data;
 }
@@ -868,11 +876,11 @@ __device__ __forceinline__ double fx_read(const long long *h, int slot)
 // the cached code of the last deposit when there is one.
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T foc_data(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
-                                      unsigned code, T x, T y, T z, T vy, T vz)
+                                      unsigned code, const T *gexp, T x, T y, T z, T vy, T vz)
 {
     T Y, vlos;
     project(k, y, z, vy, vz, Y, vlos);
-    if (code != kApUncached) return data_term_cached<Ms...>(m, tb, rec, code, vlos);
+    if (code != kApUncached) return data_term_cached<Ms...>(m, tb, rec, code, vlos, gexp);
     return data_term<Ms...>(m, tb, rec, x, Y, vlos);
 }
 
@@ -882,10 +890,11 @@ __device__ __forceinline__ T foc_data(const Model &m, const Cst<T> &k, const Tab
 // dS/dw = -ln(w/what) (eq. S+) or -ln(w/what) - 1 (eq. entropy).
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
-                                        unsigned code, T iprior, T w, T x, T y, T z, T vy, T vz, unsigned &err)
+                                        unsigned code, const T *gexp, T iprior, T w, T x, T y, T z, T vy, T vz,
+                                        unsigned &err)
 {
     if (w == T(0)) return w;  // w = 0 is a fixed point
-    const T data = foc_data<Ms...>(m, k, tb, rec, code, x, y, z, vy, vz);
+    const T data = foc_data<Ms...>(m, k, tb, rec, code, gexp, x, y, z, vy, vz);
     // A cell mean below the resolution of the fixed-point cell sums reads as 0
     // (iprior = 0); the particle's weight is then unresolved too and the entropy
     // term is dropped.
@@ -904,10 +913,11 @@ __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const T
 // u + ln(1 + eps dt F) for explicit Euler, with dS/dw = ln(what) - u.
 template <unsigned... Ms, class T>
 __device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, const Tables<T> &tb, const T *rec,
-                                            unsigned code, T lprior, T u, T x, T y, T z, T vy, T vz, unsigned &err)
+                                            unsigned code, const T *gexp, T lprior, T u, T x, T y, T z, T vy, T vz,
+                                            unsigned &err)
 {
     if (u == -HUGE_VAL) return u;  // w = 0 is a fixed point
-    const T data = foc_data<Ms...>(m, k, tb, rec, code, x, y, z, vy, vz);
+    const T data = foc_data<Ms...>(m, k, tb, rec, code, gexp, x, y, z, vy, vz);
     // a prior that reads 0 (below the resolution of the cell sums) drops the entropy term
     T dS = lprior > -HUGE_VAL ? lprior - u : T(0);
     if (m.mode == 0) dS -= T(1);
@@ -1237,7 +1247,8 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
     const bool need_cell = f.pending && m.mode == 1;
     const bool cache = m.ap_cache != 0;
     const bool need_ap = cache && f.pending;
-    T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0);
+    const bool gxc = sizeof(T) == 8 && P.gx != nullptr;  // FP64, aperture cache, a Gauss-Hermite group
+    T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0), ngx = T(0);
     int ncell = 0;
     unsigned nap = kApUncached;
     auto fetch = [&](long long j) {
@@ -1246,6 +1257,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         nw = P.w[j];
         if (need_cell) ncell = P.cell[j];
         if (need_ap) nap = P.ap[j];
+        if (need_ap && gxc) ngx = P.gx[j];
     };
     if (i0 < i1) fetch(i0);
     for (long long i = i0; i < i1; i += stride) {
@@ -1254,20 +1266,22 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         const T wst = nw;
         const int cell = ncell;
         const unsigned code = nap;
+        const T gin = ngx;
+        const T *gp = gxc ? &gin : static_cast<const T *>(nullptr);
         if (i + stride < i1) fetch(i + stride);
         T w, u;
         if constexpr (kLogWeights<T>) {
             u = wst + f.lwscale;
             if (f.pending) {
                 const T lp = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
-                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, code, lp, u, x, y, z, vy, vz, err);
+                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, code, gp, lp, u, x, y, z, vy, vz, err);
             }
             w = kexp(tb, u);
         } else {
             w = wst * f.wscale;
             if (f.pending) {
                 const T pr = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
-                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, code, pr, w, x, y, z, vy, vz, err);
+                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, code, gp, pr, w, x, y, z, vy, vz, err);
             }
             u = w;
         }
@@ -1287,6 +1301,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
             unsigned code_out = 0;
+            T gout = T(0);
             each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
                 constexpr unsigned M = decltype(Pl)::mask;
                 const GroupDesc &G = m.g[g];
@@ -1295,12 +1310,16 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                 if (p >= 0) {
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
                     if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
-                    group_kernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
-                        deposit(j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
-                    });
+                    group_kernels<M>(
+                        G, tb, p, vlos, w,
+                        [&](int j, T v, int cls) {
+                            deposit(j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
+                        },
+                        gxc && g == m.gx_group ? &gout : nullptr);
                 }
             });
             if (cache) P.ap[i] = static_cast<uint16_t>(code_out);
+            if (gxc) P.gx[i] = gout;
             wtot.add(w, k.fx_w);
             wdep += w;
         }
@@ -1481,8 +1500,9 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             T u = P.w[i] + T(sc.lwscale);
             if (sc.pending) {
                 const T lp = (m.mode == 1) ? S.iprior[P.cell[i]] : T(sc.lwhat_flat);
-                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached, lp, u, P.x[i],
-                                                           P.y[i], P.z[i], P.vy[i], P.vz[i], err);
+                u = foc_update_log<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached,
+                                                           static_cast<const T *>(nullptr), lp, u, P.x[i], P.y[i],
+                                                           P.z[i], P.vy[i], P.vz[i], err);
             }
             w = kexp(tb, u);
         } else {
@@ -1490,8 +1510,9 @@ __global__ void k_materialize(const Model m, const Cst<T> k, const State<T> P, c
             if (sc.pending) {
                 const T pr =
                     (m.mode == 1) ? S.iprior[P.cell[i]] : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
-                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached, pr, w, P.x[i],
-                                                       P.y[i], P.z[i], P.vy[i], P.vz[i], err);
+                w = foc_update<kDyn, kDyn, kDyn, kDyn>(m, k, tb, global_records<T>(b), kApUncached,
+                                                       static_cast<const T *>(nullptr), pr, w, P.x[i], P.y[i], P.z[i],
+                                                       P.vy[i], P.vz[i], err);
             }
         }
         if (sc.pending && w != T(0)) tot.add(double(w), m.fx_w);
