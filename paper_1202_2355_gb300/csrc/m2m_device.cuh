@@ -273,6 +273,28 @@ __host__ __device__ __forceinline__ float d_log1p(float x) { return log1pf(x); }
 __host__ __device__ __forceinline__ double d_log1p(double x) { return log1p(x); }
 __host__ __device__ __forceinline__ float d_floor(float x) { return floorf(x); }
 __host__ __device__ __forceinline__ double d_floor(double x) { return floor(x); }
+// Tests the FP64 step makes on bit patterns, so that they run on the integer pipe
+// instead of the FP64 pipe (which bounds that step); FP32 keeps plain compares.
+__host__ __device__ __forceinline__ bool is_zero(float v) { return v == 0.f; }
+__host__ __device__ __forceinline__ bool is_zero(double v)
+{
+#ifdef __CUDA_ARCH__
+    return (__double_as_longlong(v) << 1) == 0;  // +0 or -0
+#else
+    return v == 0.0;
+#endif
+}
+// a > b for a, b >= 0 (FP64: a positive NaN counts as greater)
+__device__ __forceinline__ bool gt_nonneg(float a, float b) { return a > b; }
+__device__ __forceinline__ bool gt_nonneg(double a, double b)
+{
+    return __double_as_longlong(a) > __double_as_longlong(b);
+}
+__device__ __forceinline__ bool is_neg_inf(double v)
+{
+    return __double_as_longlong(v) == static_cast<long long>(0xFFF0000000000000ull);
+}
+
 __host__ __device__ __forceinline__ bool d_finite(float x) { return isfinite(x); }
 __host__ __device__ __forceinline__ bool d_finite(double x) { return isfinite(x); }
 
@@ -345,11 +367,11 @@ __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, 
         return;
     }
     const T r2 = x * x + y * y + z * z;
-    const T r = d_sqrt(r2);
-    if (r == T(0)) {
+    if (is_zero(r2)) {
         ax = ay = az = T(0);
         return;
     }
+    const T r = d_sqrt(r2);
     const T ra = r + k.a;
     // -g(r)/r with g = G M(<r) / r^2
     T f = d_div(k.GM, ra * ra * r);
@@ -787,7 +809,7 @@ struct Acc<double> {
     static __host__ __device__ size_t bytes(const Model &m) { return sizeof(long long) * size_t(m.hist_words); }
     __device__ static void add(void *base, const Model &, int slot, double v, double scale)
     {
-        if (v == 0.0) return;
+        if (is_zero(v)) return;
         long long *h = static_cast<long long *>(base);
         long long hi, lo;
         fx2(v, scale, hi, lo);
@@ -916,10 +938,10 @@ __device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, con
                                             unsigned code, const T *gexp, T lprior, T u, T x, T y, T z, T vy, T vz,
                                             unsigned &err)
 {
-    if (u == -HUGE_VAL) return u;  // w = 0 is a fixed point
+    if (is_neg_inf(u)) return u;  // w = 0 is a fixed point
     const T data = foc_data<Ms...>(m, k, tb, rec, code, gexp, x, y, z, vy, vz);
     // a prior that reads 0 (below the resolution of the cell sums) drops the entropy term
-    T dS = lprior > -HUGE_VAL ? lprior - u : T(0);
+    T dS = !is_neg_inf(lprior) ? lprior - u : T(0);
     if (m.mode == 0) dS -= T(1);
     const T h = k.dteps * (k.mu * dS - data);
     T un;
@@ -932,8 +954,9 @@ __device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, con
         }
         un = u + log1p(h);
     }
-    // exp_tab overflows above 709
-    if (!(un <= T(709))) err |= kErrNonFinite;
+    // exp_tab overflows above 709 (NaN of either sign is flagged too)
+    const long long ub = __double_as_longlong(un);
+    if ((ub & 0x7fffffffffffffffll) > 0x7ff0000000000000ll || ub > 0x4086280000000000ll) err |= kErrNonFinite;
     return un;
 }
 
@@ -1170,7 +1193,7 @@ __device__ __forceinline__ const float *global_records<float>(const Buffers &b) 
 // the block-shared path, added directly.
 __device__ __forceinline__ void global_add(long long *hist, int slot, double v, double scale)
 {
-    if (v == 0.0) return;
+    if (is_zero(v)) return;
     long long hi, lo;
     fx2(v, scale, hi, lo);
     atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * slot), static_cast<unsigned long long>(hi));
@@ -1297,7 +1320,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         } else {
             if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
         }
-        if (w != T(0)) {
+        if (!is_zero(w)) {
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
             unsigned code_out = 0;
@@ -1309,7 +1332,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                 if (cache) code_out = ap_encode(m, code_out, g, p);
                 if (p >= 0) {
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
-                    if (GP<M>::v2(G) && vlos * vlos > k.v2max) err |= kErrOverflow;
+                    if (GP<M>::v2(G) && gt_nonneg(vlos * vlos, k.v2max)) err |= kErrOverflow;
                     group_kernels<M>(
                         G, tb, p, vlos, w,
                         [&](int j, T v, int cls) {
