@@ -55,7 +55,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 KERNEL_FIGURES = {
     # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B), prior cell, cached apertures
     # and cached exp(-nu^2/2) (2 + 2 + 8 B); write 80 + 2 + 8 B
-    "fp64": {"bytes": 182, "flops": None},
+    "fp64": {"bytes": 182, "flops": 151.37},
     # read 6 coordinates + w (28 B), prior cell and cached apertures (2 + 2 B);
     # write 28 B + 2 B of apertures
     "mixed": {"bytes": 62, "flops": None},
@@ -66,7 +66,11 @@ KERNEL_FIGURES = {
 # the capture); absent: not captured. Most of a step's writes are still in the
 # 129 MB L2 when the kernel ends (written back during the next launch or the L2
 # flush), so the write count is below the algorithmic one.
-DRAM_PER_UNIT = {}
+DRAM_PER_UNIT = {
+    ("c2", "fp64"): (121.0, 1_000_000),
+    ("c2", "mixed"): (32.1, 1_000_000),
+    ("c5", "mixed"): (61.4, 52_205_149),
+}
 
 
 class ClockSampler:

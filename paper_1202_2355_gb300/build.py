@@ -41,12 +41,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
         procs.append(subprocess.Popen([nvcc()] + flags + ["-c", "-o", obj, src], stdout=subprocess.PIPE,
                                       stderr=subprocess.STDOUT, text=True))
     outs = [p.communicate()[0] for p in procs]
-    if any(p.returncode for p in procs):
-        raise RuntimeError("nvcc failed:\n" + "\n".join(outs))
     tmp = SO + tag
-    r = subprocess.run([nvcc(), "-shared", ARCH, "-o", tmp] + objs, capture_output=True, text=True)
-    for o in objs:
-        os.remove(o)
+    try:
+        if any(p.returncode for p in procs):
+            raise RuntimeError("nvcc failed:\n" + "\n".join(outs))
+        r = subprocess.run([nvcc(), "-shared", ARCH, "-o", tmp] + objs, capture_output=True, text=True)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     if verbose:
