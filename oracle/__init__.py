@@ -69,7 +69,7 @@ class Obs(C.Structure):
 class Prior(C.Structure):
     _fields_ = [("mode", C.c_int), ("nE", C.c_int), ("nx", C.c_int), ("e_spacing", C.c_int),
                 ("signed_lz", C.c_int), ("update_every", C.c_int), ("Emin", C.c_double),
-                ("Emax", C.c_double)]
+                ("Emax", C.c_double), ("smoothing", C.c_int), ("lam", C.c_double)]
 
 
 class Params(C.Structure):
@@ -88,7 +88,8 @@ class Particles(C.Structure):
 class State(C.Structure):
     _fields_ = [("cell", C.POINTER(C.c_int)), ("what", _DP), ("grid_mean", _DP),
                 ("grid_count", C.POINTER(C.c_long)), ("ytil", _DP), ("yraw", _DP),
-                ("delta", _DP), ("chi2", C.c_double), ("W0", C.c_double), ("t", C.c_long)]
+                ("delta", _DP), ("chi2", C.c_double), ("W0", C.c_double), ("t", C.c_long),
+                ("grid_raw", _DP), ("lam", C.c_double)]
 
 
 def lib():
@@ -117,6 +118,9 @@ def lib():
                               C.POINTER(State)]
         L.or_run.argtypes = [C.POINTER(Potential), C.POINTER(Obs), _DP, _DP, C.POINTER(Prior),
                              C.POINTER(Params), C.POINTER(Particles), C.POINTER(State), C.c_long]
+        L.or_smooth_penalty.argtypes = [C.c_int, C.c_int, _DP]
+        L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
+        L.or_smooth_grid.restype = C.c_int
         L.or_build_targets.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP, _DP, _DP, _DP,
                                        _DP, _DP, C.POINTER(C.c_int)]
         _lib = L
@@ -173,7 +177,7 @@ class ObsSet:
 
 def prior(d: dict) -> Prior:
     return Prior(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
-                 d["update_every"], d["Emin"], d["Emax"])
+                 d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)), float(d.get("lambda", 0.0)))
 
 
 def params(d: dict) -> Params:
@@ -293,9 +297,11 @@ class Run:
         self.ytil = np.zeros(J)
         self.yraw = np.zeros(J)
         self.delta = np.zeros(J)
+        self.grid_raw = np.zeros(max(ncell, 1))
         self.st = State(self.cell.ctypes.data_as(C.POINTER(C.c_int)), _dp(self.what),
                         _dp(self.grid_mean), self.grid_count.ctypes.data_as(C.POINTER(C.c_long)),
-                        _dp(self.ytil), _dp(self.yraw), _dp(self.delta), 0.0, 0.0, 0)
+                        _dp(self.ytil), _dp(self.yraw), _dp(self.delta), 0.0, 0.0, 0,
+                        _dp(self.grid_raw), 0.0)
         lib().or_init(C.byref(obs.o), _dp(self.Y), _dp(self.sig), C.byref(self.G),
                       C.byref(self.ps.s), C.byref(self.st))
 
@@ -317,6 +323,11 @@ class Run:
         return self.st.W0
 
     @property
+    def lam(self) -> float:
+        """Smoothing weight of the last prior update (prior smoothing on)."""
+        return self.st.lam
+
+    @property
     def w(self) -> np.ndarray:
         return self.ps.a["w"]
 
@@ -325,6 +336,24 @@ class Run:
         return lib().or_force(C.byref(self.obs.o), C.byref(self.par), self.G.mode, a["w"][i],
                               self.what[i], a["x"][i], a["y"][i], a["z"][i], a["vx"][i],
                               a["vy"][i], a["vz"][i], _dp(self.delta), _dp(self.sig))
+
+
+def smooth_penalty(nE: int, nx: int) -> np.ndarray:
+    """The finite-difference penalty matrix of the prior grid (or_smooth_penalty)."""
+    P = np.zeros((nE * nx, nE * nx))
+    lib().or_smooth_penalty(nE, nx, _dp(P))
+    return P
+
+
+def smooth_grid(y, nE: int, nx: int, lam: float = 0.0):
+    """(f, lambda): the smoothed grid of eq. smooth_grid; lam <= 0 chooses lambda by GCV."""
+    y = np.ascontiguousarray(y, np.float64)
+    f = np.zeros_like(y)
+    lo = C.c_double()
+    rc = lib().or_smooth_grid(nE, nx, _dp(y), lam, _dp(f), C.byref(lo))
+    if rc != 0:
+        raise RuntimeError(f"or_smooth_grid failed ({rc})")
+    return f, lo.value
 
 
 def from_workload(wl, target_particles=None):

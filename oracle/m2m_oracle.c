@@ -332,7 +332,8 @@ double or_force(const or_obs *o, const or_params *par, int mode, double w_i, dou
     int c = or_kernel_row(o, x, y, z, vx, vy, vz, jj, kk);
     double data = 0.0;
     for (int e = 0; e < c; ++e) data += kk[e] * delta[jj[e]] / sig[jj[e]];
-    double dS = -log(w_i / what_i);
+    /* a smoothed prior can be <= 0, where -ln(w/what) is undefined: no entropy force there */
+    double dS = what_i > 0.0 ? -log(w_i / what_i) : 0.0;
     if (mode == OR_GWR) dS -= 1.0;
     return par->mu * dS - data;
 }
@@ -365,8 +366,10 @@ void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior
         for (int c = 0; c < g->nE * g->nx; ++c) {
             st->grid_mean[c] = 0.0;
             st->grid_count[c] = 0;
+            if (st->grid_raw) st->grid_raw[c] = 0.0;
         }
     }
+    st->lambda = 0.0;
     st->t = 0;
 }
 
@@ -406,6 +409,16 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
             }
             for (int c = 0; c < ncell; ++c)
                 st->grid_mean[c] = st->grid_count[c] > 0 ? gsum[c] / (double)st->grid_count[c] : 0.0;
+            if (g->smoothing) {
+                /* Sec. 2.3.2: the priors are the spline fit of the grid of cell means */
+                if (st->grid_raw)
+                    for (int c = 0; c < ncell; ++c) st->grid_raw[c] = st->grid_mean[c];
+                memcpy(gsum, st->grid_mean, sizeof(double) * (size_t)ncell);
+                if (or_smooth_grid(g->nE, g->nx, gsum, g->lambda, st->grid_mean, &st->lambda) != OR_OK) {
+                    status = OR_EARG;
+                    break;
+                }
+            }
             for (long i = 0; i < s->n; ++i) st->what[i] = st->grid_mean[st->cell[i]];
         }
         /* 6. force of change */
@@ -569,4 +582,139 @@ int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
     free(lum);
     if (iters_out) *iters_out = maxit;
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Smoothing of the grid of priors (Sec. 2.3.2)                        */
+
+/* adds w r r^T to P for the stencil row r (nz entries idx[], coef[]) */
+static void add_outer(double *P, int n, int nz, const int *idx, const double *coef, double w)
+{
+    for (int a = 0; a < nz; ++a)
+        for (int b = 0; b < nz; ++b) P[(size_t)idx[a] * n + idx[b]] += w * coef[a] * coef[b];
+}
+
+void or_smooth_penalty(int nE, int nx, double *P)
+{
+    int n = nE * nx;
+    for (size_t q = 0; q < (size_t)n * n; ++q) P[q] = 0.0;
+    int idx[4];
+    double coef[4];
+    /* f_EE = f(k-1,l) - 2 f(k,l) + f(k+1,l) */
+    for (int k = 1; k + 1 < nE; ++k)
+        for (int l = 0; l < nx; ++l) {
+            idx[0] = (k - 1) * nx + l; idx[1] = k * nx + l; idx[2] = (k + 1) * nx + l;
+            coef[0] = 1.0; coef[1] = -2.0; coef[2] = 1.0;
+            add_outer(P, n, 3, idx, coef, 1.0);
+        }
+    /* f_xx = f(k,l-1) - 2 f(k,l) + f(k,l+1) */
+    for (int k = 0; k < nE; ++k)
+        for (int l = 1; l + 1 < nx; ++l) {
+            idx[0] = k * nx + l - 1; idx[1] = k * nx + l; idx[2] = k * nx + l + 1;
+            coef[0] = 1.0; coef[1] = -2.0; coef[2] = 1.0;
+            add_outer(P, n, 3, idx, coef, 1.0);
+        }
+    /* f_Ex at the corner between (k,l) and (k+1,l+1), weighted 2 */
+    for (int k = 0; k + 1 < nE; ++k)
+        for (int l = 0; l + 1 < nx; ++l) {
+            idx[0] = (k + 1) * nx + l + 1; idx[1] = (k + 1) * nx + l; idx[2] = k * nx + l + 1; idx[3] = k * nx + l;
+            coef[0] = 1.0; coef[1] = -1.0; coef[2] = -1.0; coef[3] = 1.0;
+            add_outer(P, n, 4, idx, coef, 2.0);
+        }
+}
+
+/* Cholesky factor L (lower) of the SPD matrix M in place; returns 0 on success */
+static int cholesky(double *M, int n)
+{
+    for (int j = 0; j < n; ++j) {
+        double d = M[(size_t)j * n + j];
+        for (int k = 0; k < j; ++k) d -= M[(size_t)j * n + k] * M[(size_t)j * n + k];
+        if (!(d > 0.0)) return 1;
+        d = sqrt(d);
+        M[(size_t)j * n + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double v = M[(size_t)i * n + j];
+            for (int k = 0; k < j; ++k) v -= M[(size_t)i * n + k] * M[(size_t)j * n + k];
+            M[(size_t)i * n + j] = v / d;
+        }
+    }
+    return 0;
+}
+
+/* solves L L^T x = b (x may alias b) */
+static void chol_solve(const double *L, int n, const double *b, double *x)
+{
+    for (int i = 0; i < n; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= L[(size_t)i * n + k] * x[k];
+        x[i] = v / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = x[i];
+        for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * x[k];
+        x[i] = v / L[(size_t)i * n + i];
+    }
+}
+
+/* f = (I + lambda P)^-1 y and, when gcv is not NULL, the GCV score
+ * n |y - f|^2 / (n - tr A)^2 with tr A from the diagonal of the explicit inverse */
+static int smooth_at(const double *P, int n, const double *y, double lambda, double *f, double *gcv,
+                     double *M, double *col)
+{
+    for (size_t q = 0; q < (size_t)n * n; ++q) M[q] = lambda * P[q];
+    for (int i = 0; i < n; ++i) M[(size_t)i * n + i] += 1.0;
+    if (cholesky(M, n)) return OR_EARG;
+    chol_solve(M, n, y, f);
+    if (gcv) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) {
+            for (int k = 0; k < n; ++k) col[k] = (k == i) ? 1.0 : 0.0;
+            chol_solve(M, n, col, col);
+            tr += col[i];
+        }
+        double rss = 0.0;
+        for (int i = 0; i < n; ++i) rss += (y[i] - f[i]) * (y[i] - f[i]);
+        *gcv = (double)n * rss / ((n - tr) * (n - tr));
+    }
+    return OR_OK;
+}
+
+int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, double *lambda_out)
+{
+    if (nE < 3 || nx < 3) return OR_EARG;
+    int n = nE * nx;
+    double *P = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *M = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *col = (double *)malloc(sizeof(double) * (size_t)n);
+    int rc = OR_OK;
+    if (!P || !M || !col) rc = OR_EARG;
+    if (rc == OR_OK) {
+        or_smooth_penalty(nE, nx, P);
+        if (!(lambda > 0.0)) {
+            /* golden-section search of the GCV score over t = log10 lambda in [-4, 6] */
+            const double g = 0.5 * (sqrt(5.0) - 1.0);
+            double a = -4.0, b = 6.0;
+            double c = b - g * (b - a), d = a + g * (b - a), vc, vd;
+            rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);
+            if (rc == OR_OK) rc = smooth_at(P, n, y, pow(10.0, d), f, &vd, M, col);
+            for (int it = 0; rc == OR_OK && it < 40; ++it) {
+                if (vc <= vd) {
+                    b = d; d = c; vd = vc;
+                    c = b - g * (b - a);
+                    rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);
+                } else {
+                    a = c; c = d; vc = vd;
+                    d = a + g * (b - a);
+                    rc = smooth_at(P, n, y, pow(10.0, d), f, &vd, M, col);
+                }
+            }
+            lambda = pow(10.0, 0.5 * (a + b));
+        }
+        if (rc == OR_OK) rc = smooth_at(P, n, y, lambda, f, NULL, M, col);
+    }
+    if (lambda_out) *lambda_out = lambda;
+    free(P);
+    free(M);
+    free(col);
+    return rc;
 }

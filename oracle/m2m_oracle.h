@@ -63,6 +63,8 @@ typedef struct {
     int signed_lz;      /* 0: x = L/Lc in [0,1]; 1: x = Lz/Lc in [-1,1] */
     int update_every;
     double Emin, Emax;
+    int smoothing;      /* 0: raw cell means; 1: penalised spline fit of the grid (Sec. 2.3.2) */
+    double lambda;      /* smoothing weight; <= 0: chosen by generalized cross validation */
 } or_prior;
 
 typedef struct {
@@ -87,6 +89,8 @@ typedef struct {
     double *delta;      /* J: residuals */
     double chi2, W0;
     long t;
+    double *grid_raw;   /* nE*nx: raw cell means before smoothing (may be NULL without smoothing) */
+    double lambda;      /* smoothing weight of the last prior update */
 } or_state;
 
 int or_num_obs(const or_obs *o);
@@ -110,6 +114,18 @@ void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior
              const or_particles *s, or_state *st);
 int or_run(const or_potential *p, const or_obs *o, const double *Y, const double *sig,
            const or_prior *g, const or_params *par, or_particles *s, or_state *st, long nsteps);
+/* Finite-difference penalty of the prior grid (Sec. 2.3.2, eq. smooth_grid): P such that
+ * f.P.f = sum of (f_EE)^2 + 2 (f_Ex)^2 + (f_xx)^2 with second differences in units of one
+ * bin, f_EE at cells 1..nE-2 of each column, f_xx at cells 1..nx-2 of each row, f_Ex at the
+ * (nE-1)(nx-1) cell corners. Cell (k, l) is k*nx + l; P is dense, n*n, n = nE*nx. */
+void or_smooth_penalty(int nE, int nx, double *P);
+/* Smoothed grid f minimising |y - f|^2 + lambda f.P.f, i.e. f = (I + lambda P)^-1 y. With
+ * lambda <= 0 it is chosen by generalized cross validation: minimise n |(I-A) y|^2 / tr(I-A)^2,
+ * A = (I + lambda P)^-1, by golden-section search over log10 lambda in [-4, 6] (40 steps, the
+ * middle of the last bracket). lambda_out receives the weight used. Needs nE, nx >= 3.
+ * Returns OR_OK or OR_EARG. */
+int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, double *lambda_out);
+
 int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
                      const double *noise, double *Vp_out, double *sp_out,
                      double *Y_out, double *sig_out, int *iters_out);
