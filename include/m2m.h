@@ -133,7 +133,20 @@ typedef struct {
     int32_t signed_lz;
     int32_t update_every;          /* priors recomputed at steps t = 1, 1+P, 1+2P, ... */
     double Emin, Emax;
+    int32_t smoothing;             /* M2M_SMOOTH_*: the priors are the raw cell means, or the penalised
+                                      spline fit of the grid of cell means (Sec. 2.3.2, eq. smooth_grid) */
+    double lambda;                 /* smoothing weight; 0: chosen at every update by generalized cross
+                                      validation (golden-section search of log10 lambda in [-4, 6]) */
 } m2m_prior_grid;
+
+/* Prior smoothing (Sec. 2.3.2): f minimises |y - f|^2 + lambda sum_cells (f_EE^2 + 2 f_Ex^2
+ * + f_xx^2) over the grid of raw cell means y, with second differences in bin units (f_EE,
+ * f_xx over interior cells, f_Ex at cell corners): a plane as lambda -> infinity, the means
+ * as lambda -> 0. Needs MPR, nE, nx >= 3 and nE*nx <= 4096; the library diagonalises the
+ * grid penalty once per grid shape at creation (O((nE nx)^3) host work, about a second at
+ * 1000 cells). Cells whose fitted prior is <= 0 exert no entropy force. Not available in
+ * batches. */
+enum { M2M_SMOOTH_NONE = 0, M2M_SMOOTH_SPLINE_GCV = 1 };
 
 typedef struct {
     int32_t precision;             /* M2M_PREC_FP64: FP64 everywhere. M2M_PREC_MIXED: FP32 state,
@@ -195,6 +208,10 @@ m2m_status m2m_get_chi2(m2m_ctx *ctx, double *chi2, int32_t *J, double *delta);
  * (nE*nx); cells (n values) receives each particle's cell. Any may be NULL. */
 m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *counts, int32_t *cells,
                           int64_t n);
+
+/* Prior smoothing on: the raw cell means of the last update (nE*nx, may be NULL) and the
+ * smoothing weight used (may be NULL). M2M_ERR_STATE when smoothing is off. */
+m2m_status m2m_get_prior_smoothing(m2m_ctx *ctx, double *raw_means, double *lambda);
 
 /* Number of steps taken since the last load. */
 m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t);

@@ -697,8 +697,9 @@ int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, do
             double c = b - g * (b - a), d = a + g * (b - a), vc, vd;
             rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);
             if (rc == OR_OK) rc = smooth_at(P, n, y, pow(10.0, d), f, &vd, M, col);
-            for (int it = 0; rc == OR_OK && it < 40; ++it) {
-                if (vc <= vd) {
+            for (int it = 0; rc == OR_OK && it < 30; ++it) {
+                /* scores within 1e-12 (relative) count as a tie, kept on the lower side */
+                if (vc <= vd + 1e-12 * fabs(vd)) {
                     b = d; d = c; vd = vc;
                     c = b - g * (b - a);
                     rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);

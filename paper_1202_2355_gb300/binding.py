@@ -67,7 +67,7 @@ class Observables(C.Structure):
 class PriorGrid(C.Structure):
     _fields_ = [("mode", C.c_int32), ("nE", C.c_int32), ("nx", C.c_int32), ("e_spacing", C.c_int32),
                 ("signed_lz", C.c_int32), ("update_every", C.c_int32), ("Emin", C.c_double),
-                ("Emax", C.c_double)]
+                ("Emax", C.c_double), ("smoothing", C.c_int32), ("lam", C.c_double)]
 
 
 DEPOSIT = {"auto": 0, "shared": 1, "global": 2}
@@ -102,6 +102,7 @@ def lib():
         L.m2m_get_chi2.argtypes = [vp, _DP, C.POINTER(C.c_int32), _DP]
         L.m2m_get_priors.argtypes = [vp, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int64]
         L.m2m_get_step_count.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.m2m_get_prior_smoothing.argtypes = [vp, _DP, _DP]
         L.m2m_get_particle_count.argtypes = [vp, C.POINTER(C.c_int64)]
         L.m2m_set_timing.argtypes = [vp, C.c_int32]
         L.m2m_get_timing.argtypes = [vp, _DP, C.POINTER(C.c_int64)]
@@ -125,7 +126,7 @@ def lib():
                      "m2m_get_chi2", "m2m_get_priors", "m2m_get_step_count", "m2m_get_particle_count",
                      "m2m_save_state", "m2m_set_timing", "m2m_get_timing",
                      "m2m_load_state", "m2m_build_targets", "m2m_create_batch", "m2m_batch_size",
-                     "m2m_batch_model", "m2m_batch_autotune"):
+                     "m2m_batch_model", "m2m_batch_autotune", "m2m_get_prior_smoothing"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -187,7 +188,8 @@ class ObsDesc:
 
 def prior_grid(d: dict) -> PriorGrid:
     return PriorGrid(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
-                     d["update_every"], d["Emin"], d["Emax"])
+                     d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)),
+                     float(d.get("lambda", 0.0)))
 
 
 def _soa(p: dict, keys):
@@ -305,6 +307,13 @@ class Fit:
         self._ck(lib().m2m_get_priors(self.h, _dp(g), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                       cells.ctypes.data_as(C.POINTER(C.c_int32)), self.n))
         return g[:self.ncell], cnt[:self.ncell], cells
+
+    def prior_smoothing(self):
+        """(raw cell means of the last prior update, smoothing weight used) with smoothing on."""
+        raw = np.zeros(max(self.ncell, 1))
+        lam = C.c_double()
+        self._ck(lib().m2m_get_prior_smoothing(self.h, _dp(raw), C.byref(lam)))
+        return raw[:self.ncell], lam.value
 
     def step_count(self) -> int:
         t = C.c_int64()

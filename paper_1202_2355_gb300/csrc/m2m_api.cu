@@ -250,6 +250,15 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         m.ncell = 0;
         m.update_every = 1;
     }
+    m.smooth = pg->smoothing;
+    m.smooth_lambda = pg->lambda;
+    if (m.smooth != M2M_SMOOTH_NONE) {
+        if (m.smooth != M2M_SMOOTH_SPLINE_GCV) return fail(ctx, M2M_ERR_ARG, "unknown prior smoothing");
+        if (m.mode != M2M_REG_MPR || m.nE < 3 || m.nx < 3 || m.ncell > 4096)
+            return fail(ctx, M2M_ERR_ARG, "prior smoothing needs the MPR grid with nE, nx >= 3 and nE*nx <= 4096");
+        if (!(m.smooth_lambda >= 0.0) || !std::isfinite(m.smooth_lambda))
+            return fail(ctx, M2M_ERR_ARG, "prior smoothing lambda must be >= 0 (0: chosen by GCV)");
+    }
 
     // circular orbits
     m.lc_closed = (m.pot == 0) ? 1 : 0;
@@ -304,6 +313,8 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     h = fnv(h, ctx->Y.data(), ctx->Y.size() * 8);
     h = fnv(h, ctx->sig.data(), ctx->sig.size() * 8);
     h = fnv(h, &ctx->precision, sizeof(int));
+    h = fnv(h, &m.smooth, sizeof(int));
+    h = fnv(h, &m.smooth_lambda, sizeof(double));
     ctx->config_hash = h;
     return M2M_OK;
 }
@@ -468,6 +479,7 @@ m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs,
         if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "constant tables: %s", cudaGetErrorString(e));
     }
     if (s == M2M_OK) s = upload_tables(ctx);
+    if (s == M2M_OK) s = smooth_setup(ctx);
     if (s != M2M_OK) {
         g_create_error = ctx->err;
         m2m_destroy(ctx);
@@ -493,6 +505,8 @@ Buffers buffers(m2m_ctx *c)
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
     b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior;
     b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
+    b.prior_raw = c->d_prior_raw; b.sV = c->d_sV; b.sVT = c->d_sVT; b.sD = c->d_sD;
+    b.spart = c->d_spart; b.sz = c->d_sz; b.ss = c->d_ss;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
 }
@@ -519,6 +533,7 @@ static void launch_one(m2m_ctx *c, int push, int init)
 {
     if (c->precision == M2M_PREC_FP64) launch_step<double, 2>(c, push, init);
     else launch_step<float, 1>(c, push, init);
+    smooth_launch(c);
 }
 
 template <class T, int WPS>
@@ -527,6 +542,7 @@ static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
     cudaEventRecord(ev[0], c->stream);
     step_kernel<T>(c)<<<grid_for(c), c->block, c->smem_step, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c),
                                                                               buffers(c), 1, 0);
+    smooth_launch(c);
     cudaEventRecord(ev[1], c->stream);
 }
 
@@ -850,6 +866,19 @@ extern "C" m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *c
     return m2m_synchronize(ctx);
 }
 
+extern "C" m2m_status m2m_get_prior_smoothing(m2m_ctx *ctx, double *raw_means, double *lambda)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (!ctx->m.smooth) return fail(ctx, M2M_ERR_STATE, "prior smoothing is off");
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    if (raw_means)
+        CU(cudaMemcpyAsync(raw_means, ctx->d_prior_raw, sizeof(double) * ctx->m.ncell, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    if (lambda) CU(cudaMemcpyAsync(lambda, &ctx->d_sc->smooth_lambda, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return m2m_synchronize(ctx);
+}
+
 extern "C" m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t)
 {
     if (!ctx || !t) return M2M_ERR_ARG;
@@ -915,7 +944,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const Model &m = ctx->m;
     CkptHeader hd{};
     std::memcpy(hd.magic, "M2MSTATE", 8);
-    hd.version = 4;
+    hd.version = 5;
     hd.precision = ctx->precision;
     hd.config_hash = ctx->config_hash;
     hd.n = ctx->n;
@@ -926,7 +955,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
     const size_t apb = m.ap_cache ? 2 * n : 0, gxb = ctx->gx ? 8 * n : 0;
     std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +
-                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
+                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + (m.smooth ? 4 : 3) * m.ncell) + 8 * m.ncell +
                           sizeof(Scalars));
     char *p = buf.data();
     for (int k = 0; k < narr; ++k) {
@@ -955,6 +984,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(p, ctx->d_prior_count, 8 * m.ncell, cudaMemcpyDeviceToHost));
         p += 8 * m.ncell;
+        if (m.smooth) CU(cudaMemcpy(p, ctx->d_prior_raw, sizeof(double) * m.ncell, cudaMemcpyDeviceToHost));
+        if (m.smooth) p += sizeof(double) * m.ncell;
     }
     CU(cudaMemcpy(p, ctx->d_sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
     FILE *f = std::fopen(path, "wb");
@@ -972,7 +1003,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 4) {
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 5) {
         std::fclose(f);
         return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
     }
@@ -986,7 +1017,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     const size_t apb = m.ap_cache ? 2 * n : 0;
     const size_t gxb = (ctx->precision == M2M_PREC_FP64 && m.gx_group >= 0) ? 8 * n : 0;
     std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +
-                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + 3 * m.ncell) + 8 * m.ncell +
+                          sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + (m.smooth ? 4 : 3) * m.ncell) + 8 * m.ncell +
                           sizeof(Scalars));
     const bool ok = std::fread(buf.data(), 1, buf.size(), f) == buf.size();
     std::fclose(f);
@@ -1033,6 +1064,8 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         p += sizeof(double) * m.ncell;
         CU(cudaMemcpy(ctx->d_prior_count, p, 8 * m.ncell, cudaMemcpyHostToDevice));
         p += 8 * m.ncell;
+        if (m.smooth) CU(cudaMemcpy(ctx->d_prior_raw, p, sizeof(double) * m.ncell, cudaMemcpyHostToDevice));
+        if (m.smooth) p += sizeof(double) * m.ncell;
     }
     CU(cudaMemcpy(ctx->d_sc, p, sizeof(Scalars), cudaMemcpyHostToDevice));
     CU(cudaMemset(ctx->d_hist, 0, sizeof(long long) * m.hist_words));
@@ -1266,6 +1299,7 @@ void destroy_impl(m2m_ctx *ctx)
     free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
     free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
+    smooth_free(ctx);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -45,6 +45,10 @@ struct m2m_ctx {
     double *d_rec = nullptr, *d_iprior = nullptr, *d_lprior = nullptr;
     float *d_recf = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
+    // prior smoothing (m2m_smooth.cu)
+    double *d_prior_raw = nullptr, *d_sV = nullptr, *d_sVT = nullptr, *d_sD = nullptr;
+    double *d_spart = nullptr, *d_sz = nullptr, *d_ss = nullptr;
+    int smooth_ch = 1;
     m2m::Scalars *d_sc = nullptr;
     double *d_wout = nullptr;
     long long wout_cap = 0;
@@ -91,6 +95,11 @@ m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs, con
 m2m_status check_device_errors(m2m_ctx *ctx);
 m2m::Buffers buffers(m2m_ctx *c);
 void destroy_impl(m2m_ctx *ctx);
+
+// prior smoothing (m2m_smooth.cu)
+m2m_status smooth_setup(m2m_ctx *ctx);
+void smooth_free(m2m_ctx *ctx);
+void smooth_launch(m2m_ctx *ctx);
 
 // batch runtime (m2m_batch.cu)
 m2m_status batch_step(m2m_ctx *ctx, int64_t nsteps);

@@ -83,6 +83,9 @@ struct Model {
     // first group with Gauss-Hermite kernels, -1 none) is also kept from the deposit
     // for the next force of change (same nu, same value)
     int gx_group;
+    // prior smoothing (Sec. 2.3.2): 0 off; lambda > 0 fixed, else chosen by GCV
+    int smooth;
+    double smooth_lambda;
 };
 
 constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
@@ -190,6 +193,9 @@ struct Scalars {
     int pending;        // the previous step's force of change is still to be applied
     unsigned err;       // latched kErr* bits
     unsigned blocks_done;  // blocks of the running step kernel that have flushed their sums
+    int smooth_pending;    // new raw cell means wait for the prior smoothing kernels
+    unsigned smooth_blocks;   // blocks of the running smoothing kernel that have finished
+    double smooth_lambda;  // smoothing weight of the last prior update
 };
 
 template <class T>
@@ -231,6 +237,9 @@ struct Buffers {
     double *iprior;                  // per cell: 1/prior (0 when the prior reads as 0)
     double *lprior;                  // per cell: ln prior (-inf when the prior reads as 0)
     long long *prior_count;          // per cell: particle count at the last update
+    double *prior_raw;               // per cell: raw cell mean before smoothing (smoothing on)
+    const double *sV, *sVT, *sD;     // smoothing: eigenvectors of the grid penalty (V, V^T) and eigenvalues
+    double *spart, *sz, *ss;         // smoothing scratch: chunk partial sums, V^T y, smoothed coefficients
     long long *hist;                 // global fixed-point sums
     double *ytil, *yraw, *delta;
     Scalars *sc;
@@ -1144,10 +1153,14 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
             const long long cnt = __ldcg(b.hist + m.off_count + c);
             const double sum = fx_read<WPS>(b.hist, m.J + 1 + c) / m.fx_w * s_ren;
             const double pr = cnt > 0 ? sum / double(cnt) : 0.0;  // mean weight of the cell
+            b.prior_count[c] = cnt;
+            if (m.smooth) {  // the smoothing kernels turn the raw means into the priors
+                b.prior_raw[c] = pr;
+                continue;
+            }
             b.prior[c] = pr;
             b.iprior[c] = pr > 0.0 ? 1.0 / pr : 0.0;
             b.lprior[c] = pr > 0.0 ? log(pr) : -HUGE_VAL;
-            b.prior_count[c] = cnt;
         }
     }
     __syncthreads();
@@ -1164,6 +1177,7 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
         sc.lwscale = log(s_ren);
         sc.pending = init ? 0 : (t > m.n_relax ? 1 : 0);
         sc.blocks_done = 0;
+        if (prior_step && m.smooth) sc.smooth_pending = 1;
     }
 }
 
