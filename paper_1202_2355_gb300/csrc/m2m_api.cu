@@ -252,6 +252,8 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     }
     m.smooth = pg->smoothing;
     m.smooth_lambda = pg->lambda;
+    m.win_group = -1;
+    m.win_lo = m.win_n = 0;
     if (m.smooth != M2M_SMOOTH_NONE) {
         if (m.smooth != M2M_SMOOTH_SPLINE_GCV) return fail(ctx, M2M_ERR_ARG, "unknown prior smoothing");
         if (m.mode != M2M_REG_MPR || m.nE < 3 || m.nx < 3 || m.ncell > 4096)
@@ -350,13 +352,32 @@ static typename StepKernel<T>::Fn step_kernel(const m2m_ctx *c)
     return reinterpret_cast<typename StepKernel<T>::Fn>(c->kstep);
 }
 
+// Resident blocks per SM the aperture window of the global-deposit kernel is sized for.
+static const int kGlobalDepositBlocks = 3;
+
 template <class T, int WPS>
 static m2m_status configure_kernels(m2m_ctx *ctx)
 {
     // the finalize reuses the start of the dynamic shared memory for a block reduction
     const size_t red = size_t(256) * sizeof(double);
     const size_t smem_shared = std::max(smem_bytes<T>(ctx->m, 1, 1), red);
-    const size_t smem_global = std::max(smem_bytes<T>(ctx->m, 0, 0), red);
+    // global deposit: an aperture window of the largest group keeps block-shared sums,
+    // sized so that kGlobalDepositBlocks blocks fit on an SM
+    {
+        Model &m = ctx->m;
+        int smsm = 0;
+        CU(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+        int best = 0;
+        for (int g = 1; g < m.n_groups; ++g)
+            if (m.g[g].n_kinds * m.g[g].n_ap > m.g[best].n_kinds * m.g[best].n_ap) best = g;
+        m.win_group = best;
+        m.win_n = 0;
+        const long long per_block = smsm / kGlobalDepositBlocks - 2048 - (long long)smem_bytes<T>(m, 0, 0, 0);
+        const long long slot_bytes = sizeof(T) == 8 ? 16 : 12;
+        if (per_block > 0) m.win_n = int(std::min<long long>(m.g[best].n_ap, per_block / (slot_bytes * m.g[best].n_kinds)));
+        m.win_lo = (m.g[best].n_ap - m.win_n) / 2;  // until the first deposit places it
+    }
+    const size_t smem_global = std::max(smem_bytes<T>(ctx->m, 2, 0, 0), red);
     ctx->smem_mat = smem_bytes<T>(ctx->m, 0, 0);
     int maxsm = 0;
     CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
@@ -394,6 +415,17 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     if ((s = up(ctx->d_edges, ctx->edges)) != M2M_OK) return s;
     if ((s = up(ctx->d_Vp, ctx->Vp)) != M2M_OK) return s;
     if ((s = up(ctx->d_isp, ctx->isp)) != M2M_OK) return s;
+    {
+        std::vector<float> vf(ctx->Vp.begin(), ctx->Vp.end()), sf(ctx->isp.begin(), ctx->isp.end());
+        free_dev(ctx->d_Vpf);
+        free_dev(ctx->d_ispf);
+        if (!vf.empty()) {
+            CU(cudaMalloc(&ctx->d_Vpf, vf.size() * sizeof(float)));
+            CU(cudaMalloc(&ctx->d_ispf, sf.size() * sizeof(float)));
+            CU(cudaMemcpy(ctx->d_Vpf, vf.data(), vf.size() * sizeof(float), cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(ctx->d_ispf, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
     if ((s = up(ctx->d_lcE, ctx->lcE)) != M2M_OK) return s;
     if ((s = up(ctx->d_Y, ctx->Y)) != M2M_OK) return s;
     if ((s = up(ctx->d_sig, ctx->sig)) != M2M_OK) return s;
@@ -501,7 +533,7 @@ extern "C" m2m_status m2m_create(const m2m_potential *pot, const m2m_observables
 Buffers buffers(m2m_ctx *c)
 {
     Buffers b;
-    b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.lcE = c->d_lcE; b.lut = c->d_lut;
+    b.edges = c->d_edges; b.Vp = c->d_Vp; b.isp = c->d_isp; b.Vpf = c->d_Vpf; b.ispf = c->d_ispf; b.lcE = c->d_lcE; b.lut = c->d_lut;
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
     b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior;
     b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
@@ -618,6 +650,22 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     launch_one(ctx, 0, 1);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->global_dep && m.win_n > 0 && m.win_n < m.g[m.win_group].n_ap) {
+        // place the aperture window on the densest range of the first deposit (any
+        // placement gives the same sums; this one keeps most deposits block-shared)
+        const GroupDesc &G = m.g[m.win_group];
+        std::vector<double> y(G.n_ap);
+        CU(cudaMemcpy(y.data(), ctx->d_yraw + G.obs_off, sizeof(double) * G.n_ap, cudaMemcpyDeviceToHost));
+        double run = 0.0, best = -1.0;
+        for (int p = 0; p < G.n_ap; ++p) {
+            run += std::fabs(y[p]);
+            if (p >= m.win_n) run -= std::fabs(y[p - m.win_n]);
+            if (p + 1 >= m.win_n && run > best) {
+                best = run;
+                m.win_lo = p + 1 - m.win_n;
+            }
+        }
+    }
     if (ctx->graph) {
         cudaGraphExecDestroy(ctx->graph);
         ctx->graph = nullptr;
@@ -1293,7 +1341,7 @@ void destroy_impl(m2m_ctx *ctx)
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_state(ctx);
-    free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
+    free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_Vpf); free_dev(ctx->d_ispf); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
     free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_recf); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
     free_dev(ctx->d_ytil);
@@ -1419,7 +1467,7 @@ __global__ void __launch_bounds__(256) k_static_observe(const Model m, const Cst
             const int p = aperture<kDyn>(G, tb.esq, nullptr, x[i], Y);
             if (p >= 0) {
                 if (G.has_v2 && vlos * vlos > k.v2max) err |= kErrOverflow;
-                group_kernels<kDyn>(G, tb, p, vlos, wi, [&](int j, double v, int cls) {
+                group_kernels<kDyn>(G, tb, p, vlos, wi, [&](int j, double v, int cls, int) {
                     Acc<double>::add(h, m, j, v, cls == kClassMass ? m.fx_w : (cls == kClassVel ? m.fx_v2 : m.fx_gh));
                 });
             }

@@ -38,6 +38,7 @@ struct m2m_ctx {
     uint16_t *ap = nullptr;  // cached apertures (Model::ap_cache)
     double *gx = nullptr;    // cached exp(-nu^2/2) (Model::gx_group, FP64 mode)
     double *d_edges = nullptr, *d_Vp = nullptr, *d_isp = nullptr, *d_lcE = nullptr;
+    float *d_Vpf = nullptr, *d_ispf = nullptr;
     unsigned short *d_lut = nullptr;
     double *d_Y = nullptr, *d_sig = nullptr, *d_post = nullptr, *d_iscale = nullptr;
     int *d_kind = nullptr;

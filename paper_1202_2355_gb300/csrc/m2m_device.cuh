@@ -86,6 +86,9 @@ struct Model {
     // prior smoothing (Sec. 2.3.2): 0 off; lambda > 0 fixed, else chosen by GCV
     int smooth;
     double smooth_lambda;
+    // global-deposit kernel: apertures [win_lo, win_lo + win_n) of group win_group keep
+    // block-shared sums (the densest range, placed at load); the rest deposit globally
+    int win_group, win_lo, win_n;
 };
 
 constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
@@ -224,6 +227,7 @@ constexpr bool kCacheAccel = sizeof(T) == 8;
 
 struct Buffers {
     const double *edges, *Vp, *isp;  // per group edges, per aperture V_p and 1/sigma_p
+    const float *Vpf, *ispf;         // FP32 copies of V_p and 1/sigma_p (read from global memory)
     const unsigned short *lut;       // annulus lookup tables (FP32 path)
     const double *lcE;               // E_c table
     const double *Y, *sig;
@@ -530,7 +534,8 @@ struct Tables {
 __device__ __forceinline__ float kexp(const Tables<float> &, float x) { return __expf(x); }
 __device__ __forceinline__ double kexp(const Tables<double> &tb, double x) { return exp_tab(x, tb.e2); }
 
-// Emits emit(slot, w K_slot, class) for every kernel of group G at aperture p:
+// Emits emit(slot, w K_slot, class, kind index in the group) for every kernel of group G
+// at aperture p:
 // surface mass (K = 1), v_los^2, v_los, and the Gauss-Hermite b_n with H_n from the
 // recurrence H_{n+1} = 2 nu H_n - 2 n H_{n-1}, evaluated once up to the group's
 // highest order.
@@ -540,9 +545,9 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
 {
     using P = GP<M>;
     const int base = G.obs_off + p;
-    if (P::mass(G)) emit(base + G.k_mass * G.n_ap, w, kClassMass);
-    if (P::v2(G)) emit(base + G.k_v2 * G.n_ap, w * vlos * vlos, kClassVel);
-    if (P::v1(G)) emit(base + G.k_v1 * G.n_ap, w * vlos, kClassVel);
+    if (P::mass(G)) emit(base + G.k_mass * G.n_ap, w, kClassMass, G.k_mass);
+    if (P::v2(G)) emit(base + G.k_v2 * G.n_ap, w * vlos * vlos, kClassVel, G.k_v2);
+    if (P::v1(G)) emit(base + G.k_v1 * G.n_ap, w * vlos, kClassVel, G.k_v1);
     const int nmax = P::max_gh(G);
     if (nmax >= 0) {
         const T nu = (vlos - tb.vp[G.ap_off + p]) * tb.isp[G.ap_off + p];
@@ -550,15 +555,16 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
         if (gexp_out) *gexp_out = ge;
         const T we = w * ge;
         T hm1 = T(1), h = T(2) * nu;
-        if (P::gh(G, 0)) emit(base + G.k_gh[0] * G.n_ap, T(gh_c(0)) * we, kClassGH);
-        if (P::gh(G, 1)) emit(base + G.k_gh[1] * G.n_ap, h * we, kClassGH);
+        if (P::gh(G, 0)) emit(base + G.k_gh[0] * G.n_ap, T(gh_c(0)) * we, kClassGH, G.k_gh[0]);
+        if (P::gh(G, 1)) emit(base + G.k_gh[1] * G.n_ap, h * we, kClassGH, G.k_gh[1]);
 #pragma unroll
         for (int n = 1; n < 6; ++n) {
             if (n < nmax) {
                 const T hn1 = T(2) * nu * h - T(2 * n) * hm1;
                 hm1 = h;
                 h = hn1;
-                if (P::gh(G, n + 1)) emit(base + G.k_gh[n + 1] * G.n_ap, T(gh_c(n + 1)) * h * we, kClassGH);
+                if (P::gh(G, n + 1))
+                    emit(base + G.k_gh[n + 1] * G.n_ap, T(gh_c(n + 1)) * h * we, kClassGH, G.k_gh[n + 1]);
             }
         }
     }
@@ -979,47 +985,60 @@ struct Smem {
     unsigned short *lut;
 };
 
+// Block sums of the global-deposit kernel's aperture window: one slot per kind and
+// window aperture, laid out as Acc<T> slots.
 template <class T>
-__host__ __device__ inline size_t acc_bytes_padded(const Model &m)
+__host__ __device__ inline size_t window_bytes(const Model &m)
 {
-    return (Acc<T>::bytes(m) + 15) / 16 * 16;
+    const size_t slots = m.win_n > 0 ? size_t(m.g[m.win_group].n_kinds) * m.win_n : 0;
+    return slots * (sizeof(T) == 8 ? 2 * sizeof(long long) : 3 * sizeof(int));
+}
+
+// hist: 0 no block sums, 1 all (Acc<T>), 2 the aperture window of the global deposit
+template <class T>
+__host__ __device__ inline size_t acc_bytes_padded(const Model &m, int hist = 1)
+{
+    const size_t b = hist == 2 ? window_bytes<T>(m) : Acc<T>::bytes(m);
+    return (b + 15) / 16 * 16;
 }
 
 // Dynamic shared memory of a kernel holding the block sums (with_hist) and the
 // force-of-change records (with_rec) in shared memory; the global-deposit step
 // kernel keeps both in global memory.
 template <class T>
-__host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist, int with_rec = 1)
+__host__ __device__ inline size_t smem_bytes(const Model &m, int with_hist, int with_rec = 1, int with_vp = 1)
 {
-    size_t b = with_hist ? acc_bytes_padded<T>(m) : 0;
-    b += sizeof(T) * size_t((with_rec ? m.n_ap_total * m.rec_len : 0) + m.ncell + m.n_edges_total + 2 * m.n_ap_total);
+    size_t b = with_hist ? acc_bytes_padded<T>(m, with_hist) : 0;
+    b += sizeof(T) * size_t((with_rec ? m.n_ap_total * m.rec_len : 0) + m.ncell + m.n_edges_total +
+                            (with_vp ? 2 * m.n_ap_total : 0));
     b = (b + 7) / 8 * 8 + sizeof(double) * 32;
     b += sizeof(unsigned short) * size_t(m.n_lut) + 16;
     return b;
 }
 
 template <class T>
-__device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, int with_hist, int with_rec = 1)
+__device__ __forceinline__ Smem<T> carve(const Model &m, unsigned char *base, int with_hist, int with_rec = 1,
+                                         int with_vp = 1)
 {
     Smem<T> s;
     s.h = base;
-    T *t = reinterpret_cast<T *>(base + (with_hist ? acc_bytes_padded<T>(m) : 0));
+    T *t = reinterpret_cast<T *>(base + (with_hist ? acc_bytes_padded<T>(m, with_hist) : 0));
     s.c = t;
     s.iprior = s.c + (with_rec ? m.n_ap_total * m.rec_len : 0);
     s.esq = s.iprior + m.ncell;
     s.vp = s.esq + m.n_edges_total;
-    s.isp = s.vp + m.n_ap_total;
-    unsigned char *e = reinterpret_cast<unsigned char *>(s.isp + m.n_ap_total);
+    s.isp = s.vp + (with_vp ? m.n_ap_total : 0);
+    unsigned char *e = reinterpret_cast<unsigned char *>(s.isp + (with_vp ? m.n_ap_total : 0));
     s.e2 = reinterpret_cast<double *>(base + (e - base + 7) / 8 * 8);
     s.lut = reinterpret_cast<unsigned short *>(s.e2 + 32);
     return s;
 }
 
 template <class T>
-__device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, const Smem<T> &s)
+__device__ __forceinline__ void load_tables(const Model &m, const Buffers &b, const Smem<T> &s, int with_vp = 1)
 {
     for (int k = threadIdx.x; k < m.n_edges_total; k += blockDim.x) s.esq[k] = T(b.edges[k] * b.edges[k]);
-    for (int k = threadIdx.x; k < m.n_ap_total; k += blockDim.x) {
+    for (int k = threadIdx.x; with_vp && k < m.n_ap_total; k += blockDim.x) {
         s.vp[k] = T(b.Vp[k]);
         s.isp[k] = T(b.isp[k]);
     }
@@ -1203,6 +1222,21 @@ __device__ __forceinline__ const double *global_records<double>(const Buffers &b
 template <>
 __device__ __forceinline__ const float *global_records<float>(const Buffers &b) { return b.recf; }
 
+// V_p and 1/sigma_p per aperture in global memory (the global-deposit kernel keeps its
+// shared memory for the aperture window)
+template <class T>
+__device__ __forceinline__ const T *global_vp(const Buffers &b);
+template <>
+__device__ __forceinline__ const double *global_vp<double>(const Buffers &b) { return b.Vp; }
+template <>
+__device__ __forceinline__ const float *global_vp<float>(const Buffers &b) { return b.Vpf; }
+template <class T>
+__device__ __forceinline__ const T *global_isp(const Buffers &b);
+template <>
+__device__ __forceinline__ const double *global_isp<double>(const Buffers &b) { return b.isp; }
+template <>
+__device__ __forceinline__ const float *global_isp<float>(const Buffers &b) { return b.ispf; }
+
 // One deposit into the global sums (global-deposit mode): the fixed-point words of
 // the block-shared path, added directly.
 __device__ __forceinline__ void global_add(long long *hist, int slot, double v, double scale)
@@ -1245,9 +1279,8 @@ __device__ __forceinline__ StepFlags<T> step_flags(const Model &m, const Scalars
 template <class T, bool GA>
 __device__ __forceinline__ void block_zero(const Model &m, const Smem<T> &S)
 {
-    if (GA) return;
     int *z = static_cast<int *>(S.h);
-    const int nw = int(Acc<T>::bytes(m) / sizeof(int));
+    const int nw = int((GA ? window_bytes<T>(m) : Acc<T>::bytes(m)) / sizeof(int));
     for (int q = threadIdx.x; q < nw; q += blockDim.x) z[q] = 0;
 }
 
@@ -1263,7 +1296,7 @@ __device__ __forceinline__ void block_tables(const Model &m, const Buffers &b, c
             for (int q = threadIdx.x; q < m.ncell; q += blockDim.x) S.iprior[q] = T(pr[q]);
         }
     }
-    load_tables(m, b, S);
+    load_tables(m, b, S, GA ? 0 : 1);
 }
 
 // The per-particle part of one step for particles i0, i0 + stride, ... below i1:
@@ -1274,7 +1307,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                                                const Smem<T> &S, const StepFlags<T> &f, int push, long long i0,
                                                long long i1, long long stride, unsigned &err, Total<T> &wtot, T &wdep)
 {
-    const Tables<T> tb{S.esq, S.lut, S.vp, S.isp, S.e2};
+    const Tables<T> tb{S.esq, S.lut, GA ? global_vp<T>(b) : S.vp, GA ? global_isp<T>(b) : S.isp, S.e2};
     const T *rec = GA ? global_records<T>(b) : S.c;
     auto deposit = [&](int slot, T v, T scale) {
         if constexpr (GA) global_add(b.hist, slot, v, scale);
@@ -1349,8 +1382,17 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                     if (GP<M>::v2(G) && gt_nonneg(vlos * vlos, k.v2max)) err |= kErrOverflow;
                     group_kernels<M>(
                         G, tb, p, vlos, w,
-                        [&](int j, T v, int cls) {
-                            deposit(j, v, cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh));
+                        [&](int j, T v, int cls, int kk) {
+                            const T scale = cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh);
+                            if constexpr (GA) {
+                                const unsigned a = unsigned(p - m.win_lo);
+                                if (g == m.win_group && a < unsigned(m.win_n))
+                                    Acc<T>::add(S.h, m, kk * m.win_n + int(a), v, scale);
+                                else
+                                    global_add(b.hist, j, v, scale);
+                            } else {
+                                Acc<T>::add(S.h, m, j, v, scale);
+                            }
                         },
                         gxc && g == m.gx_group ? &gout : nullptr);
                 }
@@ -1391,6 +1433,17 @@ __device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, con
     for (int o = 16; o > 0; o >>= 1) wdep += __shfl_xor_sync(0xffffffffu, wdep, o);
     if ((threadIdx.x & 31) == 0 && wdep != T(0)) atomicAdd(&b.sc->Wcheck, double(wdep));
     __syncthreads();
+    if (GA) {  // the aperture window's sums go to their observables' global words
+        const GroupDesc &G = m.g[m.win_group < 0 ? 0 : m.win_group];
+        const int slots = m.win_n > 0 ? G.n_kinds * m.win_n : 0;
+        for (int q = threadIdx.x; q < WPS * slots; q += blockDim.x) {
+            const int slot = q / WPS, wd = q - slot * WPS;
+            const int kk = slot / m.win_n, a = slot - kk * m.win_n;
+            const long long v = Acc<T>::word(S.h, m, q);
+            const int j = G.obs_off + kk * G.n_ap + m.win_lo + a;
+            if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + WPS * j + wd), static_cast<unsigned long long>(v));
+        }
+    }
     const int words = GA ? 0 : (prior_step ? m.hist_words : m.off_grid);
     for (int q = threadIdx.x; q < words; q += blockDim.x) {
         if (q >= WPS * m.J && q < WPS * (m.J + 1)) continue;  // the total is already global
@@ -1406,7 +1459,7 @@ __global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> 
                                                     const Buffers b, int push, int init)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Smem<T> S = carve<T>(m, smem, GA ? 0 : 1, GA ? 0 : 1);
+    const Smem<T> S = carve<T>(m, smem, GA ? 2 : 1, GA ? 0 : 1, GA ? 0 : 1);
     __shared__ bool am_last;
 
     const StepFlags<T> f = step_flags<T>(m, *b.sc, init);
