@@ -158,8 +158,12 @@ typedef struct {
                                       M2M_UPDATE_EULER: w <- w (1 + eps dt F) */
     int64_t n_relax;               /* steps t <= n_relax update no weights (Sec. 4.1) */
     void *stream;                  /* cudaStream_t to run on; NULL: the library creates one */
-    int32_t block;                 /* threads per block of the step kernel; 0: tuned */
-    int32_t blocks_per_sm;         /* resident blocks per SM; 0: tuned */
+    int32_t block;                 /* threads per block of the step kernel, a multiple of 32: at most
+                                      256, or 1024 for the mixed-precision global-deposit kernel;
+                                      0: 256 (512 for the global-deposit kernel) */
+    int32_t blocks_per_sm;         /* resident blocks per SM; 0: as many as fit. With global
+                                      deposits it also sizes the aperture window (a share of
+                                      the SM's shared memory per block) */
     int32_t deposit;               /* M2M_DEPOSIT_*: where the step kernel accumulates y_j */
 } m2m_options;
 

@@ -352,46 +352,54 @@ static typename StepKernel<T>::Fn step_kernel(const m2m_ctx *c)
     return reinterpret_cast<typename StepKernel<T>::Fn>(c->kstep);
 }
 
-// Resident blocks per SM the aperture window of the global-deposit kernel is sized for.
-static const int kGlobalDepositBlocks = 3;
-
 template <class T, int WPS>
 static m2m_status configure_kernels(m2m_ctx *ctx)
 {
+    Model &m = ctx->m;
     // the finalize reuses the start of the dynamic shared memory for a block reduction
-    const size_t red = size_t(256) * sizeof(double);
-    const size_t smem_shared = std::max(smem_bytes<T>(ctx->m, 1, 1), red);
-    // global deposit: an aperture window of the largest group keeps block-shared sums,
-    // sized so that kGlobalDepositBlocks blocks fit on an SM
-    {
-        Model &m = ctx->m;
-        int smsm = 0;
-        CU(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-        int best = 0;
-        for (int g = 1; g < m.n_groups; ++g)
-            if (m.g[g].n_kinds * m.g[g].n_ap > m.g[best].n_kinds * m.g[best].n_ap) best = g;
-        m.win_group = best;
-        m.win_n = 0;
-        const long long per_block = smsm / kGlobalDepositBlocks - 2048 - (long long)smem_bytes<T>(m, 0, 0, 0);
-        const long long slot_bytes = sizeof(T) == 8 ? 16 : 12;
-        if (per_block > 0) m.win_n = int(std::min<long long>(m.g[best].n_ap, per_block / (slot_bytes * m.g[best].n_kinds)));
-        m.win_lo = (m.g[best].n_ap - m.win_n) / 2;  // until the first deposit places it
-    }
-    const size_t smem_global = std::max(smem_bytes<T>(ctx->m, 2, 0, 0), red);
-    ctx->smem_mat = smem_bytes<T>(ctx->m, 0, 0);
-    int maxsm = 0;
+    const size_t smem_shared = std::max(smem_bytes<T>(m, 1, 1), size_t(256) * sizeof(double));
+    int maxsm = 0, smsm = 0;
     CU(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    CU(cudaDeviceGetAttribute(&smsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
     // block-shared sums while the sums and records fit in shared memory, else global deposits
     if (ctx->deposit == M2M_DEPOSIT_SHARED && smem_shared > size_t(maxsm))
         return fail(ctx, M2M_ERR_ARG, "shared deposit needs %zu B of shared memory (limit %d)", smem_shared, maxsm);
     ctx->global_dep = ctx->deposit == M2M_DEPOSIT_GLOBAL ||
                       (ctx->deposit == M2M_DEPOSIT_AUTO && smem_shared > size_t(maxsm));
-    ctx->smem_step = ctx->global_dep ? smem_global : smem_shared;
+    const int max_block = ctx->global_dep ? kStepMaxThreads<T, true> : kStepMaxThreads<T, false>;
+    // 512 threads in two blocks per SM was the fastest shape of the mixed-precision
+    // global-deposit kernel on 64x64 maps (1024 x 1 and 256 x 4 were 8-10 % slower)
+    if (ctx->block == 0) ctx->block = std::min(max_block, 512);
+    if (ctx->block % 32 != 0 || ctx->block < 32 || ctx->block > max_block)
+        return fail(ctx, M2M_ERR_ARG, "block must be a multiple of 32, <= %d", max_block);
+    ctx->kstep = reinterpret_cast<void *>(ctx->global_dep ? pick_step<T, WPS, true>(m) : pick_step<T, WPS, false>(m));
+    const size_t red = size_t(ctx->block) * sizeof(double);
+    m.win_group = 0;
+    m.win_lo = m.win_n = 0;
+    if (ctx->global_dep) {
+        // an aperture window of the largest group keeps block-shared sums, as large as the
+        // blocks that registers and threads allow on an SM (or blocks_per_sm) leave room for
+        int rb = 0;
+        const size_t base = std::max(smem_bytes<T>(m, 0, 0, 0), red);
+        CU(cudaFuncSetAttribute(step_kernel<T>(ctx), cudaFuncAttributeMaxDynamicSharedMemorySize, int(base)));
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rb, step_kernel<T>(ctx), ctx->block, base));
+        if (rb < 1) return fail(ctx, M2M_ERR_ARG, "step kernel cannot be resident with block %d", ctx->block);
+        if (ctx->bps > 0 && ctx->bps < rb) rb = ctx->bps;
+        int best = 0;
+        for (int g = 1; g < m.n_groups; ++g)
+            if (m.g[g].n_kinds * m.g[g].n_ap > m.g[best].n_kinds * m.g[best].n_ap) best = g;
+        m.win_group = best;
+        // 1 KB per block is reserved by the runtime; 1 KB more covers the carve's alignment
+        const long long per_block = std::min<long long>(smsm / rb, maxsm) - 2048 - (long long)smem_bytes<T>(m, 0, 0, 0);
+        const long long slot_bytes = sizeof(T) == 8 ? 16 : 12;
+        if (per_block > 0) m.win_n = int(std::min<long long>(m.g[best].n_ap, per_block / (slot_bytes * m.g[best].n_kinds)));
+        m.win_lo = (m.g[best].n_ap - m.win_n) / 2;  // until the load places it
+    }
+    ctx->smem_step = ctx->global_dep ? std::max(smem_bytes<T>(m, 2, 0, 0), red) : smem_shared;
+    ctx->smem_mat = smem_bytes<T>(m, 0, 0);
     if (ctx->smem_step > size_t(maxsm))
         return fail(ctx, M2M_ERR_ARG, "observable tables and prior grid need %zu B of shared memory (limit %d)",
                     ctx->smem_step, maxsm);
-    ctx->kstep = reinterpret_cast<void *>(ctx->global_dep ? pick_step<T, WPS, true>(ctx->m)
-                                                           : pick_step<T, WPS, false>(ctx->m));
     CU(cudaFuncSetAttribute(step_kernel<T>(ctx), cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_step)));
     CU(cudaFuncSetAttribute(k_materialize<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ctx->smem_mat)));
     int occ = 0;
@@ -487,8 +495,7 @@ m2m_status create_impl(const m2m_potential *pot, const m2m_observables *obs,
         if (e != cudaSuccess) s = fail(ctx, M2M_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
     }
     if (s == M2M_OK) {
-        ctx->block = (opt->block > 0) ? opt->block : 256;
-        if (ctx->block % 32 != 0 || ctx->block > 256) s = fail(ctx, M2M_ERR_ARG, "block must be a multiple of 32, <= 256");
+        ctx->block = opt->block > 0 ? opt->block : 0;  // checked once the deposit is known
         ctx->bps = opt->blocks_per_sm;
         ctx->deposit = opt->deposit;
         if (ctx->deposit < M2M_DEPOSIT_AUTO || ctx->deposit > M2M_DEPOSIT_GLOBAL)
@@ -820,11 +827,11 @@ extern "C" m2m_status m2m_synchronize(m2m_ctx *ctx)
 template <class T, int WPS>
 static void launch_materialize(m2m_ctx *c)
 {
-    const int g = grid_for(c);
+    const int g = c->nsm * 4;
     cudaMemsetAsync(c->d_acc, 0, 2 * sizeof(long long), c->stream);
-    k_materialize<T><<<g, c->block, c->smem_mat, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c), buffers(c),
-                                                              c->d_wout, c->d_acc);
-    k_scale<<<g, c->block, 0, c->stream>>>(c->d_wout, c->n, c->d_acc, c->m, c->d_sc);
+    k_materialize<T><<<g, 256, c->smem_mat, c->stream>>>(c->m, make_cst<T>(c->m), state<T>(c), buffers(c),
+                                                         c->d_wout, c->d_acc);
+    k_scale<<<g, 256, 0, c->stream>>>(c->d_wout, c->n, c->d_acc, c->m, c->d_sc);
 }
 
 extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)

@@ -1130,6 +1130,20 @@ static __device__ void build_records(const Model &m, const Buffers &b)
 // Run by the last block of the step kernel once every block has added its sums:
 // converts the fixed-point sums, renormalises, smooths (eq. myts), forms Delta_j,
 // chi^2 (eqs. delta, chi) and the force-of-change coefficients, the prior means on
+// Sums red[0 .. blockDim) into red[0] for any block size: the part above the largest
+// power of two is folded in first. Called after red is written and synchronised.
+__device__ __forceinline__ void block_fold(double *red)
+{
+    int p2 = 1;
+    while (2 * p2 <= int(blockDim.x)) p2 *= 2;
+    if (int(threadIdx.x) >= p2) red[threadIdx.x - p2] += red[threadIdx.x];
+    __syncthreads();
+    for (int s = p2 / 2; s > 0; s >>= 1) {
+        if (int(threadIdx.x) < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+}
+
 // update steps, and clears the sums for the next step. red: blockDim doubles.
 template <int WPS>
 __device__ void finalize_block(const Model &m, const Buffers &b, long long n, int init, int prior_step,
@@ -1163,10 +1177,7 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
     red[threadIdx.x] = part;
     __syncthreads();
     build_records(m, b);
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-        __syncthreads();
-    }
+    block_fold(red);
     if (prior_step) {
         for (int c = threadIdx.x; c < m.ncell; c += blockDim.x) {
             const long long cnt = __ldcg(b.hist + m.off_count + c);
@@ -1239,20 +1250,25 @@ __device__ __forceinline__ const float *global_isp<float>(const Buffers &b) { re
 
 // One deposit into the global sums (global-deposit mode): the fixed-point words of
 // the block-shared path, added directly.
+// Adds v to a 64-bit integer sum in global memory, without reading the result back.
+__device__ __forceinline__ void red_add(long long *p, long long v)
+{
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ void global_add(long long *hist, int slot, double v, double scale)
 {
     if (is_zero(v)) return;
     long long hi, lo;
     fx2(v, scale, hi, lo);
-    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * slot), static_cast<unsigned long long>(hi));
-    if (lo) atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * slot + 1), static_cast<unsigned long long>(lo));
+    red_add(hist + 2 * slot, hi);
+    if (lo) red_add(hist + 2 * slot + 1, lo);
 }
 __device__ __forceinline__ void global_add(long long *hist, int slot, float v, float scale)
 {
     if (v == 0.f) return;
     const Limbs l = split(v, scale);
-    atomicAdd(reinterpret_cast<unsigned long long *>(hist + slot),
-              static_cast<unsigned long long>(limbs_value(l.hi, l.mid, l.lo)));
+    red_add(hist + slot, limbs_value(l.hi, l.mid, l.lo));
 }
 
 // Per-step flags of one fit, read from its scalars at the start of the step.
@@ -1405,7 +1421,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         if (f.prior_step) {
             const int c = prior_cell(m, k, b.lcE, x, y, z, vx, vy, vz);
             deposit(m.J + 1 + c, w, k.fx_w);
-            if constexpr (GA) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + m.off_count + c), 1ull);
+            if constexpr (GA) red_add(b.hist + m.off_count + c, 1);
             else Acc<T>::count(S.h, m, c);
             P.cell[i] = static_cast<uint16_t>(c);
         }
@@ -1428,7 +1444,7 @@ __device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, con
         long long v = wtot.word(q, k.fx_w);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0 && v != 0)
-            atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + WPS * m.J + q), static_cast<unsigned long long>(v));
+            red_add(b.hist + WPS * m.J + q, v);
     }
     for (int o = 16; o > 0; o >>= 1) wdep += __shfl_xor_sync(0xffffffffu, wdep, o);
     if ((threadIdx.x & 31) == 0 && wdep != T(0)) atomicAdd(&b.sc->Wcheck, double(wdep));
@@ -1441,21 +1457,27 @@ __device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, con
             const int kk = slot / m.win_n, a = slot - kk * m.win_n;
             const long long v = Acc<T>::word(S.h, m, q);
             const int j = G.obs_off + kk * G.n_ap + m.win_lo + a;
-            if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + WPS * j + wd), static_cast<unsigned long long>(v));
+            if (v != 0) red_add(b.hist + WPS * j + wd, v);
         }
     }
     const int words = GA ? 0 : (prior_step ? m.hist_words : m.off_grid);
     for (int q = threadIdx.x; q < words; q += blockDim.x) {
         if (q >= WPS * m.J && q < WPS * (m.J + 1)) continue;  // the total is already global
         const long long v = Acc<T>::word(S.h, m, q);
-        if (v != 0) atomicAdd(reinterpret_cast<unsigned long long *>(b.hist + q), static_cast<unsigned long long>(v));
+        if (v != 0) red_add(b.hist + q, v);
     }
     __threadfence();
     __syncthreads();
 }
 
+// Threads per block the step kernel is compiled for. The mixed-precision global-deposit
+// kernel runs up to 1024 threads in one block per SM, so that one aperture window takes
+// the whole shared memory of the SM.
+template <class T, bool GA>
+constexpr int kStepMaxThreads = (GA && sizeof(T) == 4) ? 1024 : 256;
+
 template <class T, int WPS, int MINB, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-__global__ void __launch_bounds__(256, MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
+__global__ void __launch_bounds__(kStepMaxThreads<T, GA>, (GA && sizeof(T) == 4) ? 1 : MINB) k_step(const Model m, const Cst<T> k, const State<T> P,
                                                     const Buffers b, int push, int init)
 {
     extern __shared__ __align__(16) unsigned char smem[];
