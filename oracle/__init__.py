@@ -79,6 +79,13 @@ class Params(C.Structure):
 
 
 _DP = C.POINTER(C.c_double)
+_LP = C.POINTER(C.c_long)
+_IP = C.POINTER(C.c_int)
+
+
+class SphGrid(C.Structure):
+    _fields_ = [("n_r", C.c_int), ("n_phi", C.c_int), ("n_ct", C.c_int), ("r_min", C.c_double),
+                ("r_max", C.c_double)]
 
 
 class Particles(C.Structure):
@@ -121,6 +128,17 @@ def lib():
         L.or_smooth_penalty.argtypes = [C.c_int, C.c_int, _DP]
         L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
         L.or_smooth_grid.restype = C.c_int
+        L.or_sph_bin.argtypes = [C.POINTER(SphGrid), C.c_double, C.c_double, C.c_double]
+        L.or_sph_velocity.argtypes = [C.c_double] * 6 + [_DP, _DP, _DP]
+        L.or_kin_sums.argtypes = [C.POINTER(SphGrid), C.POINTER(Particles), _DP, _LP]
+        L.or_kin_moments.argtypes = [C.c_long, _DP, _LP, C.c_long, _DP, _DP, _IP]
+        L.or_delta_kin.argtypes = [C.c_long, _DP, _LP, _DP, _LP, C.c_long, _DP]
+        L.or_delta_kin.restype = C.c_long
+        L.or_grid_weights.argtypes = [C.POINTER(Potential), C.POINTER(Prior), C.POINTER(Particles), _DP, _DP, _LP]
+        L.or_delta_grid.argtypes = [C.c_int, _DP, _DP]
+        L.or_delta_grid.restype = C.c_double
+        L.or_weight_rms.argtypes = [C.c_int, _DP, _LP, C.c_long]
+        L.or_weight_rms.restype = C.c_double
         L.or_build_targets.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP, _DP, _DP, _DP,
                                        _DP, _DP, C.POINTER(C.c_int)]
         _lib = L
@@ -362,3 +380,83 @@ def from_workload(wl, target_particles=None):
     tp = ParticleSet(wl.target if target_particles is None else target_particles)
     Y, sig, _ = build_targets(obs, tp, wl.err_per_obs(), wl.noise)
     return obs, Y, sig
+
+
+# ---------------------------------------------------------------------------
+# diagnostics (Sec. 4.1, Sec. 5)
+# ---------------------------------------------------------------------------
+
+KIN_SUMS = 7
+
+
+def _lp(a: np.ndarray):
+    assert a.dtype == np.int64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_LP)
+
+
+def sph_grid(d: dict) -> SphGrid:
+    return SphGrid(d["n_r"], d["n_phi"], d["n_ct"], d["r_min"], d["r_max"])
+
+
+def sph_bin(grid: dict, x, y, z) -> int:
+    return lib().or_sph_bin(C.byref(sph_grid(grid)), x, y, z)
+
+
+def sph_velocity(x, y, z, vx, vy, vz):
+    o = [C.c_double(), C.c_double(), C.c_double()]
+    lib().or_sph_velocity(x, y, z, vx, vy, vz, *[C.byref(v) for v in o])
+    return np.array([v.value for v in o])
+
+
+def kin_sums(grid: dict, ps: ParticleSet):
+    """(sums[nbins, 7], counts[nbins]) of the spherical-bin kinematics."""
+    nb = grid["n_r"] * grid["n_phi"] * grid["n_ct"]
+    sums = np.zeros(nb * KIN_SUMS)
+    cnt = np.zeros(nb, np.int64)
+    lib().or_kin_sums(C.byref(sph_grid(grid)), C.byref(ps.s), _dp(sums), _lp(cnt))
+    return sums.reshape(nb, KIN_SUMS), cnt
+
+
+def kin_moments(sums, counts, min_count: int = 1):
+    """(mean[nbins, 3], disp[nbins, 3], valid[nbins]) from kin_sums."""
+    sums = np.ascontiguousarray(sums, np.float64).ravel()
+    counts = np.ascontiguousarray(counts, np.int64)
+    nb = len(counts)
+    mean, disp = np.zeros(3 * nb), np.zeros(3 * nb)
+    valid = np.zeros(nb, np.int32)
+    lib().or_kin_moments(nb, _dp(sums), _lp(counts), min_count, _dp(mean), _dp(disp),
+                         valid.ctypes.data_as(_IP))
+    return mean.reshape(nb, 3), disp.reshape(nb, 3), valid.astype(bool)
+
+
+def delta_kin(sums_m, counts_m, sums_t, counts_t, min_count: int = 1):
+    """(out[7], bins used): rms model-minus-target difference of the six moments, and overall."""
+    sm = np.ascontiguousarray(sums_m, np.float64).ravel()
+    st = np.ascontiguousarray(sums_t, np.float64).ravel()
+    cm = np.ascontiguousarray(counts_m, np.int64)
+    ct = np.ascontiguousarray(counts_t, np.int64)
+    out = np.zeros(7)
+    used = lib().or_delta_kin(len(cm), _dp(sm), _lp(cm), _dp(st), _lp(ct), min_count, _dp(out))
+    return out, used
+
+
+def grid_weights(pot: dict, pri: dict, ps: ParticleSet):
+    """(wsum, wdev2, count) per (E, x) cell of the prior grid."""
+    nc = pri["nE"] * pri["nx"]
+    ws, wd = np.zeros(nc), np.zeros(nc)
+    cnt = np.zeros(nc, np.int64)
+    P, G = potential(pot), prior(pri)
+    lib().or_grid_weights(C.byref(P), C.byref(G), C.byref(ps.s), _dp(ws), _dp(wd), _lp(cnt))
+    return ws, wd, cnt
+
+
+def delta_grid(w_model, w_target) -> float:
+    wm = np.ascontiguousarray(w_model, np.float64)
+    wt = np.ascontiguousarray(w_target, np.float64)
+    return lib().or_delta_grid(len(wm), _dp(wm), _dp(wt))
+
+
+def weight_rms(wdev2, count, min_count: int = 50) -> float:
+    wd = np.ascontiguousarray(wdev2, np.float64)
+    cnt = np.ascontiguousarray(count, np.int64)
+    return lib().or_weight_rms(len(wd), _dp(wd), _lp(cnt), min_count)

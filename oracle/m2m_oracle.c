@@ -29,6 +29,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 static const double OR_PI = 3.14159265358979323846;
 
 /* ------------------------------------------------------------------ */
@@ -718,4 +722,176 @@ int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, do
     free(M);
     free(col);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics (Sec. 4.1: Delta_grid, intrinsic kinematics in          */
+/* spherical bins; Sec. 5, Fig. res: weight rms in the (E, x) cells)   */
+/* ------------------------------------------------------------------ */
+
+int or_sph_bin(const or_sph_grid *g, double x, double y, double z)
+{
+    double r = sqrt(x * x + y * y + z * z);
+    if (!(r < g->r_max)) return -1;
+    int ir;
+    if (r < g->r_min) {
+        ir = 0;
+    } else {
+        double f = (log(r) - log(g->r_min)) / (log(g->r_max) - log(g->r_min));
+        ir = 1 + (int)floor(f * (g->n_r - 1));
+        if (ir > g->n_r - 1) ir = g->n_r - 1;
+    }
+    double ct = r > 0.0 ? z / r : 1.0;
+    int ic = (int)floor((ct + 1.0) * 0.5 * g->n_ct);
+    if (ic < 0) ic = 0;
+    if (ic > g->n_ct - 1) ic = g->n_ct - 1;
+    double phi = atan2(y, x);
+    int ip = (int)floor((phi + M_PI) / (2.0 * M_PI) * g->n_phi);
+    if (ip < 0) ip = 0;
+    if (ip > g->n_phi - 1) ip = g->n_phi - 1;
+    return (ir * g->n_ct + ic) * g->n_phi + ip;
+}
+
+void or_sph_velocity(double x, double y, double z, double vx, double vy, double vz,
+                     double *vr, double *vth, double *vph)
+{
+    double R = sqrt(x * x + y * y);
+    double r = sqrt(R * R + z * z);
+    double cp = 1.0, sp = 0.0;  /* azimuth 0 on the z axis */
+    if (R > 0.0) {
+        cp = x / R;
+        sp = y / R;
+    }
+    double ct = 1.0, st = 0.0;  /* e_r = e_z at the centre */
+    if (r > 0.0) {
+        ct = z / r;
+        st = R / r;
+    }
+    /* e_r = (st cp, st sp, ct), e_theta = (ct cp, ct sp, -st), e_phi = (-sp, cp, 0) */
+    *vr = vx * st * cp + vy * st * sp + vz * ct;
+    *vth = vx * ct * cp + vy * ct * sp - vz * st;
+    *vph = -vx * sp + vy * cp;
+}
+
+void or_kin_sums(const or_sph_grid *g, const or_particles *s, double *sums, long *counts)
+{
+    long nb = (long)g->n_r * g->n_ct * g->n_phi;
+    for (long b = 0; b < nb; ++b) {
+        counts[b] = 0;
+        for (int q = 0; q < OR_KIN_SUMS; ++q) sums[b * OR_KIN_SUMS + q] = 0.0;
+    }
+    for (long i = 0; i < s->n; ++i) {
+        int b = or_sph_bin(g, s->x[i], s->y[i], s->z[i]);
+        if (b < 0) continue;
+        double v[3];
+        or_sph_velocity(s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], &v[0], &v[1], &v[2]);
+        double w = s->w[i];
+        double *o = sums + (long)b * OR_KIN_SUMS;
+        o[0] += w;
+        for (int c = 0; c < 3; ++c) {
+            o[1 + c] += w * v[c];
+            o[4 + c] += w * v[c] * v[c];
+        }
+        counts[b] += 1;
+    }
+}
+
+void or_kin_moments(long nbins, const double *sums, const long *counts, long min_count,
+                    double *mean, double *disp, int *valid)
+{
+    for (long b = 0; b < nbins; ++b) {
+        const double *o = sums + b * OR_KIN_SUMS;
+        int ok = counts[b] >= min_count && counts[b] > 0 && o[0] > 0.0;
+        valid[b] = ok;
+        for (int c = 0; c < 3; ++c) {
+            double m = ok ? o[1 + c] / o[0] : 0.0;
+            double v2 = ok ? o[4 + c] / o[0] - m * m : 0.0;
+            mean[3 * b + c] = m;
+            disp[3 * b + c] = v2 > 0.0 ? sqrt(v2) : 0.0;
+        }
+    }
+}
+
+long or_delta_kin(long nbins, const double *sums_m, const long *counts_m, const double *sums_t,
+                  const long *counts_t, long min_count, double *out)
+{
+    double *mm = malloc(sizeof(double) * 3 * nbins), *dm = malloc(sizeof(double) * 3 * nbins);
+    double *mt = malloc(sizeof(double) * 3 * nbins), *dt = malloc(sizeof(double) * 3 * nbins);
+    int *vm = malloc(sizeof(int) * nbins), *vt = malloc(sizeof(int) * nbins);
+    or_kin_moments(nbins, sums_m, counts_m, min_count, mm, dm, vm);
+    or_kin_moments(nbins, sums_t, counts_t, min_count, mt, dt, vt);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    long used = 0;
+    for (long b = 0; b < nbins; ++b) {
+        if (!(vm[b] && vt[b])) continue;
+        for (int c = 0; c < 3; ++c) {
+            double d1 = mm[3 * b + c] - mt[3 * b + c];
+            double d2 = dm[3 * b + c] - dt[3 * b + c];
+            acc[c] += d1 * d1;
+            acc[3 + c] += d2 * d2;
+        }
+        used += 1;
+    }
+    double all = 0.0;
+    for (int q = 0; q < 6; ++q) {
+        out[q] = used > 0 ? sqrt(acc[q] / used) : 0.0;
+        all += acc[q];
+    }
+    out[6] = used > 0 ? sqrt(all / (6.0 * used)) : 0.0;
+    free(mm); free(dm); free(mt); free(dt); free(vm); free(vt);
+    return used;
+}
+
+void or_grid_weights(const or_potential *p, const or_prior *g, const or_particles *s,
+                     double *wsum, double *wdev2, long *count)
+{
+    int nc = g->nE * g->nx;
+    int *cell = malloc(sizeof(int) * (s->n > 0 ? s->n : 1));
+    for (int c = 0; c < nc; ++c) {
+        wsum[c] = 0.0;
+        wdev2[c] = 0.0;
+        count[c] = 0;
+    }
+    for (long i = 0; i < s->n; ++i) {
+        cell[i] = or_cell(p, g, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], NULL, NULL);
+        wsum[cell[i]] += s->w[i];
+        count[cell[i]] += 1;
+    }
+    for (long i = 0; i < s->n; ++i) {
+        int c = cell[i];
+        double d = s->w[i] - wsum[c] / (double)count[c];
+        wdev2[c] += d * d;
+    }
+    free(cell);
+}
+
+double or_delta_grid(int ncell, const double *w_model, const double *w_target)
+{
+    double tm = 0.0, tt = 0.0;
+    for (int c = 0; c < ncell; ++c) {
+        tm += w_model[c];
+        tt += w_target[c];
+    }
+    if (!(tm > 0.0) || !(tt > 0.0)) return 0.0;
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < ncell; ++c) {
+        double wt = w_target[c] / tt, wm = w_model[c] / tm;
+        if (!(wt > 0.0)) continue;
+        double r = (wt - wm) / wt;
+        num += wt * r * r;
+        den += wt;
+    }
+    return sqrt(num / den);
+}
+
+double or_weight_rms(int ncell, const double *wdev2, const long *count, long min_count)
+{
+    double s = 0.0;
+    long n = 0;
+    for (int c = 0; c < ncell; ++c) {
+        if (count[c] <= min_count) continue;
+        s += wdev2[c];
+        n += count[c];
+    }
+    return n > 0 ? sqrt(s / (double)n) : 0.0;
 }

@@ -127,6 +127,46 @@ void or_smooth_penalty(int nE, int nx, double *P);
  * Returns OR_OK or OR_EARG. */
 int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, double *lambda_out);
 
+/* ---- Diagnostics of a fitted particle model (Sec. 4.1; Sec. 5, Fig. res) ---- */
+
+/* Spherical polar bins of the intrinsic kinematics: n_r radial shells, the first [0, r_min)
+ * and n_r - 1 shells equally spaced in ln r from r_min to r_max (quasi-logarithmic); n_ct
+ * equal bins in cos(theta) on [-1, 1] (theta from the z axis); n_phi equal bins in the azimuth
+ * phi = atan2(y, x) on [-pi, pi]. Bin (i_r * n_ct + i_ct) * n_phi + i_phi; r >= r_max: -1. */
+typedef struct {
+    int n_r, n_phi, n_ct;
+    double r_min, r_max;
+} or_sph_grid;
+
+#define OR_KIN_SUMS 7  /* per bin: sum w, sum w v_r, w v_theta, w v_phi, w v_r^2, w v_theta^2, w v_phi^2 */
+
+int or_sph_bin(const or_sph_grid *g, double x, double y, double z);
+/* Velocity components along e_r, e_theta, e_phi. On the z axis phi = 0 is used; at r = 0,
+ * e_r = e_z. */
+void or_sph_velocity(double x, double y, double z, double vx, double vy, double vz,
+                     double *vr, double *vth, double *vph);
+/* Per-bin weighted sums (OR_KIN_SUMS per bin) and particle counts, zeroed first. */
+void or_kin_sums(const or_sph_grid *g, const or_particles *s, double *sums, long *counts);
+/* Mean velocities and dispersions of the bins with at least min_count particles and a
+ * positive mass (others: 0 and valid[b] = 0). mean, disp: 3 per bin (r, theta, phi). */
+void or_kin_moments(long nbins, const double *sums, const long *counts, long min_count,
+                    double *mean, double *disp, int *valid);
+/* rms over the bins valid in both models of the difference of each moment, model minus
+ * target: out[0..2] mean v_r, v_theta, v_phi; out[3..5] sigma_r, sigma_theta, sigma_phi;
+ * out[6] the rms over all six. Returns the number of bins used. */
+long or_delta_kin(long nbins, const double *sums_m, const long *counts_m, const double *sums_t,
+                  const long *counts_t, long min_count, double *out);
+/* Weights of the fit in the (E, x) grid of the priors: per cell the sum of weights, the count,
+ * and the sum of squared deviations from the cell's mean weight (two passes). */
+void or_grid_weights(const or_potential *p, const or_prior *g, const or_particles *s,
+                     double *wsum, double *wdev2, long *count);
+/* Mass-weighted relative rms difference of model and target cell weights (Sec. 4.1, eq. of
+ * Delta_grid), each normalised to unit total first; cells with no target weight are left out. */
+double or_delta_grid(int ncell, const double *w_model, const double *w_target);
+/* rms of the particle weights about their cell means over the cells with more than min_count
+ * particles (Fig. res): sqrt(sum wdev2 / sum count) over those cells; 0 if there are none. */
+double or_weight_rms(int ncell, const double *wdev2, const long *count, long min_count);
+
 int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
                      const double *noise, double *Vp_out, double *sp_out,
                      double *Y_out, double *sig_out, int *iters_out);
