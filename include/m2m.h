@@ -316,6 +316,76 @@ m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double
 m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, const double *pos_dev,
                               const double *vel_dev, const double *w_dev, double *y_dev, void *stream);
 
+/* ------------------------------------------------------------------ diagnostics
+ *
+ * How well a fit recovers what the data do not show directly (Sec. 4.1): the target's
+ * intrinsic kinematics, and its phase-space structure in the (E, x) grid of the priors
+ * (Delta_grid); and how smooth the particle model is, as the rms of the weights about
+ * their cell means (Sec. 5, Fig. res).
+ *
+ * The binning calls take either the fit's own particles (n = 0 and pos, vel, w all NULL:
+ * the state in the fit's precision and the weights of m2m_get_weights), or n particles
+ * from the caller's host arrays (pos, vel: 3n values each, x then y then z; w: n values),
+ * for example a realisation of the target. Bins are decided in FP64. Sums are FP64
+ * atomics: equal to an ordered sum up to rounding, not bit-reproducible. Outputs go to
+ * caller-owned host buffers. The calls synchronise the fit's stream. */
+
+/* Spherical polar bins of the intrinsic kinematics (Sec. 4.1): n_r shells, the first
+ * [0, r_min) and n_r - 1 shells equally spaced in ln r from r_min to r_max; n_ct equal
+ * bins of cos(theta) on [-1, 1], theta from the z axis; n_phi equal bins of the azimuth
+ * phi = atan2(y, x) on [-pi, pi] (theta = 0 at the centre, phi = 0 on the z axis; upper
+ * edges go to the last bin). Bin b = (i_r * n_ct + i_ct) * n_phi + i_phi. Particles with
+ * r >= r_max are not binned. */
+typedef struct {
+    int32_t n_r, n_phi, n_ct;      /* n_r >= 2, n_phi >= 1, n_ct >= 1, at most 2^24 bins */
+    double r_min, r_max;           /* 0 < r_min < r_max */
+} m2m_sph_grid;
+
+#define M2M_KIN_SUMS 7             /* per bin: sum w; sum w v_r, w v_theta, w v_phi;
+                                      sum w v_r^2, w v_theta^2, w v_phi^2 */
+
+/* Per-bin sums (nbins * M2M_KIN_SUMS doubles, bin-major) and particle counts (nbins,
+ * may be NULL) of the particles in the spherical grid; nbins = n_r * n_phi * n_ct.
+ * Errors: M2M_ERR_ARG (grid, sizes, arrays), M2M_ERR_STATE (no particles loaded, or a
+ * batch handle), M2M_ERR_CUDA / M2M_ERR_OOM. */
+m2m_status m2m_diag_kinematics(m2m_ctx *ctx, const m2m_sph_grid *grid, int64_t n, const double *pos,
+                               const double *vel, const double *w, double *sums, int64_t *counts,
+                               int64_t nbins);
+
+/* Weights of the particles in an (E, x) grid with the fit's potential: per cell the sum of
+ * weights wsum, the sum of squared deviations from the cell's mean weight wdev2 (two
+ * passes; may be NULL) and the count (may be NULL); ncell = nE * nx. grid NULL: the fit's
+ * own MPR grid (a GWR fit must pass one); its mode, update_every and smoothing are
+ * ignored. Errors as m2m_diag_kinematics. */
+m2m_status m2m_diag_grid(m2m_ctx *ctx, const m2m_prior_grid *grid, int64_t n, const double *pos,
+                         const double *vel, const double *w, double *wsum, double *wdev2,
+                         int64_t *counts, int32_t ncell);
+
+/* Mean velocities and dispersions (3 per bin: r, theta, phi) from the per-bin sums; bins
+ * with fewer than min_count particles or no mass get zeros and valid[b] = 0 (valid may
+ * be NULL). Host arithmetic; errors go to m2m_last_error(NULL). */
+m2m_status m2m_kin_moments(int64_t nbins, const double *sums, const int64_t *counts, int64_t min_count,
+                           double *mean, double *disp, int32_t *valid);
+
+/* Intrinsic-kinematics comparison (Sec. 4.1): over the bins valid in both (as in
+ * m2m_kin_moments), the rms of model minus target of each moment: out[0..2] mean v_r,
+ * v_theta, v_phi; out[3..5] sigma_r, sigma_theta, sigma_phi; out[6] the rms over all six.
+ * bins_used (may be NULL) receives the number of bins compared. Host arithmetic. */
+m2m_status m2m_delta_kin(int64_t nbins, const double *sums_model, const int64_t *counts_model,
+                         const double *sums_target, const int64_t *counts_target, int64_t min_count,
+                         double *out, int64_t *bins_used);
+
+/* Delta_grid (Sec. 4.1): sqrt(sum_c wt_c ((wt_c - wm_c)/wt_c)^2 / sum_c wt_c) with the model's
+ * and the target's cell weights each normalised to unit total first; cells without target
+ * weight are left out; 0 if either total is not positive. Host arithmetic. */
+m2m_status m2m_delta_grid(int32_t ncell, const double *w_model, const double *w_target, double *delta);
+
+/* rms of the particle weights about their cell means (Sec. 5, Fig. res) over the cells
+ * with more than min_count particles: sqrt(sum wdev2 / sum counts); 0 if there are none.
+ * Host arithmetic. */
+m2m_status m2m_weight_rms(int32_t ncell, const double *wdev2, const int64_t *counts, int64_t min_count,
+                          double *rms);
+
 /* One-line description of the last error on this context ("" if none); valid
  * until the next call on the context. ctx may be NULL for creation errors. */
 const char *m2m_last_error(const m2m_ctx *ctx);

@@ -121,6 +121,16 @@ def lib():
         L.m2m_batch_model.argtypes = [vp, C.c_int32, C.POINTER(vp)]
         L.m2m_batch_autotune.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int64)]
+        _I64P = C.POINTER(C.c_int64)
+        L.m2m_diag_kinematics.argtypes = [vp, C.POINTER(SphGrid), C.c_int64, _DP, _DP, _DP, _DP, _I64P, C.c_int64]
+        L.m2m_diag_grid.argtypes = [vp, C.POINTER(PriorGrid), C.c_int64, _DP, _DP, _DP, _DP, _DP, _I64P, C.c_int32]
+        L.m2m_kin_moments.argtypes = [C.c_int64, _DP, _I64P, C.c_int64, _DP, _DP, C.POINTER(C.c_int32)]
+        L.m2m_delta_kin.argtypes = [C.c_int64, _DP, _I64P, _DP, _I64P, C.c_int64, _DP, _I64P]
+        L.m2m_delta_grid.argtypes = [C.c_int32, _DP, _DP, _DP]
+        L.m2m_weight_rms.argtypes = [C.c_int32, _DP, _I64P, C.c_int64, _DP]
+        for name in ("m2m_diag_kinematics", "m2m_diag_grid", "m2m_kin_moments", "m2m_delta_kin",
+                     "m2m_delta_grid", "m2m_weight_rms"):
+            getattr(L, name).restype = C.c_int
         for name in ("m2m_create", "m2m_load_particles", "m2m_load_particles_device", "m2m_step",
                      "m2m_synchronize", "m2m_get_weights", "m2m_get_state", "m2m_get_observables",
                      "m2m_get_chi2", "m2m_get_priors", "m2m_get_step_count", "m2m_get_particle_count",
@@ -184,6 +194,70 @@ class ObsDesc:
             self.sig = np.ascontiguousarray(sig, np.float64)
             self.o.Y = _dp(self.Y)
             self.o.sigY = _dp(self.sig)
+
+
+class SphGrid(C.Structure):
+    _fields_ = [("n_r", C.c_int32), ("n_phi", C.c_int32), ("n_ct", C.c_int32), ("r_min", C.c_double),
+                ("r_max", C.c_double)]
+
+
+KIN_SUMS = 7
+
+
+def _i64(a):
+    assert a.dtype == np.int64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_int64))
+
+
+def _particles(particles):
+    """(n, pos, vel, w) SoA host arrays of a particle dict, or the fit's own (0, None...)."""
+    if particles is None:
+        return 0, None, None, None
+    pos = _soa(particles, ("x", "y", "z"))
+    vel = _soa(particles, ("vx", "vy", "vz"))
+    w = np.ascontiguousarray(particles["w"], np.float64)
+    return len(w), pos, vel, w
+
+
+def kin_moments(sums, counts, min_count: int = 1):
+    """(mean[nb, 3], disp[nb, 3], valid[nb]) of the spherical-bin sums (m2m_kin_moments)."""
+    sums = np.ascontiguousarray(sums, np.float64).ravel()
+    counts = np.ascontiguousarray(counts, np.int64)
+    nb = len(counts)
+    mean, disp = np.zeros(3 * nb), np.zeros(3 * nb)
+    valid = np.zeros(nb, np.int32)
+    _check(lib().m2m_kin_moments(nb, _dp(sums), _i64(counts), min_count, _dp(mean), _dp(disp),
+                                 valid.ctypes.data_as(C.POINTER(C.c_int32))))
+    return mean.reshape(nb, 3), disp.reshape(nb, 3), valid.astype(bool)
+
+
+def delta_kin(sums_m, counts_m, sums_t, counts_t, min_count: int = 1):
+    """(out[7], bins used): rms model-minus-target difference of the six moments (m2m_delta_kin)."""
+    sm = np.ascontiguousarray(sums_m, np.float64).ravel()
+    st = np.ascontiguousarray(sums_t, np.float64).ravel()
+    cm = np.ascontiguousarray(counts_m, np.int64)
+    ct = np.ascontiguousarray(counts_t, np.int64)
+    out = np.zeros(7)
+    used = C.c_int64()
+    _check(lib().m2m_delta_kin(len(cm), _dp(sm), _i64(cm), _dp(st), _i64(ct), min_count, _dp(out),
+                               C.byref(used)))
+    return out, used.value
+
+
+def delta_grid(w_model, w_target) -> float:
+    wm = np.ascontiguousarray(w_model, np.float64)
+    wt = np.ascontiguousarray(w_target, np.float64)
+    d = C.c_double()
+    _check(lib().m2m_delta_grid(len(wm), _dp(wm), _dp(wt), C.byref(d)))
+    return d.value
+
+
+def weight_rms(wdev2, counts, min_count: int = 50) -> float:
+    wd = np.ascontiguousarray(wdev2, np.float64)
+    cnt = np.ascontiguousarray(counts, np.int64)
+    r = C.c_double()
+    _check(lib().m2m_weight_rms(len(wd), _dp(wd), _i64(cnt), min_count, C.byref(r)))
+    return r.value
 
 
 def prior_grid(d: dict) -> PriorGrid:
@@ -307,6 +381,30 @@ class Fit:
         self._ck(lib().m2m_get_priors(self.h, _dp(g), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                       cells.ctypes.data_as(C.POINTER(C.c_int32)), self.n))
         return g[:self.ncell], cnt[:self.ncell], cells
+
+    def diag_kinematics(self, grid: dict, particles: dict | None = None):
+        """(sums[nbins, 7], counts[nbins]) of the fit's particles (or of `particles`, a dict
+        of x..vz, w host arrays) in spherical polar bins (m2m_diag_kinematics)."""
+        g = SphGrid(grid["n_r"], grid["n_phi"], grid["n_ct"], grid["r_min"], grid["r_max"])
+        nb = grid["n_r"] * grid["n_phi"] * grid["n_ct"]
+        sums = np.zeros(nb * KIN_SUMS)
+        cnt = np.zeros(nb, np.int64)
+        n, pos, vel, w = _particles(particles)
+        self._ck(lib().m2m_diag_kinematics(self.h, C.byref(g), n, _dp(pos), _dp(vel), _dp(w), _dp(sums),
+                                           _i64(cnt), nb))
+        return sums.reshape(nb, KIN_SUMS), cnt
+
+    def diag_grid(self, grid: dict | None = None, particles: dict | None = None):
+        """(wsum, wdev2, counts) per (E, x) cell of the fit's grid (or `grid`) for the fit's
+        particles (or `particles`) (m2m_diag_grid)."""
+        G = None if grid is None else prior_grid(dict(grid, mode=grid.get("mode", "mpr")))
+        nc = grid["nE"] * grid["nx"] if grid is not None else self.ncell
+        ws, wd = np.zeros(max(nc, 1)), np.zeros(max(nc, 1))
+        cnt = np.zeros(max(nc, 1), np.int64)
+        n, pos, vel, w = _particles(particles)
+        self._ck(lib().m2m_diag_grid(self.h, None if G is None else C.byref(G), n, _dp(pos), _dp(vel), _dp(w),
+                                     _dp(ws), _dp(wd), _i64(cnt), nc))
+        return ws[:nc], wd[:nc], cnt[:nc]
 
     def prior_smoothing(self):
         """(raw cell means of the last prior update, smoothing weight used) with smoothing on."""

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SO = os.path.join(HERE, "_build", "libm2m.so")
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = [os.path.join(CSRC, f) for f in ("m2m_api.cu", "m2m_batch.cu", "m2m_smooth.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("m2m_api.cu", "m2m_batch.cu", "m2m_smooth.cu", "m2m_diag.cu")]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -70,6 +70,33 @@ static void free_state(m2m_ctx *c)
 
 // ------------------------------------------------------------------ creation
 
+m2m_status grid_fields(m2m_ctx *ctx, Model &m, const m2m_prior_grid *pg)
+{
+    m.nE = pg->nE;
+    m.nx = pg->nx;
+    m.e_spacing = pg->e_spacing;
+    m.signed_lz = pg->signed_lz ? 1 : 0;
+    if (m.nE < 1 || m.nx < 1 || (long long)m.nE * m.nx > 65535)
+        return fail(ctx, M2M_ERR_ARG, "the (E, x) grid needs nE, nx >= 1, nE*nx <= 65535");
+    const double lo = pg->Emin, hi = pg->Emax;
+    if (!(hi > lo)) return fail(ctx, M2M_ERR_ARG, "prior grid needs Emax > Emin");
+    if (m.e_spacing == M2M_E_LOGNEG) {
+        if (!(hi < 0)) return fail(ctx, M2M_ERR_ARG, "ln(-E) spacing needs Emin < Emax < 0");
+        m.s_lo = std::log(-lo);
+        m.s_den = std::log(-hi) - std::log(-lo);
+    } else if (m.e_spacing == M2M_E_EXP) {
+        m.s_lo = std::exp(lo);
+        m.s_den = std::exp(hi) - std::exp(lo);
+    } else if (m.e_spacing == M2M_E_LINEAR) {
+        m.s_lo = lo;
+        m.s_den = hi - lo;
+    } else {
+        return fail(ctx, M2M_ERR_ARG, "unknown E spacing");
+    }
+    m.ncell = m.nE * m.nx;
+    return M2M_OK;
+}
+
 static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_observables *obs,
                               const m2m_prior_grid *pg, const m2m_options *opt)
 {
@@ -228,24 +255,9 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.signed_lz = pg->signed_lz ? 1 : 0;
     m.update_every = pg->update_every;
     if (m.mode == M2M_REG_MPR) {
-        if (m.nE < 1 || m.nx < 1 || (long long)m.nE * m.nx > 65535 || m.update_every < 1)
-            return fail(ctx, M2M_ERR_ARG, "MPR grid needs nE, nx >= 1, nE*nx <= 65535, update_every >= 1");
-        const double lo = pg->Emin, hi = pg->Emax;
-        if (!(hi > lo)) return fail(ctx, M2M_ERR_ARG, "prior grid needs Emax > Emin");
-        if (m.e_spacing == M2M_E_LOGNEG) {
-            if (!(hi < 0)) return fail(ctx, M2M_ERR_ARG, "ln(-E) spacing needs Emin < Emax < 0");
-            m.s_lo = std::log(-lo);
-            m.s_den = std::log(-hi) - std::log(-lo);
-        } else if (m.e_spacing == M2M_E_EXP) {
-            m.s_lo = std::exp(lo);
-            m.s_den = std::exp(hi) - std::exp(lo);
-        } else if (m.e_spacing == M2M_E_LINEAR) {
-            m.s_lo = lo;
-            m.s_den = hi - lo;
-        } else {
-            return fail(ctx, M2M_ERR_ARG, "unknown E spacing");
-        }
-        m.ncell = m.nE * m.nx;
+        if (m.update_every < 1) return fail(ctx, M2M_ERR_ARG, "MPR grid needs update_every >= 1");
+        m2m_status gs = grid_fields(ctx, m, pg);
+        if (gs != M2M_OK) return gs;
     } else {
         m.ncell = 0;
         m.update_every = 1;
@@ -841,16 +853,23 @@ extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (n != ctx->n || (n > 0 && !w)) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count (%lld)", ctx->n);
     if (n == 0) return m2m_synchronize(ctx);
-    if (ctx->wout_cap < n) {
+    m2m_status s = current_weights(ctx);
+    if (s != M2M_OK) return s;
+    CU(cudaMemcpyAsync(w, ctx->d_wout, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    return m2m_synchronize(ctx);
+}
+
+m2m_status current_weights(m2m_ctx *ctx)
+{
+    if (ctx->wout_cap < ctx->n) {
         free_dev(ctx->d_wout);
-        CU(cudaMalloc(&ctx->d_wout, sizeof(double) * n));
-        ctx->wout_cap = n;
+        CU(cudaMalloc(&ctx->d_wout, sizeof(double) * ctx->n));
+        ctx->wout_cap = ctx->n;
     }
     if (ctx->precision == M2M_PREC_FP64) launch_materialize<double, 2>(ctx);
     else launch_materialize<float, 1>(ctx);
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(w, ctx->d_wout, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
-    return m2m_synchronize(ctx);
+    return M2M_OK;
 }
 
 extern "C" m2m_status m2m_get_state(m2m_ctx *ctx, double *pos, double *vel, int64_t n)

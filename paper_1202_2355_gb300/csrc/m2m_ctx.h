@@ -97,6 +97,13 @@ m2m_status check_device_errors(m2m_ctx *ctx);
 m2m::Buffers buffers(m2m_ctx *c);
 void destroy_impl(m2m_ctx *ctx);
 
+// The (E, x) grid fields of a model (nE, nx, spacing, signed L_z, s_lo, s_den, ncell)
+// from a grid descriptor, validated.
+m2m_status grid_fields(m2m_ctx *ctx, m2m::Model &m, const m2m_prior_grid *pg);
+// The fit's weights as of the end of its last step into ctx->d_wout (n doubles), queued
+// on ctx->stream (the pending update applied, as m2m_get_weights).
+m2m_status current_weights(m2m_ctx *ctx);
+
 // prior smoothing (m2m_smooth.cu)
 m2m_status smooth_setup(m2m_ctx *ctx);
 void smooth_free(m2m_ctx *ctx);

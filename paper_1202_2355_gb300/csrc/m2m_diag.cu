@@ -1,0 +1,392 @@
+// Diagnostics of a fitted particle model on the device.
+//
+// Sec. 4.1 judges a fit by how well it recovers the target's intrinsic kinematics and
+// its phase-space structure:
+// - the intrinsic velocity moments (streaming velocities and dispersions along e_r,
+//   e_theta, e_phi) in spherical polar bins: shells quasi-logarithmic in r, equal bins in
+//   the azimuth phi and in cos(theta); the comparison with the target is the rms
+//   difference of each moment over the bins both models populate;
+// - Delta_grid, the mass-weighted relative rms difference of the model's and the
+//   target's weights in the (E, x) cells of the prior grid.
+// Sec. 5 (Fig. res) adds the rms of the particle weights about their cell means over the
+// cells holding more than a minimum number of particles.
+//
+// The kernels bin either the fit's own particles (their state in the fit's precision,
+// with the weights as of the end of the last step) or particles the caller passes from
+// the host (a target realisation). Positions and velocities are taken to FP64 and every
+// bin is decided in FP64. The per-bin sums are FP64 atomics in global memory: they equal
+// an ordered sum up to rounding. The comparisons (moments, Delta_kin, Delta_grid, rms)
+// are a few thousand bins of host arithmetic.
+#include "m2m_ctx.h"
+
+#include <cmath>
+#include <vector>
+
+using namespace m2m;
+
+namespace {
+
+constexpr int kKinSums = M2M_KIN_SUMS;
+constexpr int kDiagThreads = 256;
+
+// Spherical bins: shell 0 is [0, r_min); shells 1 .. n_r-1 are equal in ln r up to r_max.
+struct SphBins {
+    int n_r, n_phi, n_ct;
+    double r_min, r_max, ln_rmin, ln_span;  // ln(r_max) - ln(r_min)
+};
+
+__device__ int sph_bin(const SphBins &g, double x, double y, double z)
+{
+    const double r = sqrt(x * x + y * y + z * z);
+    if (!(r < g.r_max)) return -1;
+    int ir = 0;
+    if (r >= g.r_min) {
+        const double f = (log(r) - g.ln_rmin) / g.ln_span;
+        ir = 1 + int(floor(f * (g.n_r - 1)));
+        if (ir > g.n_r - 1) ir = g.n_r - 1;
+    }
+    const double ct = r > 0.0 ? z / r : 1.0;
+    int ic = int(floor((ct + 1.0) * 0.5 * g.n_ct));
+    ic = ic < 0 ? 0 : (ic > g.n_ct - 1 ? g.n_ct - 1 : ic);
+    const double ph = atan2(y, x);
+    int ip = int(floor((ph + 3.14159265358979323846) / (2.0 * 3.14159265358979323846) * g.n_phi));
+    ip = ip < 0 ? 0 : (ip > g.n_phi - 1 ? g.n_phi - 1 : ip);
+    return (ir * g.n_ct + ic) * g.n_phi + ip;
+}
+
+// v along e_r, e_theta, e_phi; phi = 0 on the z axis and e_r = e_z at the centre.
+__device__ void sph_velocity(double x, double y, double z, double vx, double vy, double vz, double v[3])
+{
+    const double R = sqrt(x * x + y * y);
+    const double r = sqrt(R * R + z * z);
+    const double cp = R > 0.0 ? x / R : 1.0, sp = R > 0.0 ? y / R : 0.0;
+    const double ct = r > 0.0 ? z / r : 1.0, st = r > 0.0 ? R / r : 0.0;
+    v[0] = vx * st * cp + vy * st * sp + vz * ct;
+    v[1] = vx * ct * cp + vy * ct * sp - vz * st;
+    v[2] = -vx * sp + vy * cp;
+}
+
+template <class T>
+struct Particles {
+    const T *x, *y, *z, *vx, *vy, *vz;
+    const double *w;
+    long long n;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kDiagThreads) k_kin_sums(const SphBins g, const Particles<T> p, double *sums,
+                                                           unsigned long long *counts)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = double(p.x[i]), y = double(p.y[i]), z = double(p.z[i]);
+        const int b = sph_bin(g, x, y, z);
+        if (b < 0) continue;
+        double v[3];
+        sph_velocity(x, y, z, double(p.vx[i]), double(p.vy[i]), double(p.vz[i]), v);
+        const double w = p.w[i];
+        double *o = sums + (long long)b * kKinSums;
+        atomicAdd(o, w);
+        for (int c = 0; c < 3; ++c) {
+            atomicAdd(o + 1 + c, w * v[c]);
+            atomicAdd(o + 4 + c, w * v[c] * v[c]);
+        }
+        atomicAdd(counts + b, 1ull);
+    }
+}
+
+// First pass over the (E, x) grid: each particle's cell, the cell's weight and count.
+template <class T>
+__global__ void __launch_bounds__(kDiagThreads) k_grid_sums(const Model m, const Cst<double> k, const double *lcE,
+                                                            const Particles<T> p, int *cell, double *wsum,
+                                                            unsigned long long *counts)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = prior_cell<double>(m, k, lcE, double(p.x[i]), double(p.y[i]), double(p.z[i]),
+                                         double(p.vx[i]), double(p.vy[i]), double(p.vz[i]));
+        cell[i] = c;
+        atomicAdd(wsum + c, p.w[i]);
+        atomicAdd(counts + c, 1ull);
+    }
+}
+
+// Second pass: squared deviations from the cell means.
+__global__ void __launch_bounds__(kDiagThreads) k_grid_dev(long long n, const int *cell, const double *w,
+                                                           const double *wsum, const unsigned long long *counts,
+                                                           double *wdev2)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = cell[i];
+        const double d = w[i] - wsum[c] / double(counts[c]);
+        atomicAdd(wdev2 + c, d * d);
+    }
+}
+
+// Device copies of the particles the diagnostics bin, and the scratch they need; freed on
+// destruction.
+struct Scratch {
+    std::vector<void *> blocks;
+    ~Scratch()
+    {
+        for (void *p : blocks) cudaFree(p);
+    }
+    template <class U>
+    cudaError_t get(U **p, size_t count)
+    {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(U) * count);
+        if (e == cudaSuccess) blocks.push_back(*p);
+        return e;
+    }
+};
+
+#define CS(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? M2M_ERR_OOM : M2M_ERR_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                            \
+    } while (0)
+
+// The particles to bin: the caller's host arrays (copied to the device as FP64), or with
+// n == 0 and no arrays the fit's own state and its current weights. kind: 0 = caller's
+// (FP64), 1 = fit's FP64 state, 2 = fit's FP32 state.
+struct Source {
+    int kind = 0;
+    Particles<double> d{};
+    Particles<float> f{};
+};
+
+m2m_status source(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *w, Scratch &S,
+                  Source &src)
+{
+    if (!ctx->sub.empty())
+        return fail(ctx, M2M_ERR_STATE, "a batch context: per-fit calls take a fit handle from m2m_batch_model");
+    if (n < 0) return fail(ctx, M2M_ERR_ARG, "n must be >= 0");
+    if (n == 0 && !pos && !vel && !w) {
+        if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+        m2m_status s = current_weights(ctx);
+        if (s != M2M_OK) return s;
+        if (ctx->precision == M2M_PREC_FP64) {
+            src.kind = 1;
+            const double *const *st = reinterpret_cast<const double *const *>(ctx->st);
+            src.d = {st[0], st[1], st[2], st[3], st[4], st[5], ctx->d_wout, ctx->n};
+        } else {
+            src.kind = 2;
+            const float *const *st = reinterpret_cast<const float *const *>(ctx->st);
+            src.f = {st[0], st[1], st[2], st[3], st[4], st[5], ctx->d_wout, ctx->n};
+        }
+        return M2M_OK;
+    }
+    if (n > 0 && (!pos || !vel || !w))
+        return fail(ctx, M2M_ERR_ARG, "pos, vel and w are required for n > 0 (or all NULL with n = 0)");
+    double *d = nullptr;
+    CS(S.get(&d, size_t(7) * size_t(n)));
+    if (n > 0) {
+        CS(cudaMemcpyAsync(d, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CS(cudaMemcpyAsync(d + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CS(cudaMemcpyAsync(d + 6 * n, w, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    src.kind = 0;
+    src.d = {d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, d + 6 * n, n};
+    return M2M_OK;
+}
+
+int grid_of(const m2m_ctx *ctx, long long n)
+{
+    const long long want = (n + kDiagThreads - 1) / kDiagThreads;
+    const long long cap = (long long)(ctx->nsm > 0 ? ctx->nsm : 1) * 8;
+    return int(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+}  // namespace
+
+extern "C" m2m_status m2m_diag_kinematics(m2m_ctx *ctx, const m2m_sph_grid *grid, int64_t n, const double *pos,
+                                          const double *vel, const double *w, double *sums, int64_t *counts,
+                                          int64_t nbins)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!grid || !sums) return fail(ctx, M2M_ERR_ARG, "grid and sums are required");
+    if (grid->n_r < 2 || grid->n_phi < 1 || grid->n_ct < 1 || !(grid->r_min > 0.0) ||
+        !(grid->r_max > grid->r_min) || !std::isfinite(grid->r_max))
+        return fail(ctx, M2M_ERR_ARG, "spherical grid needs n_r >= 2, n_phi, n_ct >= 1 and 0 < r_min < r_max");
+    const long long nb = (long long)grid->n_r * grid->n_phi * grid->n_ct;
+    if (nb > (1ll << 24)) return fail(ctx, M2M_ERR_ARG, "spherical grid has more than 2^24 bins");
+    if (nbins != nb) return fail(ctx, M2M_ERR_ARG, "nbins must be n_r*n_phi*n_ct (%lld)", nb);
+    Scratch S;
+    Source src;
+    m2m_status s = source(ctx, n, pos, vel, w, S, src);
+    if (s != M2M_OK) return s;
+    double *d_sums = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    CS(S.get(&d_sums, size_t(nb) * kKinSums));
+    CS(S.get(&d_cnt, size_t(nb)));
+    CS(cudaMemsetAsync(d_sums, 0, sizeof(double) * nb * kKinSums, ctx->stream));
+    CS(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * nb, ctx->stream));
+    const SphBins g{grid->n_r, grid->n_phi, grid->n_ct, grid->r_min, grid->r_max, std::log(grid->r_min),
+                    std::log(grid->r_max) - std::log(grid->r_min)};
+    const long long np = src.kind == 2 ? src.f.n : src.d.n;
+    if (np > 0) {
+        if (src.kind == 2) k_kin_sums<float><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.f, d_sums, d_cnt);
+        else k_kin_sums<double><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.d, d_sums, d_cnt);
+        CS(cudaGetLastError());
+    }
+    CS(cudaMemcpyAsync(sums, d_sums, sizeof(double) * nb * kKinSums, cudaMemcpyDeviceToHost, ctx->stream));
+    if (counts)
+        CS(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    CS(cudaStreamSynchronize(ctx->stream));
+    return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
+}
+
+extern "C" m2m_status m2m_diag_grid(m2m_ctx *ctx, const m2m_prior_grid *grid, int64_t n, const double *pos,
+                                    const double *vel, const double *w, double *wsum, double *wdev2,
+                                    int64_t *counts, int32_t ncell)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!wsum) return fail(ctx, M2M_ERR_ARG, "wsum is required");
+    if (!ctx->sub.empty())
+        return fail(ctx, M2M_ERR_STATE, "a batch context: per-fit calls take a fit handle from m2m_batch_model");
+    Model m = ctx->m;
+    if (grid) {
+        m2m_status gs = grid_fields(ctx, m, grid);
+        if (gs != M2M_OK) return gs;
+    } else if (m.mode != M2M_REG_MPR) {
+        return fail(ctx, M2M_ERR_ARG, "a GWR fit has no (E, x) grid: pass one");
+    }
+    if (ncell != m.ncell) return fail(ctx, M2M_ERR_ARG, "ncell must be nE*nx (%d)", m.ncell);
+    Scratch S;
+    Source src;
+    m2m_status s = source(ctx, n, pos, vel, w, S, src);
+    if (s != M2M_OK) return s;
+    const long long np = src.kind == 2 ? src.f.n : src.d.n;
+    double *d_ws = nullptr, *d_wd = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    int *d_cell = nullptr;
+    CS(S.get(&d_ws, size_t(ncell)));
+    CS(S.get(&d_wd, size_t(ncell)));
+    CS(S.get(&d_cnt, size_t(ncell)));
+    CS(S.get(&d_cell, size_t(np)));
+    CS(cudaMemsetAsync(d_ws, 0, sizeof(double) * ncell, ctx->stream));
+    CS(cudaMemsetAsync(d_wd, 0, sizeof(double) * ncell, ctx->stream));
+    CS(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ncell, ctx->stream));
+    if (np > 0) {
+        const Cst<double> kd = make_cst<double>(m);
+        const int gr = grid_of(ctx, np);
+        if (src.kind == 2) {
+            k_grid_sums<float><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.f, d_cell, d_ws, d_cnt);
+            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.f.w, d_ws, d_cnt, d_wd);
+        } else {
+            k_grid_sums<double><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.d, d_cell, d_ws, d_cnt);
+            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.d.w, d_ws, d_cnt, d_wd);
+        }
+        CS(cudaGetLastError());
+    }
+    CS(cudaMemcpyAsync(wsum, d_ws, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    if (wdev2) CS(cudaMemcpyAsync(wdev2, d_wd, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    if (counts) CS(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    CS(cudaStreamSynchronize(ctx->stream));
+    return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
+}
+
+// ------------------------------------------------------------------ host arithmetic
+
+namespace {
+
+// Mean velocity and dispersion of the three components of one bin; false if the bin has
+// fewer than min_count particles or no mass.
+bool moments(const double *o, int64_t count, int64_t min_count, double mean[3], double disp[3])
+{
+    if (count < min_count || count <= 0 || !(o[0] > 0.0)) return false;
+    for (int c = 0; c < 3; ++c) {
+        mean[c] = o[1 + c] / o[0];
+        const double v2 = o[4 + c] / o[0] - mean[c] * mean[c];
+        disp[c] = v2 > 0.0 ? std::sqrt(v2) : 0.0;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" m2m_status m2m_kin_moments(int64_t nbins, const double *sums, const int64_t *counts, int64_t min_count,
+                                      double *mean, double *disp, int32_t *valid)
+{
+    if (nbins < 0 || (nbins > 0 && (!sums || !counts || !mean || !disp)))
+        return fail(nullptr, M2M_ERR_ARG, "m2m_kin_moments: null argument or nbins < 0");
+    for (int64_t b = 0; b < nbins; ++b) {
+        const bool ok = moments(sums + b * kKinSums, counts[b], min_count, mean + 3 * b, disp + 3 * b);
+        if (!ok)
+            for (int c = 0; c < 3; ++c) mean[3 * b + c] = disp[3 * b + c] = 0.0;
+        if (valid) valid[b] = ok ? 1 : 0;
+    }
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_delta_kin(int64_t nbins, const double *sums_model, const int64_t *counts_model,
+                                    const double *sums_target, const int64_t *counts_target, int64_t min_count,
+                                    double *out, int64_t *bins_used)
+{
+    if (nbins < 0 || !out || (nbins > 0 && (!sums_model || !counts_model || !sums_target || !counts_target)))
+        return fail(nullptr, M2M_ERR_ARG, "m2m_delta_kin: null argument or nbins < 0");
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    int64_t used = 0;
+    for (int64_t b = 0; b < nbins; ++b) {
+        double mm[3], dm[3], mt[3], dt[3];
+        if (!moments(sums_model + b * kKinSums, counts_model[b], min_count, mm, dm)) continue;
+        if (!moments(sums_target + b * kKinSums, counts_target[b], min_count, mt, dt)) continue;
+        for (int c = 0; c < 3; ++c) {
+            acc[c] += (mm[c] - mt[c]) * (mm[c] - mt[c]);
+            acc[3 + c] += (dm[c] - dt[c]) * (dm[c] - dt[c]);
+        }
+        ++used;
+    }
+    double all = 0.0;
+    for (int q = 0; q < 6; ++q) {
+        out[q] = used > 0 ? std::sqrt(acc[q] / double(used)) : 0.0;
+        all += acc[q];
+    }
+    out[6] = used > 0 ? std::sqrt(all / (6.0 * double(used))) : 0.0;
+    if (bins_used) *bins_used = used;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_delta_grid(int32_t ncell, const double *w_model, const double *w_target, double *delta)
+{
+    if (ncell < 0 || !delta || (ncell > 0 && (!w_model || !w_target)))
+        return fail(nullptr, M2M_ERR_ARG, "m2m_delta_grid: null argument or ncell < 0");
+    double tm = 0.0, tt = 0.0;
+    for (int c = 0; c < ncell; ++c) {
+        tm += w_model[c];
+        tt += w_target[c];
+    }
+    *delta = 0.0;
+    if (!(tm > 0.0) || !(tt > 0.0)) return M2M_OK;
+    double num = 0.0, den = 0.0;
+    for (int c = 0; c < ncell; ++c) {
+        const double wt = w_target[c] / tt;
+        if (!(wt > 0.0)) continue;
+        const double r = (wt - w_model[c] / tm) / wt;
+        num += wt * r * r;
+        den += wt;
+    }
+    *delta = std::sqrt(num / den);
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_weight_rms(int32_t ncell, const double *wdev2, const int64_t *counts, int64_t min_count,
+                                     double *rms)
+{
+    if (ncell < 0 || !rms || (ncell > 0 && (!wdev2 || !counts)))
+        return fail(nullptr, M2M_ERR_ARG, "m2m_weight_rms: null argument or ncell < 0");
+    double s = 0.0;
+    int64_t n = 0;
+    for (int c = 0; c < ncell; ++c) {
+        if (counts[c] <= min_count) continue;
+        s += wdev2[c];
+        n += counts[c];
+    }
+    *rms = n > 0 ? std::sqrt(s / double(n)) : 0.0;
+    return M2M_OK;
+}
