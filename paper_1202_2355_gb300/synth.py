@@ -104,13 +104,14 @@ def hernquist_sigma2_iso(r, M=1.0, a=1.0):
     return M / (12.0 * a) * t
 
 
-def jeans_sigma2_table(tracer_density, total_mass, rmin=1e-5, rmax=1e5, n=2000):
-    """Isotropic Jeans sigma_r^2(r) of a tracer in a spherical mass model, on a log grid.
+def jeans_sigma2_table(tracer_density, total_mass, rmin=1e-5, rmax=1e5, n=2000, beta=0.0):
+    """Jeans sigma_r^2(r) of a tracer with constant anisotropy beta = 1 - sigma_t^2/sigma_r^2
+    in a spherical mass model, on a log grid (beta = 0: isotropic).
 
-    rho sigma^2 (r) = int_r^inf rho(r') M(r')/r'^2 dr', evaluated by 16-point
-    Gauss-Legendre quadrature on each log-spaced segment, summed outside-in, with
-    the r^-6 power-law tail beyond rmax added analytically.
-    Returns (log r grid, sigma^2 on the grid).
+    rho sigma_r^2 r^(2 beta) (r) = int_r^inf rho(r') r'^(2 beta) M(r')/r'^2 dr', evaluated by
+    16-point Gauss-Legendre quadrature on each log-spaced segment, summed outside-in, with
+    the r^(2 beta - 6) power-law tail beyond rmax added analytically.
+    Returns (log r grid, sigma_r^2 on the grid).
     """
     lr = np.linspace(math.log(rmin), math.log(rmax), n)
     xg, wg = np.polynomial.legendre.leggauss(16)
@@ -119,15 +120,16 @@ def jeans_sigma2_table(tracer_density, total_mass, rmin=1e-5, rmax=1e5, n=2000):
         a_, b_ = lr[k], lr[k + 1]
         t = 0.5 * (b_ - a_) * xg + 0.5 * (b_ + a_)
         rr = np.exp(t)
-        f = tracer_density(rr) * total_mass(rr) / rr ** 2 * rr  # dr = r dlnr
+        f = tracer_density(rr) * rr ** (2.0 * beta) * total_mass(rr) / rr ** 2 * rr  # dr = r dlnr
         seg[k] = 0.5 * (b_ - a_) * np.dot(wg, f)
-    # tail: rho ~ C r^-4, M ~ Mtot at large r -> integrand ~ C Mtot r^-6
+    # tail: rho ~ C r^-4, M ~ Mtot at large r -> integrand ~ C Mtot r^(2 beta - 6)
     rt = rmax
     c4 = tracer_density(np.array([rt]))[0] * rt ** 4
     mt = total_mass(np.array([rt]))[0]
-    tail = c4 * mt * rt ** -5 / 5.0
+    tail = c4 * mt * rt ** (2.0 * beta - 5.0) / (5.0 - 2.0 * beta)
     cum = np.concatenate([np.cumsum(seg[::-1])[::-1], [0.0]]) + tail
-    return lr, cum / tracer_density(np.exp(lr))
+    r = np.exp(lr)
+    return lr, cum / (tracer_density(r) * r ** (2.0 * beta))
 
 
 def sigma2_from_table(table, r):
