@@ -17,9 +17,9 @@ _SO = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 MAX_GROUPS = 4
-MAX_KINDS = 8
+MAX_KINDS = 16
 POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
-GEOM = {"annuli": 0, "pixels": 1}
+GEOM = {"annuli": 0, "pixels": 1, "shells": 2}
 MODE = {"gwr": 0, "mpr": 1}
 ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
 RULE = {"exp": 0, "euler": 1}
@@ -32,6 +32,9 @@ def kind_code(name: str) -> int:
         return 1
     if name.startswith("gh"):
         return 10 + int(name[2:])
+    if name.startswith("alm_"):  # alm_<l>_<m>: coefficient of the real Y_lm on shells
+        l, m = (int(v) for v in name[4:].split("_"))
+        return 100 + l * (l + 1) + m
     raise ValueError(name)
 
 
@@ -128,6 +131,8 @@ def lib():
         L.or_smooth_penalty.argtypes = [C.c_int, C.c_int, _DP]
         L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
         L.or_smooth_grid.restype = C.c_int
+        L.or_ylm.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double]
+        L.or_ylm.restype = C.c_double
         L.or_sph_bin.argtypes = [C.POINTER(SphGrid), C.c_double, C.c_double, C.c_double]
         L.or_sph_velocity.argtypes = [C.c_double] * 6 + [_DP, _DP, _DP]
         L.or_kin_sums.argtypes = [C.POINTER(SphGrid), C.POINTER(Particles), _DP, _LP]
@@ -177,7 +182,7 @@ class ObsSet:
             G = self.o.g[gi]
             G.geometry = GEOM[g.geometry]
             G.n_ap = g.n_ap
-            if g.geometry == "annuli":
+            if g.geometry in ("annuli", "shells"):
                 e = np.ascontiguousarray(g.edges, np.float64)
                 self._keep.append(e)
                 G.edges = _dp(e)
@@ -460,3 +465,12 @@ def weight_rms(wdev2, count, min_count: int = 50) -> float:
     wd = np.ascontiguousarray(wdev2, np.float64)
     cnt = np.ascontiguousarray(count, np.int64)
     return lib().or_weight_rms(len(wd), _dp(wd), _lp(cnt), min_count)
+
+
+# ---------------------------------------------------------------------------
+# spherical-harmonic density coefficients (eq. alm)
+# ---------------------------------------------------------------------------
+
+def ylm(l: int, m: int, cos_theta: float, phi: float) -> float:
+    """Real spherical harmonic of unit norm, without the Condon-Shortley phase."""
+    return lib().or_ylm(l, m, cos_theta, phi)

@@ -189,6 +189,55 @@ static int aperture(const or_group *G, double X, double Y, double *area)
     return (int)fy * G->nx + (int)fx;
 }
 
+double or_ylm(int l, int m, double cos_theta, double phi)
+{
+    int am = m < 0 ? -m : m;
+    double x = cos_theta;
+    double s = sqrt(fmax(0.0, 1.0 - x * x));
+    /* P_am^am = (2 am - 1)!! s^am, then P_l^am by the recurrence in l */
+    double pmm = 1.0;
+    for (int i = 1; i <= am; ++i) pmm *= (2.0 * i - 1.0) * s;
+    double plm = pmm;
+    if (l > am) {
+        double p1 = x * (2.0 * am + 1.0) * pmm, p0 = pmm;
+        for (int ll = am + 2; ll <= l; ++ll) {
+            double p2 = (x * (2.0 * ll - 1.0) * p1 - (ll + am - 1.0) * p0) / (ll - am);
+            p0 = p1;
+            p1 = p2;
+        }
+        plm = p1;
+    }
+    /* N_lm = sqrt((2l+1)/(4 pi) (l-am)!/(l+am)!) */
+    double ratio = 1.0;
+    for (int i = l - am + 1; i <= l + am; ++i) ratio /= i;
+    double N = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * ratio);
+    if (m == 0) return N * plm;
+    if (m > 0) return sqrt(2.0) * N * plm * cos(am * phi);
+    return sqrt(2.0) * N * plm * sin(am * phi);
+}
+
+int or_cic(const or_group *G, double r, int *k_out, double *g_out)
+{
+    const double *e = G->edges;
+    int n = G->n_ap;
+    if (r < e[0]) {
+        k_out[0] = 0;
+        g_out[0] = 1.0;
+        return 1;
+    }
+    for (int k = 1; k < n; ++k) {
+        if (e[k - 1] <= r && r < e[k]) {
+            double d = e[k] - e[k - 1];
+            k_out[0] = k - 1;
+            g_out[0] = (e[k] - r) / d;
+            k_out[1] = k;
+            g_out[1] = (r - e[k - 1]) / d;
+            return 2;
+        }
+    }
+    return 0;
+}
+
 /* Non-zero entries K_ij of one particle: observable index and value. */
 int or_kernel_row(const or_obs *o, double x, double y, double z,
                   double vx, double vy, double vz, int *j_out, double *K_out)
@@ -199,6 +248,28 @@ int or_kernel_row(const or_obs *o, double x, double y, double z,
     int cnt = 0, off = 0;
     for (int g = 0; g < o->n_groups; ++g) {
         const or_group *G = &o->g[g];
+        if (G->geometry == OR_SHELLS) {
+            /* eq. alm: K = gamma_k^CIC(r) Y_lm(theta, phi), the total luminosity carried
+             * by the weights */
+            double r = sqrt(x * x + y * y + z * z);
+            double ct = r > 0.0 ? z / r : 1.0;
+            double phi = atan2(y, x);
+            int kp[2];
+            double gp[2];
+            int np = or_cic(G, r, kp, gp);
+            for (int a = 0; a < np; ++a) {
+                for (int k = 0; k < G->n_kinds; ++k) {
+                    int lm = G->kinds[k] - OR_ALM0;
+                    int l = (int)floor(sqrt((double)lm));
+                    int m = lm - l * (l + 1);
+                    j_out[cnt] = off + k * G->n_ap + kp[a];
+                    K_out[cnt] = gp[a] * or_ylm(l, m, ct, phi);
+                    ++cnt;
+                }
+            }
+            off += G->n_kinds * G->n_ap;
+            continue;
+        }
         double area = 0.0;
         int p = aperture(G, X, Y, &area);
         if (p >= 0) {
@@ -225,8 +296,8 @@ int or_kernel_row(const or_obs *o, double x, double y, double z,
 void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K)
 {
     int J = or_num_obs(o);
-    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
-    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    int jj[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
     memset(K, 0, sizeof(double) * (size_t)s->n * (size_t)J);
     for (long i = 0; i < s->n; ++i) {
         int c = or_kernel_row(o, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], jj, kk);
@@ -238,8 +309,8 @@ void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K)
 void or_observe(const or_obs *o, const or_particles *s, double *y)
 {
     int J = or_num_obs(o);
-    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
-    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    int jj[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
     for (int j = 0; j < J; ++j) y[j] = 0.0;
     for (long i = 0; i < s->n; ++i) {
         int c = or_kernel_row(o, s->x[i], s->y[i], s->z[i], s->vx[i], s->vy[i], s->vz[i], jj, kk);
@@ -331,8 +402,8 @@ double or_force(const or_obs *o, const or_params *par, int mode, double w_i, dou
                 double x, double y, double z, double vx, double vy, double vz,
                 const double *delta, const double *sig)
 {
-    int jj[OR_MAX_GROUPS * OR_MAX_KINDS];
-    double kk[OR_MAX_GROUPS * OR_MAX_KINDS];
+    int jj[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
+    double kk[2 * OR_MAX_GROUPS * OR_MAX_KINDS];
     int c = or_kernel_row(o, x, y, z, vx, vy, vz, jj, kk);
     double data = 0.0;
     for (int e = 0; e < c; ++e) data += kk[e] * delta[jj[e]] / sig[jj[e]];
@@ -489,8 +560,8 @@ int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
         double *b2 = (double *)calloc((size_t)n_ap, sizeof(double));
         double *V = Vp_out + apoff, *S = sp_out + apoff;
         int has_gh = 0;
-        for (int k = 0; k < G->n_kinds; ++k) has_gh |= G->kinds[k] >= OR_GH0;
-        for (long i = 0; i < tg->n; ++i) {
+        for (int k = 0; k < G->n_kinds; ++k) has_gh |= G->kinds[k] >= OR_GH0 && G->kinds[k] < OR_ALM0;
+        for (long i = 0; G->geometry != OR_SHELLS && i < tg->n; ++i) {
             double X, Y, v, area;
             project(o->incl_deg, tg->x[i], tg->y[i], tg->z[i], tg->vy[i], tg->vz[i], &X, &Y, &v);
             int p = aperture(G, X, Y, &area);
@@ -510,9 +581,22 @@ int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
                 S[p] = 1.0;
             }
             if (has_gh && !(l[p] > 0.0 && S[p] > 0.0)) bad = 1;
+            if (G->geometry == OR_SHELLS) {
+                /* shells: l[p] = sum of (w gamma_p)^2, the shot noise of the coefficients */
+                l[p] = 0.0;
+            }
         }
         G->Vp = V;
         G->sp = S;
+        if (G->geometry == OR_SHELLS) {
+            for (long i = 0; i < tg->n; ++i) {
+                double r = sqrt(tg->x[i] * tg->x[i] + tg->y[i] * tg->y[i] + tg->z[i] * tg->z[i]);
+                int kp[2];
+                double gp[2];
+                int np = or_cic(G, r, kp, gp);
+                for (int a = 0; a < np; ++a) l[kp[a]] += (tg->w[i] * gp[a]) * (tg->w[i] * gp[a]);
+            }
+        }
         for (int p = 0; p < n_ap; ++p) lum[apoff + p] = l[p];
         if (bad) {
             free(l); free(m1); free(m2); free(b1); free(b2); free(lum);
@@ -561,7 +645,12 @@ int or_build_targets(or_obs *o, const or_particles *tg, const double *err,
                 int j = off + k * G->n_ap + p;
                 int kind = G->kinds[k];
                 double gn = noise ? noise[j] : 0.0;
-                if (kind == OR_MASS) {
+                if (kind >= OR_ALM0) {
+                    /* shot noise of a_lm,k for an isotropic realisation, sum (w gamma)^2 / (4 pi),
+                     * scaled by err */
+                    sig_out[j] = err[j] * sqrt(lum[apoff + p] / (4.0 * OR_PI));
+                    Y_out[j] = y[j] + sig_out[j] * gn;
+                } else if (kind == OR_MASS) {
                     sig_out[j] = err[j] * y[j];
                     Y_out[j] = y[j] * (1.0 + err[j] * gn);
                 } else {

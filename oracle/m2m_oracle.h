@@ -20,13 +20,17 @@ extern "C" {
 #endif
 
 #define OR_MAX_GROUPS 4
-#define OR_MAX_KINDS 8
+#define OR_MAX_KINDS 16
 
 enum { OR_POT_HERNQUIST = 0, OR_POT_HERNQUIST_NFW = 1, OR_POT_LOG = 2 };
-enum { OR_ANNULI = 0, OR_PIXELS = 1 };
-/* observable kinds: surface mass density, luminosity-weighted v_los^2,
- * and Gauss-Hermite b_n = l h_n for n = 0..6 (kind OR_GH0 + n) */
-enum { OR_MASS = 0, OR_V2 = 1, OR_GH0 = 10 };
+/* apertures: annuli or pixels on the sky; or the 3-D radial grid of the spherical-harmonic
+ * density coefficients (eq. alm), with cloud-in-cell weights between grid radii */
+enum { OR_ANNULI = 0, OR_PIXELS = 1, OR_SHELLS = 2 };
+/* observable kinds: surface mass density, luminosity-weighted v_los^2, Gauss-Hermite
+ * b_n = l h_n for n = 0..6 (kind OR_GH0 + n), and on shells the coefficients a_lm of the
+ * real spherical harmonic Y_lm, 0 <= l <= 6, |m| <= l (kind OR_ALM0 + l (l + 1) + m) */
+enum { OR_MASS = 0, OR_V2 = 1, OR_GH0 = 10, OR_ALM0 = 100 };
+#define OR_ALM_LMAX 6
 enum { OR_GWR = 0, OR_MPR = 1 };
 enum { OR_E_LOGNEG = 0, OR_E_EXP = 1, OR_E_LINEAR = 2 };
 enum { OR_UPDATE_EXP = 0, OR_UPDATE_EULER = 1 };
@@ -41,8 +45,9 @@ typedef struct {
 
 typedef struct {
     int geometry;       /* OR_ANNULI or OR_PIXELS */
-    int n_ap;           /* number of apertures (annuli, or nx*ny pixels) */
-    const double *edges;/* annuli: n_ap+1 increasing projected radii */
+    int n_ap;           /* number of apertures (annuli, nx*ny pixels, or shell grid radii) */
+    const double *edges;/* annuli: n_ap+1 increasing projected radii; shells: n_ap increasing
+                           3-D grid radii r_0 > 0 */
     int nx, ny;         /* pixels */
     double xlo, xhi, ylo, yhi;
     int n_kinds;
@@ -100,6 +105,17 @@ void or_accel(const or_potential *p, double x, double y, double z,
 void or_leapfrog(const or_potential *p, or_particles *s, double dt);
 double or_hermite(int n, double x);
 double or_gh_kernel(int n, double nu);
+/* Real spherical harmonic, unit norm over the sphere, without the Condon-Shortley phase:
+ * m = 0: N_l0 P_l(cos t); m > 0: sqrt2 N_lm P_l^m(cos t) cos(m phi); m < 0: sqrt2 N_l|m|
+ * P_l^|m|(cos t) sin(|m| phi); N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), P_m^m = (2m-1)!!
+ * (1 - x^2)^(m/2) >= 0. */
+double or_ylm(int l, int m, double cos_theta, double phi);
+/* Cloud-in-cell weights of radius r on the grid of a shell group: r_{k-1} <= r < r_k gives
+ * (r_k - r)/(r_k - r_{k-1}) to point k-1 and (r - r_{k-1})/(r_k - r_{k-1}) to point k; r < r_0
+ * gives 1 to point 0; r >= r_{n-1} nothing. Returns the number of points (0..2). */
+int or_cic(const or_group *G, double r, int *k_out, double *g_out);
+/* Non-zero entries K_ij of one particle (at most 2 OR_MAX_GROUPS OR_MAX_KINDS): observable
+ * index and value. */
 int or_kernel_row(const or_obs *o, double x, double y, double z,
                   double vx, double vy, double vz, int *j_out, double *K_out);
 void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K);

@@ -42,16 +42,19 @@ KIND_NAMES = ("mass", "v2", "gh0", "gh1", "gh2", "gh3", "gh4", "gh5", "gh6")
 
 @dataclass
 class Group:
-    geometry: str                     # "annuli" or "pixels"
+    geometry: str                     # "annuli", "pixels" or "shells"
     kinds: list                       # symbolic kinds
-    errs: list                        # error per kind (relative for mass/v2, absolute for gh)
-    edges: np.ndarray | None = None   # annuli edges
+    errs: list                        # error per kind (relative for mass/v2, absolute for gh,
+                                      # a multiple of the target's shot noise for alm)
+    edges: np.ndarray | None = None   # annuli edges; shells: the 3-D grid radii
     nx: int = 0
     ny: int = 0
     box: tuple = (0.0, 0.0, 0.0, 0.0)  # xlo, xhi, ylo, yhi
 
     @property
     def n_ap(self) -> int:
+        if self.geometry == "shells":
+            return len(self.edges)
         return len(self.edges) - 1 if self.geometry == "annuli" else self.nx * self.ny
 
 
