@@ -59,19 +59,31 @@ enum {
     M2M_POT_LOG = 2            /* phi = v0^2/2 ln(r0^2 + R^2 + z^2/q^2)             (eq. log_halo) */
 };
 
-/* Aperture geometries on the sky. */
+/* Aperture geometries: on the sky, or the 3-D radial grid of the density expansion. */
 enum {
     M2M_GEOM_ANNULI = 0,       /* half-open annuli edges[p] <= R < edges[p+1] */
-    M2M_GEOM_PIXELS = 1        /* nx*ny pixels over [xlo,xhi) x [ylo,yhi); p = py*nx + px */
+    M2M_GEOM_PIXELS = 1,       /* nx*ny pixels over [xlo,xhi) x [ylo,yhi); p = py*nx + px */
+    M2M_GEOM_SHELLS = 2        /* grid radii r_p = edges[p], p < n_ap, of the 3-D radius r, with
+                                  cloud-in-cell weights (eq. alm): r_{p-1} <= r < r_p gives
+                                  (r_p - r)/(r_p - r_{p-1}) to point p-1 and (r - r_{p-1})/(r_p - r_{p-1})
+                                  to point p; r < r_0 gives 1 to point 0; r >= r_{n_ap-1} nothing */
 };
 
 /* Observable kinds (kernel K_j of eq. obs, with the aperture selection delta_pi). */
 enum {
     M2M_OBS_MASS = 0,          /* surface mass density: K = 1/area_p */
     M2M_OBS_V2 = 1,            /* luminosity-weighted second moment: K = v_los^2 */
-    M2M_OBS_GH0 = 10           /* b_n = l h_n: K = 2 sqrt(pi) u_n(nu), nu = (v_los - V_p)/sigma_p,
+    M2M_OBS_GH0 = 10,          /* b_n = l h_n: K = 2 sqrt(pi) u_n(nu), nu = (v_los - V_p)/sigma_p,
                                   kind M2M_OBS_GH0 + n for n = 0..6 (eq. lumghn) */
+    M2M_OBS_ALM0 = 100         /* shells only: a_lm,p, K = gamma_p(r) Y_lm(theta, phi) (eq. alm), the total
+                                  luminosity carried by the weights; kind M2M_OBS_ALM(l, m) */
 };
+/* Coefficient of the real spherical harmonic Y_lm, 0 <= l <= M2M_ALM_LMAX, |m| <= l: unit norm
+ * over the sphere, without the Condon-Shortley phase; m = 0: N_l0 P_l(cos theta); m > 0:
+ * sqrt2 N_lm P_l^m(cos theta) cos(m phi); m < 0: sqrt2 N_l|m| P_l^|m|(cos theta) sin(|m| phi);
+ * N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!); theta from the z axis, phi = atan2(y, x). */
+#define M2M_OBS_ALM(l, m) (M2M_OBS_ALM0 + (l) * ((l) + 1) + (m))
+#define M2M_ALM_LMAX 6
 
 enum { M2M_REG_GWR = 0, M2M_REG_MPR = 1 };            /* eq. entropy / eq. S+ with moving priors */
 enum { M2M_E_LOGNEG = 0, M2M_E_EXP = 1, M2M_E_LINEAR = 2 }; /* E-axis bins uniform in ln(-E), exp(E), E */
@@ -85,7 +97,7 @@ enum { M2M_UPDATE_EXP = 0, M2M_UPDATE_EULER = 1 };
 enum { M2M_DEPOSIT_AUTO = 0, M2M_DEPOSIT_SHARED = 1, M2M_DEPOSIT_GLOBAL = 2 };
 
 #define M2M_MAX_GROUPS 4
-#define M2M_MAX_KINDS 8
+#define M2M_MAX_KINDS 16
 
 /* Fixed potential. Unused fields are ignored. */
 typedef struct {
@@ -100,7 +112,8 @@ typedef struct {
 typedef struct {
     int32_t geometry;              /* M2M_GEOM_* */
     int32_t n_ap;                  /* annuli: number of annuli; pixels: must equal nx*ny */
-    const double *edges;           /* host, n_ap+1 strictly increasing radii (annuli only) */
+    const double *edges;           /* host: annuli, n_ap+1 strictly increasing radii >= 0; shells, n_ap
+                                      strictly increasing grid radii > 0 */
     int32_t nx, ny;                /* pixels only */
     double xlo, xhi, ylo, yhi;     /* pixels only */
     int32_t n_kinds;               /* 1..M2M_MAX_KINDS */
@@ -283,7 +296,10 @@ m2m_status m2m_load_state(m2m_ctx *ctx, const char *path);
  * iterations); then Y_j and sigma_j from the per-observable error err[j]
  * (relative on the surface density, relative on v_rms for M2M_OBS_V2, absolute
  * on h_n for GH kinds) with optional Gaussian noise noise[j] (standard normals,
- * may be NULL) added in the same variable. obs->Y/sigY and the groups' Vp/sp are
+ * may be NULL) added in the same variable. For a_lm kinds on shells (eq. alm)
+ * sigma_j = err[j] sqrt(sum_i (w_i gamma_p(r_i))^2 / (4 pi)), the shot noise of the
+ * coefficient of an isotropic realisation (the same for every l, m), and Y_j = y_j +
+ * sigma_j noise[j]; shells have no V_p, sigma_p (0 and 1 are returned). obs->Y/sigY and the groups' Vp/sp are
  * ignored on input. Outputs are host arrays: Y, sigY (J), Vp, sp (sum of n_ap
  * over groups, group order). Runs on the device in FP64; synchronous.
  * Errors: M2M_ERR_TARGET for an empty aperture in a group with a GH kind. */
@@ -292,7 +308,8 @@ m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double
                              const double *noise, double *Y, double *sigY, double *Vp,
                              double *sp, int32_t *iterations);
 
-/* Observables without device allocation. The paper has no counterpart: this call
+/* Observables without device allocation (annuli and pixels; shell groups are rejected).
+ * The paper has no counterpart: this call
  * exists for callers that cannot call cudaMalloc, for example code running inside
  * another runtime's memory pool, under a policy that forbids allocation after
  * start-up, or next to a framework whose allocator owns the device. It computes

@@ -16,9 +16,9 @@ _SO = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libm2m
 _lib = None
 
 MAX_GROUPS = 4
-MAX_KINDS = 8
+MAX_KINDS = 16
 POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
-GEOM = {"annuli": 0, "pixels": 1}
+GEOM = {"annuli": 0, "pixels": 1, "shells": 2}
 MODE = {"gwr": 0, "mpr": 1}
 ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
 PREC = {"fp64": 0, "mixed": 1}
@@ -34,6 +34,9 @@ def kind_code(name: str) -> int:
         return 1
     if name.startswith("gh"):
         return 10 + int(name[2:])
+    if name.startswith("alm_"):  # alm_<l>_<m>: coefficient of the real Y_lm on shells
+        l, m = (int(v) for v in name[4:].split("_"))
+        return 100 + l * (l + 1) + m
     raise ValueError(f"unknown observable kind {name!r}")
 
 
@@ -175,7 +178,7 @@ class ObsDesc:
             G = self.o.groups[gi]
             G.geometry = GEOM[g.geometry]
             G.n_ap = g.n_ap
-            if g.geometry == "annuli":
+            if g.geometry in ("annuli", "shells"):
                 e = np.ascontiguousarray(g.edges, np.float64)
                 self._keep.append(e)
                 G.edges = _dp(e)

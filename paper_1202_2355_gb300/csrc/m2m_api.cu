@@ -173,6 +173,17 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
             }
             G.e0sq_f = float(S.edges[0] * S.edges[0]);
             G.ensq_f = float(S.edges[S.n_ap] * S.edges[S.n_ap]);
+        } else if (S.geometry == M2M_GEOM_SHELLS) {
+            if (!S.edges) return fail(ctx, M2M_ERR_ARG, "group %d: shells need the grid radii in edges", g);
+            for (int p = 0; p < S.n_ap; ++p) {
+                if (!std::isfinite(S.edges[p]) || !(S.edges[p] > 0) || (p > 0 && !(S.edges[p] > S.edges[p - 1])))
+                    return fail(ctx, M2M_ERR_ARG, "group %d: grid radii must be finite, > 0 and increasing", g);
+                ctx->edges.push_back(S.edges[p]);
+            }
+            ned += S.n_ap;
+            G.lut_off = int(ctx->lut.size());
+            G.lut_n = 0;
+            for (int p = 0; p < S.n_ap; ++p) area[p] = 1.0;
         } else if (S.geometry == M2M_GEOM_PIXELS) {
             if (S.nx < 1 || S.ny < 1 || (long long)S.nx * S.ny != S.n_ap || !(S.xhi > S.xlo) || !(S.yhi > S.ylo))
                 return fail(ctx, M2M_ERR_ARG, "group %d: pixels need nx*ny == n_ap and a non-empty box", g);
@@ -192,6 +203,33 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         bool has_gh = false;
         for (int k = 0; k < S.n_kinds; ++k) {
             const int kind = S.kinds[k];
+            if (S.geometry == M2M_GEOM_SHELLS) {
+                // eq. alm: the real Y_lm of each kind; N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!)
+                const int lm = kind - kKindAlm0;
+                int l = 0;
+                while ((l + 1) * (l + 1) <= lm) ++l;
+                const int mm = lm - l * (l + 1);
+                if (lm < 0 || l > M2M_ALM_LMAX)
+                    return fail(ctx, M2M_ERR_ARG, "group %d: shells take a_lm kinds with l <= %d only", g, M2M_ALM_LMAX);
+                for (int k2 = 0; k2 < k; ++k2)
+                    if (S.kinds[k2] == kind) return fail(ctx, M2M_ERR_ARG, "group %d: kind %d listed twice", g, kind);
+                const int am = mm < 0 ? -mm : mm;
+                double ratio = 1.0;
+                for (int i = l - am + 1; i <= l + am; ++i) ratio /= double(i);
+                double nrm = std::sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
+                if (mm != 0) nrm *= std::sqrt(2.0);
+                G.kinds[k] = kind;
+                G.alm_l[k] = (signed char)l;
+                G.alm_m[k] = (signed char)mm;
+                G.alm_norm[k] = nrm;
+                G.alm_norm_f[k] = float(nrm);
+                for (int p = 0; p < S.n_ap; ++p) {
+                    ctx->obs_kind.push_back(kind);
+                    ctx->obs_post.push_back(1.0);
+                    ctx->area_of_obs.push_back(1.0);
+                }
+                continue;
+            }
             const bool ok = kind == kKindMass || kind == kKindV2 || is_gh(kind) || (ctx->internal && kind == kKindV1);
             if (!ok) return fail(ctx, M2M_ERR_ARG, "group %d: unknown observable kind %d", g, kind);
             G.kinds[k] = kind;
@@ -234,6 +272,8 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     int max_gh = -1;
     for (int g = 0; g < m.n_groups; ++g) max_gh = std::max(max_gh, m.g[g].max_gh);
     m.rec_len = 5 + (max_gh + 1);
+    for (int g = 0; g < m.n_groups; ++g)  // shell records hold c_j of each a_lm
+        if (m.g[g].geometry == M2M_GEOM_SHELLS) m.rec_len = std::max(m.rec_len, m.g[g].n_kinds);
     ctx->Y.assign(J, 0.0);
     ctx->sig.assign(J, 1.0);
     if (obs->Y && obs->sigY) {
@@ -310,7 +350,11 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.off_grid = (m.J + 1) * m.wps;
     // aperture cache: one 16-bit code per particle (two small groups or one group)
     m.ap_cache = 0;
-    if (m.n_groups == 1 && m.g[0].n_ap < int(kApNone16)) m.ap_cache = 2;
+    bool shells = false;
+    for (int g = 0; g < m.n_groups; ++g) shells |= m.g[g].geometry == M2M_GEOM_SHELLS;
+    if (shells) {
+        // the a_lm are found from the 3-D position: nothing to cache
+    } else if (m.n_groups == 1 && m.g[0].n_ap < int(kApNone16)) m.ap_cache = 2;
     else if (m.n_groups == 2 && m.g[0].n_ap < int(kApNone8) && m.g[1].n_ap < int(kApNone8)) m.ap_cache = 1;
     m.gx_group = -1;
     for (int g = 0; m.ap_cache && m.gx_group < 0 && g < m.n_groups; ++g)
@@ -378,6 +422,10 @@ static m2m_status configure_kernels(m2m_ctx *ctx)
         return fail(ctx, M2M_ERR_ARG, "shared deposit needs %zu B of shared memory (limit %d)", smem_shared, maxsm);
     ctx->global_dep = ctx->deposit == M2M_DEPOSIT_GLOBAL ||
                       (ctx->deposit == M2M_DEPOSIT_AUTO && smem_shared > size_t(maxsm));
+    for (int g = 0; ctx->global_dep && g < m.n_groups; ++g)
+        if (m.g[g].geometry == M2M_GEOM_SHELLS)
+            return fail(ctx, M2M_ERR_ARG, "shell groups (a_lm) need the shared deposit (%zu B of shared memory, limit %d)",
+                        smem_shared, maxsm);
     const int max_block = ctx->global_dep ? kStepMaxThreads<T, true> : kStepMaxThreads<T, false>;
     // 512 threads in two blocks per SM was the fastest shape of the mixed-precision
     // global-deposit kernel on 64x64 maps (1024 x 1 and 256 x 4 were 8-10 % slower)
@@ -1187,111 +1235,152 @@ extern "C" m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, c
     pg.update_every = 1;
     m2m_options opt{};
     opt.precision = M2M_PREC_FP64;
-    // pass 1: luminosity, first and second moments per aperture
-    m2m_observables o1 = *obs;
-    o1.Y = o1.sigY = nullptr;
+    // the line-of-sight groups (annuli, pixels) get V_p, sigma_p in passes 1 and 2; shell
+    // groups get the sums of (w gamma)^2 of their grid points for the a_lm errors
     int nap_total = 0;
-    for (int g = 0; g < o1.n_groups; ++g) {
-        o1.groups[g].n_kinds = 3;
-        o1.groups[g].kinds[0] = kKindMass;
-        o1.groups[g].kinds[1] = kKindV1;
-        o1.groups[g].kinds[2] = kKindV2;
-        o1.groups[g].Vp = o1.groups[g].sp = nullptr;
+    std::vector<int> los, apoff(obs->n_groups);
+    for (int g = 0; g < obs->n_groups; ++g) {
+        apoff[g] = nap_total;
         nap_total += obs->groups[g].n_ap;
+        if (obs->groups[g].geometry != M2M_GEOM_SHELLS) los.push_back(g);
     }
-    m2m_status s = create_impl(&pot, &o1, &pg, 0, 0, 0, &opt, 1, &ctx);
-    if (s != M2M_OK) return s;
-    s = m2m_load_particles(ctx, n, pos, vel, w);
+    std::vector<double> lum(nap_total, 0.0), V(nap_total, 0.0), S(nap_total, 1.0);
+    std::vector<char> has_gh(obs->n_groups, 0);
+    for (int g = 0; g < obs->n_groups; ++g) {
+        const m2m_obs_group &Gs = obs->groups[g];
+        if (Gs.geometry != M2M_GEOM_SHELLS) continue;
+        if (!Gs.edges || Gs.n_ap < 1) return fail(nullptr, M2M_ERR_ARG, "group %d: shells need the grid radii", g);
+        double *l2 = lum.data() + apoff[g];
+        for (int64_t i = 0; i < n; ++i) {
+            const double x = pos[i], yy = pos[n + i], z = pos[2 * n + i];
+            const double r = std::sqrt(x * x + yy * yy + z * z);
+            const double *e = Gs.edges;
+            if (!(r < e[Gs.n_ap - 1])) continue;
+            if (r < e[0]) {
+                l2[0] += w[i] * w[i];
+                continue;
+            }
+            int k = 1;
+            while (!(r < e[k])) ++k;
+            const double d = e[k] - e[k - 1], g0 = w[i] * (e[k] - r) / d, g1 = w[i] * (r - e[k - 1]) / d;
+            l2[k - 1] += g0 * g0;
+            l2[k] += g1 * g1;
+        }
+    }
+    m2m_status s = M2M_OK;
     std::vector<double> y;
-    if (s == M2M_OK) s = observe_now(ctx, y);
-    if (s != M2M_OK) {
-        g_create_error = ctx->err;
-        m2m_destroy(ctx);
-        return s;
-    }
-    std::vector<double> lum(nap_total), V(nap_total), S(nap_total);
-    std::vector<char> has_gh(o1.n_groups, 0);
-    int ap = 0;
-    for (int g = 0; g < o1.n_groups; ++g) {
-        const GroupDesc &G = ctx->m.g[g];
-        for (int k = 0; k < obs->groups[g].n_kinds; ++k) has_gh[g] |= is_gh(obs->groups[g].kinds[k]);
-        for (int p = 0; p < G.n_ap; ++p, ++ap) {
-            const int jm = G.obs_off + p;
-            const double l = y[jm] * ctx->area_of_obs[jm];
-            lum[ap] = l;
-            if (l > 0) {
-                V[ap] = y[G.obs_off + G.n_ap + p] / l;
-                const double var = y[G.obs_off + 2 * G.n_ap + p] / l - V[ap] * V[ap];
-                S[ap] = var > 0 ? std::sqrt(var) : 0.0;
-            } else {
-                V[ap] = 0.0;
-                S[ap] = 1.0;
-            }
-            if (has_gh[g] && !(l > 0 && S[ap] > 0)) {
-                m2m_destroy(ctx);
-                return fail(nullptr, M2M_ERR_TARGET, "group %d aperture %d is empty or has zero dispersion", g, p);
-            }
+    int maxit = 0;
+    if (!los.empty()) {
+        // pass 1: luminosity, first and second moments per aperture
+        m2m_observables o1 = *obs;
+        o1.Y = o1.sigY = nullptr;
+        o1.n_groups = int(los.size());
+        for (size_t q = 0; q < los.size(); ++q) {
+            o1.groups[q] = obs->groups[los[q]];
+            o1.groups[q].n_kinds = 3;
+            o1.groups[q].kinds[0] = kKindMass;
+            o1.groups[q].kinds[1] = kKindV1;
+            o1.groups[q].kinds[2] = kKindV2;
+            o1.groups[q].Vp = o1.groups[q].sp = nullptr;
         }
-    }
-    m2m_destroy(ctx);
-    ctx = nullptr;
-    // pass 2: correct V_p, sigma_p until h1 = h2 = 0 (eq. h1h2)
-    m2m_observables o2 = *obs;
-    o2.Y = o2.sigY = nullptr;
-    std::vector<std::vector<double>> vbuf(o2.n_groups), sbuf(o2.n_groups);
-    ap = 0;
-    for (int g = 0; g < o2.n_groups; ++g) {
-        const int na = obs->groups[g].n_ap;
-        vbuf[g].assign(V.begin() + ap, V.begin() + ap + na);
-        sbuf[g].assign(S.begin() + ap, S.begin() + ap + na);
-        for (int p = 0; p < na; ++p)
-            if (!(sbuf[g][p] > 0)) sbuf[g][p] = 1.0;
-        o2.groups[g].n_kinds = 2;
-        o2.groups[g].kinds[0] = kKindGH0 + 1;
-        o2.groups[g].kinds[1] = kKindGH0 + 2;
-        o2.groups[g].Vp = vbuf[g].data();
-        o2.groups[g].sp = sbuf[g].data();
-        ap += na;
-    }
-    s = create_impl(&pot, &o2, &pg, 0, 0, 0, &opt, 1, &ctx);
-    if (s != M2M_OK) return s;
-    s = m2m_load_particles(ctx, n, pos, vel, w);
-    int it = 0, maxit = 0;
-    std::vector<char> active(o2.n_groups);
-    for (int g = 0; g < o2.n_groups; ++g) active[g] = has_gh[g];
-    for (it = 0; s == M2M_OK && it < 200; ++it) {
-        bool any = false;
-        for (int g = 0; g < o2.n_groups; ++g) any |= active[g] != 0;
-        if (!any) break;
-        s = observe_now(ctx, y);
-        if (s != M2M_OK) break;
-        ap = 0;
-        for (int g = 0; g < o2.n_groups; ++g) {
-            const GroupDesc &G = ctx->m.g[g];
-            double worst = 0.0;
+        s = create_impl(&pot, &o1, &pg, 0, 0, 0, &opt, 1, &ctx);
+        if (s != M2M_OK) return s;
+        s = m2m_load_particles(ctx, n, pos, vel, w);
+        if (s == M2M_OK) s = observe_now(ctx, y);
+        if (s != M2M_OK) {
+            g_create_error = ctx->err;
+            m2m_destroy(ctx);
+            return s;
+        }
+        for (size_t q = 0; q < los.size(); ++q) {
+            const int g = los[q];
+            const GroupDesc &G = ctx->m.g[q];
+            for (int k = 0; k < obs->groups[g].n_kinds; ++k) has_gh[g] |= is_gh(obs->groups[g].kinds[k]);
             for (int p = 0; p < G.n_ap; ++p) {
-                const int a = ap + p;
-                if (!active[g]) continue;
-                const double h1 = y[G.obs_off + p] / lum[a];
-                const double h2 = y[G.obs_off + G.n_ap + p] / lum[a];
-                worst = std::fmax(worst, std::fmax(std::fabs(h1), std::fabs(h2)));
-                const double s_old = 1.0 / ctx->isp[a];
-                ctx->Vp[a] += std::sqrt(2.0) * s_old * h1;
-                ctx->isp[a] = 1.0 / (s_old + std::sqrt(2.0) * s_old * h2);
+                const int ap = apoff[g] + p;
+                const int jm = G.obs_off + p;
+                const double l = y[jm] * ctx->area_of_obs[jm];
+                lum[ap] = l;
+                if (l > 0) {
+                    V[ap] = y[G.obs_off + G.n_ap + p] / l;
+                    const double var = y[G.obs_off + 2 * G.n_ap + p] / l - V[ap] * V[ap];
+                    S[ap] = var > 0 ? std::sqrt(var) : 0.0;
+                } else {
+                    V[ap] = 0.0;
+                    S[ap] = 1.0;
+                }
+                if (has_gh[g] && !(l > 0 && S[ap] > 0)) {
+                    m2m_destroy(ctx);
+                    return fail(nullptr, M2M_ERR_TARGET, "group %d aperture %d is empty or has zero dispersion", g, p);
+                }
             }
-            if (active[g]) {
-                if (worst <= 1e-12) active[g] = 0;
-                maxit = it;
-            }
-            ap += G.n_ap;
         }
+        m2m_destroy(ctx);
+        ctx = nullptr;
+        // pass 2: correct V_p, sigma_p until h1 = h2 = 0 (eq. h1h2)
+        m2m_observables o2 = o1;
+        std::vector<std::vector<double>> vb(los.size()), sb(los.size());
+        for (size_t q = 0; q < los.size(); ++q) {
+            const int g = los[q], na = obs->groups[g].n_ap;
+            vb[q].assign(V.begin() + apoff[g], V.begin() + apoff[g] + na);
+            sb[q].assign(S.begin() + apoff[g], S.begin() + apoff[g] + na);
+            for (int p = 0; p < na; ++p)
+                if (!(sb[q][p] > 0)) sb[q][p] = 1.0;
+            o2.groups[q].n_kinds = 2;
+            o2.groups[q].kinds[0] = kKindGH0 + 1;
+            o2.groups[q].kinds[1] = kKindGH0 + 2;
+            o2.groups[q].Vp = vb[q].data();
+            o2.groups[q].sp = sb[q].data();
+        }
+        s = create_impl(&pot, &o2, &pg, 0, 0, 0, &opt, 1, &ctx);
+        if (s != M2M_OK) return s;
+        s = m2m_load_particles(ctx, n, pos, vel, w);
+        std::vector<char> active(los.size());
+        for (size_t q = 0; q < los.size(); ++q) active[q] = has_gh[los[q]];
+        for (int it = 0; s == M2M_OK && it < 200; ++it) {
+            bool any = false;
+            for (size_t q = 0; q < los.size(); ++q) any |= active[q] != 0;
+            if (!any) break;
+            s = observe_now(ctx, y);
+            if (s != M2M_OK) break;
+            int a0 = 0;  // apertures of ctx, in the order of the line-of-sight groups
+            for (size_t q = 0; q < los.size(); ++q) {
+                const GroupDesc &G = ctx->m.g[q];
+                const int g = los[q];
+                double worst = 0.0;
+                for (int p = 0; active[q] && p < G.n_ap; ++p) {
+                    const int a = a0 + p;
+                    const double h1 = y[G.obs_off + p] / lum[apoff[g] + p];
+                    const double h2 = y[G.obs_off + G.n_ap + p] / lum[apoff[g] + p];
+                    worst = std::fmax(worst, std::fmax(std::fabs(h1), std::fabs(h2)));
+                    const double s_old = 1.0 / ctx->isp[a];
+                    ctx->Vp[a] += std::sqrt(2.0) * s_old * h1;
+                    ctx->isp[a] = 1.0 / (s_old + std::sqrt(2.0) * s_old * h2);
+                }
+                if (active[q]) {
+                    if (worst <= 1e-12) active[q] = 0;
+                    maxit = it;
+                }
+                a0 += G.n_ap;
+            }
+        }
+        int a0 = 0;
+        for (size_t q = 0; q < los.size(); ++q) {
+            const int g = los[q];
+            for (int p = 0; p < obs->groups[g].n_ap; ++p) {
+                V[apoff[g] + p] = ctx->Vp[a0 + p];
+                S[apoff[g] + p] = 1.0 / ctx->isp[a0 + p];
+            }
+            a0 += obs->groups[g].n_ap;
+        }
+        if (s != M2M_OK) g_create_error = ctx->err;
+        m2m_destroy(ctx);
+        ctx = nullptr;
+        if (s != M2M_OK) return s;
     }
-    std::vector<double> Vfin(ctx->Vp), Sfin(ctx->isp.size());
-    for (size_t a = 0; a < Sfin.size(); ++a) Sfin[a] = 1.0 / ctx->isp[a];
-    if (s != M2M_OK) g_create_error = ctx->err;
-    m2m_destroy(ctx);
-    ctx = nullptr;
-    if (s != M2M_OK) return s;
+    const std::vector<double> &Vfin = V, &Sfin = S;
+    std::vector<std::vector<double>> vbuf(obs->n_groups), sbuf(obs->n_groups);
+    int ap = 0;
     // pass 3: the requested observables with the fitted Gaussian parameters
     m2m_observables o3 = *obs;
     o3.Y = o3.sigY = nullptr;
@@ -1322,7 +1411,11 @@ extern "C" m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, c
                 const int kind = G.kinds[k];
                 const double gn = noise ? noise[j] : 0.0;
                 const double l = lum[ap + p];
-                if (kind == kKindMass) {
+                if (kind >= kKindAlm0) {
+                    // shot noise of a_lm of an isotropic realisation: sum (w gamma)^2 / (4 pi)
+                    sigY[j] = err[j] * std::sqrt(l / (4.0 * 3.14159265358979323846));
+                    Y[j] = y[j] + sigY[j] * gn;
+                } else if (kind == kKindMass) {
                     sigY[j] = err[j] * y[j];
                     Y[j] = y[j] * (1.0 + err[j] * gn);
                 } else if (kind == kKindV2) {

@@ -142,5 +142,6 @@ inline unsigned group_mask(const m2m::GroupDesc &G)
     for (int n = 0; n < 7; ++n)
         if (G.k_gh[n] >= 0) mk |= m2m::bit_gh(n);
     if (G.geometry == 1) mk |= m2m::kBitPix;
+    if (G.geometry == 2) mk |= m2m::kBitShell;
     return mk;
 }

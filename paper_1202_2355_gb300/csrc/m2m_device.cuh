@@ -18,16 +18,17 @@
 namespace m2m {
 
 constexpr int kMaxGroups = 4;
-constexpr int kMaxKinds = 8;
+constexpr int kMaxKinds = 16;
 constexpr int kKindMass = 0;
 constexpr int kKindV2 = 1;
 constexpr int kKindV1 = 2;  // internal: first moment, used only to build targets
 constexpr int kKindGH0 = 10;
+constexpr int kKindAlm0 = 100;  // a_lm on shells: kKindAlm0 + l (l + 1) + m
 
 enum : unsigned { kErrNonFinite = 1u, kErrNegWeight = 2u, kErrOverflow = 4u, kErrIndex = 8u };
 
 struct GroupDesc {
-    int geometry;   // 0 annuli, 1 pixels
+    int geometry;   // 0 annuli, 1 pixels, 2 shells (3-D radial grid of the a_lm, eq. alm)
     int n_ap;
     int n_kinds;
     int obs_off;    // first observable index of the group
@@ -48,6 +49,10 @@ struct GroupDesc {
     // plan: kind index (0..n_kinds-1) of each kernel in the group, or -1
     int k_mass, k_v2, k_v1;
     int k_gh[7];
+    // shells: l and m of each kind, and the factor of the real Y_lm (N_lm, times sqrt2 for m != 0)
+    signed char alm_l[kMaxKinds], alm_m[kMaxKinds];
+    double alm_norm[kMaxKinds];
+    float alm_norm_f[kMaxKinds];
 };
 
 struct Model {
@@ -97,7 +102,7 @@ constexpr unsigned kApUncached = 0xFFFFFFFFu;  // no cached code: locate the ape
 // Compile-time shape of an observable group, for step kernels specialised to a
 // configuration: bits for the kernels it deposits and its geometry. kDyn: read the
 // shape from the runtime GroupDesc (the generic kernel); 0: no such group.
-constexpr unsigned kBitMass = 1u, kBitV2 = 2u, kBitV1 = 4u, kBitPix = 1u << 15;
+constexpr unsigned kBitMass = 1u, kBitV2 = 2u, kBitV1 = 4u, kBitPix = 1u << 15, kBitShell = 1u << 16;
 constexpr unsigned kDyn = 0xFFFFFFFFu;
 __host__ __device__ constexpr unsigned bit_gh(int n) { return 8u << n; }
 __host__ __device__ constexpr int mask_max_gh(unsigned m, int n = 6)
@@ -118,6 +123,11 @@ struct GP {
     {
         if constexpr (dyn) return G.geometry == 1;
         else return (M & kBitPix) != 0u;
+    }
+    __device__ static bool shells(const GroupDesc &G)
+    {
+        if constexpr (dyn) return G.geometry == 2;
+        else return (M & kBitShell) != 0u;
     }
     __device__ static bool mass(const GroupDesc &G)
     {
@@ -595,13 +605,138 @@ __device__ __forceinline__ T group_data(const Model &m, const GroupDesc &G, cons
     return d;
 }
 
+// ---- shells: the spherical-harmonic density coefficients of eq. alm
+//
+// a_lm,p = sum_i w_i gamma_p(r_i) Y_lm(theta_i, phi_i) on grid radii r_0 < ... < r_{n-1}
+// (the total luminosity is carried by the weights). gamma is the cloud-in-cell weight:
+// between r_{p-1} and r_p linear in r, inside r_0 all on point 0, none beyond r_{n-1}.
+// Y_lm is the real spherical harmonic of unit norm without the Condon-Shortley phase,
+// from the recurrences P_m^m = (2m-1)!! sin^m, P_{m+1}^m = (2m+1) cos P_m^m,
+// (l-m) P_l^m = (2l-1) cos P_{l-1}^m - (l+m-1) P_{l-2}^m, and cos(m phi), sin(m phi) as the
+// powers of cos phi + i sin phi.
+
+// Grid points and cloud-in-cell weights of squared radius r2 (the group's squared grid
+// radii at esq + edge_off): returns 0, 1 (point p0, weight 1) or 2 (p0 and p0 + 1).
+template <class T>
+__device__ __forceinline__ int shell_cic(const GroupDesc &G, const T *esq, T r2, int &p0, T &g0, T &g1)
+{
+    const T *e = esq + G.edge_off;
+    const int n = G.n_ap;
+    if (!(r2 < e[n - 1])) return 0;
+    if (r2 < e[0]) {
+        p0 = 0;
+        g0 = T(1);
+        g1 = T(0);
+        return 1;
+    }
+    int lo = 0, hi = n - 1;  // e[lo] <= r2 < e[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (e[mid] <= r2) lo = mid;
+        else hi = mid;
+    }
+    const T r = d_sqrt(r2), ra = d_sqrt(e[lo]), rb = d_sqrt(e[hi]);
+    const T d = rb - ra;
+    p0 = lo;
+    g0 = d_div(rb - r, d);
+    g1 = d_div(r - ra, d);
+    return 2;
+}
+
+// Direction cosines of (x, y, z): cos and sin of theta (from the z axis) and of phi;
+// theta = 0 at the centre and phi = 0 on the z axis.
+template <class T>
+__device__ __forceinline__ void shell_angles(T x, T y, T z, T &ct, T &st, T &cp, T &sp)
+{
+    // explicit fused forms: the same rounding in every kernel that inlines this
+    const T R2 = fma(x, x, y * y);
+    const T R = d_sqrt(R2), r = d_sqrt(fma(z, z, R2));
+    const bool c = r > T(0), a = R > T(0);
+    ct = c ? d_div(z, r) : T(1);
+    st = c ? d_div(R, r) : T(0);
+    cp = a ? d_div(x, R) : T(1);
+    sp = a ? d_div(y, R) : T(0);
+}
+
+// Y_lm of kind kk of a shell group.
+template <class T>
+__device__ __forceinline__ T shell_ylm(const GroupDesc &G, int kk, T ct, T st, T cp, T sp)
+{
+    const int l = G.alm_l[kk], m = G.alm_m[kk], am = m < 0 ? -m : m;
+    T pmm = T(1);
+    for (int i = 1; i <= am; ++i) pmm *= T(2 * i - 1) * st;
+    T plm = pmm;
+    if (l > am) {
+        T p0 = pmm, p1 = ct * T(2 * am + 1) * pmm;
+        for (int ll = am + 2; ll <= l; ++ll) {
+            const T p2 = d_div(fma(ct * T(2 * ll - 1), p1, -(T(ll + am - 1) * p0)), T(ll - am));
+            p0 = p1;
+            p1 = p2;
+        }
+        plm = p1;
+    }
+    T c = T(1), s = T(0);
+    for (int i = 0; i < am; ++i) {
+        const T c2 = fma(c, cp, -(s * sp));
+        s = fma(s, cp, c * sp);
+        c = c2;
+    }
+    const T nrm = sizeof(T) == 8 ? T(G.alm_norm[kk]) : T(G.alm_norm_f[kk]);
+    return nrm * plm * (m > 0 ? c : (m < 0 ? s : T(1)));
+}
+
+// emit(slot, w K_slot, class, kind index) for every a_lm of the group at the particle's
+// one or two grid points.
+template <class T, class F>
+__device__ __forceinline__ void shell_kernels(const GroupDesc &G, const Tables<T> &tb, T x, T y, T z, T w, F &&emit)
+{
+    int p0 = 0;
+    T g0 = T(0), g1 = T(0);
+    const int np = shell_cic(G, tb.esq, fma(z, z, fma(x, x, y * y)), p0, g0, g1);
+    if (np == 0) return;
+    T ct, st, cp, sp;
+    shell_angles(x, y, z, ct, st, cp, sp);
+    for (int kk = 0; kk < G.n_kinds; ++kk) {
+        const T v = w * shell_ylm(G, kk, ct, st, cp, sp);
+        const int j = G.obs_off + kk * G.n_ap + p0;
+        emit(j, g0 * v, kClassGH, kk);
+        if (np == 2) emit(j + 1, g1 * v, kClassGH, kk);
+    }
+}
+
+// sum_j K_j c_j over the group's a_lm: the records of a shell group hold c_j per kind.
+template <class T>
+__device__ __forceinline__ T shell_data(const Model &m, const GroupDesc &G, const Tables<T> &tb, const T *rec, T x,
+                                        T y, T z)
+{
+    int p0 = 0;
+    T g0 = T(0), g1 = T(0);
+    const int np = shell_cic(G, tb.esq, fma(z, z, fma(x, x, y * y)), p0, g0, g1);
+    if (np == 0) return T(0);
+    T ct, st, cp, sp;
+    shell_angles(x, y, z, ct, st, cp, sp);
+    const T *r0 = rec + (G.ap_off + p0) * m.rec_len;
+    T d0 = T(0), d1 = T(0);
+    for (int kk = 0; kk < G.n_kinds; ++kk) {
+        const T Y = shell_ylm(G, kk, ct, st, cp, sp);
+        d0 = fma(Y, r0[kk], d0);
+        if (np == 2) d1 = fma(Y, r0[m.rec_len + kk], d1);
+    }
+    return fma(g0, d0, g1 * d1);
+}
+
 template <unsigned... Ms, class T>
-__device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, const T *rec, T X, T Y, T vlos)
+__device__ __forceinline__ T data_term(const Model &m, const Tables<T> &tb, const T *rec, T x, T y, T z, T X,
+                                       T Y, T vlos)
 {
     T data = T(0);
     each_group<0, Ms...>(m, [&](auto P, int g) {
         constexpr unsigned M = decltype(P)::mask;
         const GroupDesc &G = m.g[g];
+        if (GP<M>::shells(G)) {
+            data += shell_data(m, G, tb, rec, x, y, z);
+            return;
+        }
         const int p = aperture<M>(G, tb.esq, tb.lut, X, Y);
         if (p >= 0) data += group_data<M>(m, G, tb, rec, p, vlos);
     });
@@ -918,7 +1053,7 @@ __device__ __forceinline__ T foc_data(const Model &m, const Cst<T> &k, const Tab
     T Y, vlos;
     project(k, y, z, vy, vz, Y, vlos);
     if (code != kApUncached) return data_term_cached<Ms...>(m, tb, rec, code, vlos, gexp);
-    return data_term<Ms...>(m, tb, rec, x, Y, vlos);
+    return data_term<Ms...>(m, tb, rec, x, y, z, x, Y, vlos);
 }
 
 // Weight after the force of change of eq. modFOC over one step, the kernel
@@ -1086,6 +1221,14 @@ static __device__ void build_records(const Model &m, const Buffers &b)
         for (int p = threadIdx.x; p < G.n_ap; p += blockDim.x) {
             const int a = G.ap_off + p;
             double *r = b.rec + a * m.rec_len;
+            if (G.geometry == 2) {  // shells: c_j of each a_lm
+                float *rf = b.recf + a * m.rec_len;
+                for (int q = 0; q < m.rec_len; ++q) {
+                    r[q] = q < G.n_kinds ? b.c[G.obs_off + q * G.n_ap + p] : 0.0;
+                    rf[q] = float(r[q]);
+                }
+                continue;
+            }
             const bool gh = G.max_gh >= 0;
             const double V = gh ? b.Vp[a] : 0.0, is = gh ? b.isp[a] : 1.0, s = 1.0 / is;
             const int base = G.obs_off + p;
@@ -1391,6 +1534,13 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
                 constexpr unsigned M = decltype(Pl)::mask;
                 const GroupDesc &G = m.g[g];
+                if (GP<M>::shells(G)) {  // never cached; never in the global-deposit kernel
+                    shell_kernels(G, tb, x, y, z, w, [&](int j, T v, int, int) {
+                        if constexpr (GA) global_add(b.hist, j, v, k.fx_gh);
+                        else Acc<T>::add(S.h, m, j, v, k.fx_gh);
+                    });
+                    return;
+                }
                 const int p = aperture<M>(G, tb.esq, tb.lut, x, Y);
                 if (cache) code_out = ap_encode(m, code_out, g, p);
                 if (p >= 0) {
