@@ -346,6 +346,7 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         return fail(ctx, M2M_ERR_ARG, "unknown precision");
     ctx->precision = opt->precision;
     m.wps = ctx->precision == M2M_PREC_FP64 ? 2 : 1;
+    m.cache_accel = (ctx->precision == M2M_PREC_FP64 || m.pot == 1) ? 1 : 0;
     m.off_total = m.J * m.wps;
     m.off_grid = (m.J + 1) * m.wps;
     // aperture cache: one 16-bit code per particle (two small groups or one group)
@@ -649,12 +650,15 @@ static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
 
 static size_t elem_size(const m2m_ctx *c) { return c->precision == M2M_PREC_FP64 ? 8 : 4; }
 
+// x, y, z, vx, vy, vz, w and, where the step keeps it, the acceleration
+static int state_arrays(const m2m_ctx *c) { return c->m.cache_accel ? 10 : 7; }
+
 static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
 {
     if (n <= ctx->capacity && ctx->st[0]) return M2M_OK;
     free_state(ctx);
     const long long cap = n > 0 ? n : 1;
-    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    const int narr = state_arrays(ctx);
     for (int k = 0; k < narr; ++k) CU(cudaMalloc(&ctx->st[k], cap * elem_size(ctx)));
     CU(cudaMalloc(&ctx->cell, cap * sizeof(uint16_t)));
     if (ctx->m.ap_cache) CU(cudaMalloc(&ctx->ap, cap * sizeof(uint16_t)));
@@ -1066,7 +1070,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     const Model &m = ctx->m;
     CkptHeader hd{};
     std::memcpy(hd.magic, "M2MSTATE", 8);
-    hd.version = 5;
+    hd.version = 6;
     hd.precision = ctx->precision;
     hd.config_hash = ctx->config_hash;
     hd.n = ctx->n;
@@ -1074,7 +1078,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
     hd.ncell = m.ncell;
     hd.fx_w = m.fx_w; hd.fx_v2 = m.fx_v2; hd.fx_gh = m.fx_gh; hd.v2max = m.v2max;
     const size_t es = elem_size(ctx), n = size_t(ctx->n);
-    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    const int narr = state_arrays(ctx);
     const size_t apb = m.ap_cache ? 2 * n : 0, gxb = ctx->gx ? 8 * n : 0;
     std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +
                           sizeof(double) * (4 * m.J + m.n_ap_total * m.rec_len + (m.smooth ? 4 : 3) * m.ncell) + 8 * m.ncell +
@@ -1125,7 +1129,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
     FILE *f = std::fopen(path, "rb");
     if (!f) return fail(ctx, M2M_ERR_ARG, "cannot open %s", path);
     CkptHeader hd{};
-    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 5) {
+    if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, "M2MSTATE", 8) != 0 || hd.version != 6) {
         std::fclose(f);
         return fail(ctx, M2M_ERR_ARG, "%s is not an M2M state file", path);
     }
@@ -1135,7 +1139,7 @@ extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
         return fail(ctx, M2M_ERR_ARG, "%s was written for different descriptors", path);
     }
     const size_t es = elem_size(ctx), n = size_t(hd.n);
-    const int narr = ctx->precision == M2M_PREC_FP64 ? 10 : 7;
+    const int narr = state_arrays(ctx);
     const size_t apb = m.ap_cache ? 2 * n : 0;
     const size_t gxb = (ctx->precision == M2M_PREC_FP64 && m.gx_group >= 0) ? 8 * n : 0;
     std::vector<char> buf(es * n * narr + 2 * n + apb + gxb +

@@ -84,6 +84,8 @@ struct Model {
     // force of change at the start of the next (same positions): 0 none, 1 two groups
     // of at most 255 apertures (8 bits each), 2 one group (16 bits)
     int ap_cache;
+    // the acceleration at the current positions is kept between steps (always in FP64)
+    int cache_accel;
     // FP64 mode with the aperture cache: exp(-nu^2/2) of this group's aperture (the
     // first group with Gauss-Hermite kernels, -1 none) is also kept from the deposit
     // for the next force of change (same nu, same value)
@@ -228,10 +230,12 @@ struct State {
 template <class T>
 constexpr bool kLogWeights = sizeof(T) == 8;
 
-// FP64 mode keeps a(x_t) from the closing half-kick of one step for the opening
+// The step can keep a(x_t) from the closing half-kick of one step for the opening
 // half-kick of the next (the same function of the same positions, so bit-identical
-// to recomputing it): 48 more bytes of state traffic instead of one FP64 force
-// evaluation, worth it because that mode is bound by the FP64 pipe, not by HBM.
+// to recomputing it): 3 more state arrays read and written instead of one force
+// evaluation. FP64 mode always does (it is bound by the FP64 pipe, not by HBM);
+// mixed mode does where the force is dear (Model::cache_accel: the Hernquist + NFW
+// potential, whose halo term takes a logarithm and a division).
 template <class T>
 constexpr bool kCacheAccel = sizeof(T) == 8;
 
@@ -1514,7 +1518,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             }
             u = w;
         }
-        if constexpr (kCacheAccel<T>) {
+        if (kCacheAccel<T> || m.cache_accel) {
             T ax, ay, az;
             if (push) {
                 ax = P.ax[i]; ay = P.ay[i]; az = P.az[i];

@@ -98,6 +98,29 @@ def test_hernquist_nfw_fp64(_built):
     pr.close()
 
 
+def test_hernquist_nfw_mixed_first_steps(_built):
+    """Mixed precision in the composite potential, where the step keeps the acceleration
+    between steps: element by element within 1e-4 of the FP64 oracle over the first steps,
+    and a checkpoint (which carries the acceleration) resumes bit-identically."""
+    wl = W.make("c3", n=5000, n_target=50_000)
+    pr = Pair(wl, precision="mixed", prior=dict(wl.prior, update_every=10))
+    for k in (1, 4):
+        pr.step(k)
+        e = pr.errors()
+        assert e["ytil"] < 1e-4 and e["yraw"] < 1e-4, e
+        assert e["chi2"] < 1e-4, e
+    import os
+    import tempfile
+    path = os.path.join(tempfile.mkdtemp(), "nfw_mixed.ckpt")
+    pr.fit.save(path)
+    pr.fit.step(7)
+    w1 = pr.fit.weights()
+    pr.fit.restore(path)
+    pr.fit.step(7)
+    assert np.array_equal(pr.fit.weights(), w1)
+    pr.close()
+
+
 def test_flattened_log_pixel_maps_fp64(_built):
     """Inclined pixel maps of mass and h1..h4, signed-Lz grid with exp(E) spacing."""
     wl = W.make("c4", n=20_000, n_target=200_000)
