@@ -143,14 +143,6 @@ struct Scratch {
     }
 };
 
-#define CS(call)                                                                                   \
-    do {                                                                                           \
-        cudaError_t e_ = (call);                                                                   \
-        if (e_ != cudaSuccess)                                                                     \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? M2M_ERR_OOM : M2M_ERR_CUDA, "%s: %s", \
-                        #call, cudaGetErrorString(e_));                                            \
-    } while (0)
-
 // The particles to bin: the caller's host arrays (copied to the device as FP64), or with
 // n == 0 and no arrays the fit's own state and its current weights. kind: 0 = caller's
 // (FP64), 1 = fit's FP64 state, 2 = fit's FP32 state.
@@ -184,11 +176,11 @@ m2m_status source(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel,
     if (n > 0 && (!pos || !vel || !w))
         return fail(ctx, M2M_ERR_ARG, "pos, vel and w are required for n > 0 (or all NULL with n = 0)");
     double *d = nullptr;
-    CS(S.get(&d, size_t(7) * size_t(n)));
+    CU(S.get(&d, size_t(7) * size_t(n)));
     if (n > 0) {
-        CS(cudaMemcpyAsync(d, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CS(cudaMemcpyAsync(d + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
-        CS(cudaMemcpyAsync(d + 6 * n, w, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(d, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(d + 3 * n, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemcpyAsync(d + 6 * n, w, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     }
     src.kind = 0;
     src.d = {d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, d + 6 * n, n};
@@ -222,22 +214,22 @@ extern "C" m2m_status m2m_diag_kinematics(m2m_ctx *ctx, const m2m_sph_grid *grid
     if (s != M2M_OK) return s;
     double *d_sums = nullptr;
     unsigned long long *d_cnt = nullptr;
-    CS(S.get(&d_sums, size_t(nb) * kKinSums));
-    CS(S.get(&d_cnt, size_t(nb)));
-    CS(cudaMemsetAsync(d_sums, 0, sizeof(double) * nb * kKinSums, ctx->stream));
-    CS(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * nb, ctx->stream));
+    CU(S.get(&d_sums, size_t(nb) * kKinSums));
+    CU(S.get(&d_cnt, size_t(nb)));
+    CU(cudaMemsetAsync(d_sums, 0, sizeof(double) * nb * kKinSums, ctx->stream));
+    CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * nb, ctx->stream));
     const SphBins g{grid->n_r, grid->n_phi, grid->n_ct, grid->r_min, grid->r_max, std::log(grid->r_min),
                     std::log(grid->r_max) - std::log(grid->r_min)};
     const long long np = src.kind == 2 ? src.f.n : src.d.n;
     if (np > 0) {
         if (src.kind == 2) k_kin_sums<float><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.f, d_sums, d_cnt);
         else k_kin_sums<double><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.d, d_sums, d_cnt);
-        CS(cudaGetLastError());
+        CU(cudaGetLastError());
     }
-    CS(cudaMemcpyAsync(sums, d_sums, sizeof(double) * nb * kKinSums, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(sums, d_sums, sizeof(double) * nb * kKinSums, cudaMemcpyDeviceToHost, ctx->stream));
     if (counts)
-        CS(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
-    CS(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
 }
 
@@ -265,13 +257,13 @@ extern "C" m2m_status m2m_diag_grid(m2m_ctx *ctx, const m2m_prior_grid *grid, in
     double *d_ws = nullptr, *d_wd = nullptr;
     unsigned long long *d_cnt = nullptr;
     int *d_cell = nullptr;
-    CS(S.get(&d_ws, size_t(ncell)));
-    CS(S.get(&d_wd, size_t(ncell)));
-    CS(S.get(&d_cnt, size_t(ncell)));
-    CS(S.get(&d_cell, size_t(np)));
-    CS(cudaMemsetAsync(d_ws, 0, sizeof(double) * ncell, ctx->stream));
-    CS(cudaMemsetAsync(d_wd, 0, sizeof(double) * ncell, ctx->stream));
-    CS(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ncell, ctx->stream));
+    CU(S.get(&d_ws, size_t(ncell)));
+    CU(S.get(&d_wd, size_t(ncell)));
+    CU(S.get(&d_cnt, size_t(ncell)));
+    CU(S.get(&d_cell, size_t(np)));
+    CU(cudaMemsetAsync(d_ws, 0, sizeof(double) * ncell, ctx->stream));
+    CU(cudaMemsetAsync(d_wd, 0, sizeof(double) * ncell, ctx->stream));
+    CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ncell, ctx->stream));
     if (np > 0) {
         const Cst<double> kd = make_cst<double>(m);
         const int gr = grid_of(ctx, np);
@@ -282,12 +274,12 @@ extern "C" m2m_status m2m_diag_grid(m2m_ctx *ctx, const m2m_prior_grid *grid, in
             k_grid_sums<double><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.d, d_cell, d_ws, d_cnt);
             k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.d.w, d_ws, d_cnt, d_wd);
         }
-        CS(cudaGetLastError());
+        CU(cudaGetLastError());
     }
-    CS(cudaMemcpyAsync(wsum, d_ws, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
-    if (wdev2) CS(cudaMemcpyAsync(wdev2, d_wd, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
-    if (counts) CS(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
-    CS(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(wsum, d_ws, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    if (wdev2) CU(cudaMemcpyAsync(wdev2, d_wd, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    if (counts) CU(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
 }
 
