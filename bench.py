@@ -73,7 +73,7 @@ ACCEL_BYTES_MIXED = 24
 DRAM_PER_UNIT = {
     ("c2", "fp64"): (121.5, 1_000_000),
     ("c4", "mixed"): (54.9, 8_000_000),
-    ("c5", "mixed"): (85.4, 52_205_149),
+    ("c5", "mixed"): (85.2, 52_205_149),
 }
 
 

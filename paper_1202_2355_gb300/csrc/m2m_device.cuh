@@ -777,13 +777,45 @@ __device__ __forceinline__ T data_term_cached(const Model &m, const Tables<T> &t
 
 // ---------------------------------------------------------------- priors
 
-// Energy of the circular orbit of radius R in the equatorial plane.
+// v_c^2 = R |a(R)| and the potential at radius R on the x axis (R >= 0), for the
+// spherical potentials without the square root of R^2 and with one logarithm for the
+// NFW halo (shared by its potential and its enclosed mass); the flattened log halo
+// through accel and potential.
+template <class T>
+__host__ __device__ __forceinline__ void circ_terms(const Model &m, const Cst<T> &k, T R, T &vc2, T &phi)
+{
+    if (m.pot == 2) {
+        T ax, ay, az;
+        accel(m, k, R, T(0), T(0), ax, ay, az);
+        vc2 = -R * ax;
+        phi = potential(m, k, R, T(0), T(0));
+        return;
+    }
+    const T ra = R + k.a;
+    vc2 = d_div(k.GM * R, ra * ra);
+    phi = -d_div(k.GM, ra);
+    if (m.pot == 1) {
+        if (R > T(0)) {
+            const T q = d_div(R, k.rs);
+            const T l1 = d_log1p(q);
+            // mu(q) = ln(1+q) - q/(1+q); its series where the two terms cancel
+            const bool series = sizeof(T) == 8 ? q < T(1e-3) : q < T(0.3);
+            const T mu = series ? nfw_mu(q) : l1 - d_div(q, T(1) + q);
+            vc2 += d_div(k.GMs * mu, R);
+            phi -= d_div(k.GMs * l1, R);
+        } else {
+            phi += k.hn_phi0;
+        }
+    }
+}
+
+// Energy of the circular orbit of radius R in the equatorial plane: phi(R) + v_c^2/2.
 template <class T>
 __host__ __device__ __forceinline__ T circ_energy(const Model &m, const Cst<T> &k, T R)
 {
-    T ax, ay, az;
-    accel(m, k, R, T(0), T(0), ax, ay, az);
-    return potential(m, k, R, T(0), T(0)) - T(0.5) * R * ax;
+    T vc2, phi;
+    circ_terms(m, k, R, vc2, phi);
+    return phi + T(0.5) * vc2;
 }
 
 // Lc(E): closed form for the Hernquist potential (E_c = -(u+1)/(2u^2) GM/a with
@@ -815,27 +847,50 @@ __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
             if (T(__ldg(lcE + mid)) <= E) lo = mid;
             else hi = mid;
         }
-        const T e0 = T(__ldg(lcE + lo)), e1 = T(__ldg(lcE + hi));
-        const T fr = d_div(E - e0, e1 - e0);
-        R = d_exp(k.lc_lnr0 + (T(lo) + fr) * k.lc_dlnr);
-        // secant refinement, starting from the table segment's slope
-        const T Ra = d_exp(k.lc_lnr0 + T(lo) * k.lc_dlnr);
-        const T Rb = d_exp(k.lc_lnr0 + T(hi) * k.lc_dlnr);
-        T r0 = R, f0 = circ_energy(m, k, r0) - E;
-        T r1 = r0 - f0 * d_div(Rb - Ra, e1 - e0);
-        for (int it = 0; it < 3; ++it) {
-            const T f1 = circ_energy(m, k, r1) - E;
-            if (f1 == f0) break;
-            const T r2 = r1 - f1 * d_div(r1 - r0, f1 - f0);
-            r0 = r1;
-            f0 = f1;
-            r1 = r2;
+        if constexpr (sizeof(T) == 4) {
+            // FP32: inverse cubic interpolation of ln R in E through the four table
+            // points around the bracket (Lagrange), clamped to the bracket. Its error,
+            // of order (table step)^4 ~ 4e-9 in ln R, is below FP32 resolution, so no
+            // refinement by the force is needed.
+            int j0 = lo - 1;
+            j0 = j0 < 0 ? 0 : (j0 > n - 4 ? n - 4 : j0);
+            T xe[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xe[q] = T(__ldg(lcE + j0 + q));
+            T lnr = T(0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                T li = T(1);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q != i) li *= d_div(E - xe[q], xe[i] - xe[q]);
+                lnr += li * (k.lc_lnr0 + T(j0 + i) * k.lc_dlnr);
+            }
+            const T ylo = k.lc_lnr0 + T(lo) * k.lc_dlnr;
+            R = d_exp(fminf(fmaxf(lnr, ylo), ylo + k.lc_dlnr));
+        } else {
+            const T e0 = T(__ldg(lcE + lo)), e1 = T(__ldg(lcE + hi));
+            const T fr = d_div(E - e0, e1 - e0);
+            R = d_exp(k.lc_lnr0 + (T(lo) + fr) * k.lc_dlnr);
+            // secant refinement, starting from the table segment's slope
+            const T Ra = d_exp(k.lc_lnr0 + T(lo) * k.lc_dlnr);
+            const T Rb = d_exp(k.lc_lnr0 + T(hi) * k.lc_dlnr);
+            T r0 = R, f0 = circ_energy(m, k, r0) - E;
+            T r1 = r0 - f0 * d_div(Rb - Ra, e1 - e0);
+            for (int it = 0; it < 3; ++it) {
+                const T f1 = circ_energy(m, k, r1) - E;
+                if (f1 == f0) break;
+                const T r2 = r1 - f1 * d_div(r1 - r0, f1 - f0);
+                r0 = r1;
+                f0 = f1;
+                r1 = r2;
+            }
+            R = r1;
         }
-        R = r1;
     }
-    T ax, ay, az;
-    accel(m, k, R, T(0), T(0), ax, ay, az);
-    return R * d_sqrt(-R * ax);
+    T vc2, phi;
+    circ_terms(m, k, R, vc2, phi);
+    return R * d_sqrt(vc2);
 }
 
 // Cell k*nx + l of a particle: E bin from the chosen spacing (clamped), circularity
