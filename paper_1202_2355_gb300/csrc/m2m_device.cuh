@@ -327,45 +327,44 @@ __host__ __device__ __forceinline__ bool d_finite(double x) { return isfinite(x)
 
 // ---------------------------------------------------------------- potentials
 
-// NFW enclosed-mass factor mu(q) = ln(1+q) - q/(1+q). For small q the two terms
-// cancel. FP64: below q = 1e-3 the alternating series sum_k (-1)^k (k-1)/k q^k
-// (Horner). FP32: below q = 0.3 the positive series sum_{k>=2} t^k/k in
-// t = q/(1+q) (from ln(1+q) = -ln(1-t)), which has no cancellation.
+// NFW enclosed-mass factor mu(q) = ln(1+q) - q/(1+q), FP64. For small q the two terms
+// cancel: below q = 1e-3 the alternating series sum_k (-1)^k (k-1)/k q^k (Horner).
 template <class T>
 __host__ __device__ __forceinline__ T nfw_mu(T qq)
 {
-    if (sizeof(T) == 8) {
-        if (qq < T(1e-3)) {
-            T s = T(-10.0 / 11.0);
-            s = T(9.0 / 10.0) + qq * s;
-            s = T(-8.0 / 9.0) + qq * s;
-            s = T(7.0 / 8.0) + qq * s;
-            s = T(-6.0 / 7.0) + qq * s;
-            s = T(5.0 / 6.0) + qq * s;
-            s = T(-4.0 / 5.0) + qq * s;
-            s = T(3.0 / 4.0) + qq * s;
-            s = T(-2.0 / 3.0) + qq * s;
-            s = T(0.5) + qq * s;
-            return qq * qq * s;
-        }
-    } else if (qq < T(0.3)) {
-        const T t = d_div(qq, T(1) + qq);
-        T s = T(1.0 / 14.0);
-        s = T(1.0 / 13.0) + t * s;
-        s = T(1.0 / 12.0) + t * s;
-        s = T(1.0 / 11.0) + t * s;
-        s = T(1.0 / 10.0) + t * s;
-        s = T(1.0 / 9.0) + t * s;
-        s = T(1.0 / 8.0) + t * s;
-        s = T(1.0 / 7.0) + t * s;
-        s = T(1.0 / 6.0) + t * s;
-        s = T(1.0 / 5.0) + t * s;
-        s = T(1.0 / 4.0) + t * s;
-        s = T(1.0 / 3.0) + t * s;
-        s = T(0.5) + t * s;
-        return t * t * s;
+    if (qq < T(1e-3)) {
+        T s = T(-10.0 / 11.0);
+        s = T(9.0 / 10.0) + qq * s;
+        s = T(-8.0 / 9.0) + qq * s;
+        s = T(7.0 / 8.0) + qq * s;
+        s = T(-6.0 / 7.0) + qq * s;
+        s = T(5.0 / 6.0) + qq * s;
+        s = T(-4.0 / 5.0) + qq * s;
+        s = T(3.0 / 4.0) + qq * s;
+        s = T(-2.0 / 3.0) + qq * s;
+        s = T(0.5) + qq * s;
+        return qq * qq * s;
     }
     return d_log1p(qq) - d_div(qq, T(1) + qq);
+}
+
+// FP32: ln(1+q) and mu(q) together without the library log1p. Below q = 1 both come
+// from the series in t = q/(1+q) < 1/2: ln(1+q) = sum_{k>=1} t^k/k (21 terms, relative
+// truncation below 1e-8) and mu = ln(1+q) - t = sum_{k>=2} t^k/k; above, ln(1+q) from the
+// hardware log2 (__logf: a few ulp) and mu = ln(1+q) - t >= 0.19 without cancellation.
+__host__ __device__ __forceinline__ void nfw_logs(float q, float &l1, float &mu)
+{
+    const float t = d_div(q, 1.f + q);
+    if (q < 1.f) {
+        float s = 1.f / 22.f;
+#pragma unroll
+        for (int k = 21; k >= 2; --k) s = fmaf(t, s, 1.f / float(k));
+        mu = t * t * s;
+        l1 = t + mu;
+    } else {
+        l1 = d_log(1.f + q);
+        mu = l1 - t;
+    }
 }
 
 template <class T>
@@ -377,7 +376,17 @@ __host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k,
     }
     const T r = d_sqrt(x * x + y * y + z * z);
     T phi = -d_div(k.GM, r + k.a);
-    if (m.pot == 1) phi += (r > T(0)) ? -d_div(k.GMs * d_log1p(d_div(r, k.rs)), r) : k.hn_phi0;
+    if (m.pot == 1) {
+        if (!(r > T(0))) return phi + k.hn_phi0;
+        T l1;
+        if constexpr (sizeof(T) == 4) {
+            T mu;
+            nfw_logs(d_div(r, k.rs), l1, mu);
+        } else {
+            l1 = d_log1p(d_div(r, k.rs));
+        }
+        phi -= d_div(k.GMs * l1, r);
+    }
     return phi;
 }
 
@@ -402,7 +411,16 @@ __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, 
     const T ra = r + k.a;
     // -g(r)/r with g = G M(<r) / r^2
     T f = d_div(k.GM, ra * ra * r);
-    if (m.pot == 1) f += d_div(k.GMs * nfw_mu(d_div(r, k.rs)), r2 * r);
+    if (m.pot == 1) {
+        T mu;
+        if constexpr (sizeof(T) == 4) {
+            T l1;
+            nfw_logs(d_div(r, k.rs), l1, mu);
+        } else {
+            mu = nfw_mu(d_div(r, k.rs));
+        }
+        f += d_div(k.GMs * mu, r2 * r);
+    }
     ax = -f * x;
     ay = -f * y;
     az = -f * z;
@@ -797,10 +815,14 @@ __host__ __device__ __forceinline__ void circ_terms(const Model &m, const Cst<T>
     if (m.pot == 1) {
         if (R > T(0)) {
             const T q = d_div(R, k.rs);
-            const T l1 = d_log1p(q);
-            // mu(q) = ln(1+q) - q/(1+q); its series where the two terms cancel
-            const bool series = sizeof(T) == 8 ? q < T(1e-3) : q < T(0.3);
-            const T mu = series ? nfw_mu(q) : l1 - d_div(q, T(1) + q);
+            T l1, mu;
+            if constexpr (sizeof(T) == 4) {
+                nfw_logs(q, l1, mu);
+            } else {
+                // mu(q) = ln(1+q) - q/(1+q); its series where the two terms cancel
+                l1 = d_log1p(q);
+                mu = q < T(1e-3) ? nfw_mu(q) : l1 - d_div(q, T(1) + q);
+            }
             vc2 += d_div(k.GMs * mu, R);
             phi -= d_div(k.GMs * l1, R);
         } else {
