@@ -1,6 +1,6 @@
 // Diagnostics of a fitted particle model on the device.
 //
-// Sec. 4.1 judges a fit by how well it recovers the target's intrinsic kinematics and
+// Sec. 4.1 assesses a fit by how well it recovers the target's intrinsic kinematics and
 // its phase-space structure:
 // - the intrinsic velocity moments (streaming velocities and dispersions along e_r,
 //   e_theta, e_phi) in spherical polar bins: shells quasi-logarithmic in r, equal bins in

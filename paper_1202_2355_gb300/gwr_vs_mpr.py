@@ -3,7 +3,7 @@
 The comparison of Sec. 4 (Fig. mu): the same isotropic initial model is fitted to the same
 data of a target whose orbits are radially biased, once with the global entropy of eq.
 `entropy` (prior W0/N for every particle) and once with the moving priors of eq. `S+`, for
-a range of regularisation weights mu. Each final model is judged by
+a range of regularisation weights mu. Each final model is assessed by
 - chi^2/J, the fit to the data;
 - Delta_grid, how well it recovers the target's mass in the (E, x) cells (Sec. 4.1);
 - Delta_kin, the rms difference of its intrinsic velocity moments to the target's, here
@@ -55,7 +55,7 @@ def workload(n: int, n_target: int) -> W.Workload:
     return wl
 
 
-def judge(fit: B.Fit, wl: W.Workload, target_grid, target_kin, min_count: int = 100) -> dict:
+def assess(fit: B.Fit, wl: W.Workload, target_grid, target_kin, min_count: int = 100) -> dict:
     wm, wd, cm = fit.diag_grid(wl.prior)
     sm, km = fit.diag_kinematics(SHELLS)
     dk, used = B.delta_kin(sm, km, *target_kin, min_count)
@@ -76,11 +76,11 @@ def scan(n: int, n_target: int, steps: int, mus, precision: str = "mixed"):
             if mode == "initial":
                 tg, _, _ = fit.diag_grid(wl.prior, particles=wl.target)
                 tk = fit.diag_kinematics(SHELLS, particles=wl.target)
-                marks = judge(fit, wl, tg, tk)
+                marks = assess(fit, wl, tg, tk)
                 fit.step(1)  # chi^2 of the initial model: the first step updates no weights
             else:
                 fit.step(steps)
-                marks = judge(fit, wl, tg, tk)
+                marks = assess(fit, wl, tg, tk)
             row = dict(mode=mode, mu=mu, steps=0 if mode == "initial" else steps,
                        chi2_per_J=fit.chi2() / fit.J, **marks)
             fit.close()
