@@ -58,3 +58,37 @@ def test_descriptor_marshalling_counts_observables():
     assert d.o.groups[1].n_kinds == 3 and list(d.o.groups[1].kinds[:3]) == [1, 13, 14]
     assert d.o.groups[0].edges[60] == pytest.approx(20.0)
     assert [B.kind_code(k) for k in ("mass", "v2", "gh0", "gh6")] == [0, 1, 10, 16]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets of the C
+    structures in include/m2m.h (compiled here with gcc), so every call marshals the
+    layout the library reads."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("m2m_potential", B.Potential, ["kind", "G", "q"]),
+             ("m2m_obs_group", B.ObsGroup, ["geometry", "edges", "n_kinds", "kinds", "Vp", "sp"]),
+             ("m2m_observables", B.Observables, ["incl_deg", "n_groups", "groups", "Y", "sigY"]),
+             ("m2m_prior_grid", B.PriorGrid, ["mode", "Emin", "smoothing", "lambda"]),
+             ("m2m_options", B.Options, ["precision", "dt", "stream", "block", "deposit"]),
+             ("m2m_sph_grid", B.SphGrid, ["n_r", "r_min", "r_max"])]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "m2m.h"', "int main(void) {"]
+    for cname, _, fields in pairs:
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, cls, fields in pairs:
+        assert int(got[cname]) == C.sizeof(cls), cname
+        for f in fields:
+            pyname = "lam" if f == "lambda" and not hasattr(cls, "lambda") else f
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, pyname).offset, (cname, f)
