@@ -48,17 +48,23 @@ def _hbm_peak():
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 
 # Per particle-step figures of the step kernel, by precision:
-#   bytes  algorithmic state traffic (read + write);
-#   flops  FP64 flops the FP64 kernel executes (DFMA = 2, DADD/DMUL = 1: ncu
-#          sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over one
-#          step launch / N), including the iterative sqrt, division, log and exp;
+#   bytes         algorithmic state traffic of the method (read + write): the 6
+#                 coordinates and the weight read and written, and the 2-byte prior
+#                 cell read; the roofline's achieved bandwidth uses these;
+#   design_bytes  what this kernel streams by design, with the caches that trade
+#                 traffic for arithmetic (acceleration, apertures, exp(-nu^2/2));
+#   flops         FP64 flops the FP64 kernel executes (DFMA = 2, DADD/DMUL = 1: ncu
+#                 sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over
+#                 one step launch / N), including the iterative sqrt, division, log
+#                 and exp.
 KERNEL_FIGURES = {
-    # read x, y, z, vx, vy, vz, ln w, ax, ay, az (80 B), prior cell, cached apertures
-    # and cached exp(-nu^2/2) (2 + 2 + 8 B); write 80 + 2 + 8 B
-    "fp64": {"bytes": 182, "flops": 151.37},
-    # read 6 coordinates + w (28 B), prior cell and cached apertures (2 + 2 B);
-    # write 28 B + 2 B of apertures
-    "mixed": {"bytes": 62, "flops": None},
+    # method: 7 x 8 B read and written, cell 2 B = 114 B; design: read x..vz, ln w,
+    # ax..az (80 B), prior cell, cached apertures and cached exp(-nu^2/2) (2 + 2 + 8 B);
+    # write 80 + 2 + 8 B
+    "fp64": {"bytes": 114, "design_bytes": 182, "flops": 151.37},
+    # method: 7 x 4 B read and written, cell 2 B = 58 B; design: read 6 coordinates + w
+    # (28 B), prior cell and cached apertures (2 + 2 B); write 28 B + 2 B of apertures
+    "mixed": {"bytes": 58, "design_bytes": 62, "flops": None},
 }
 # Mixed-precision workloads in the Hernquist + NFW potential keep the acceleration
 # between steps as FP64 mode does: a_x, a_y, a_z read and written (24 B more).
@@ -138,18 +144,21 @@ def roofline(workload: str, precision: str, n: int, ms_per_launch: float) -> dic
     """Roofline of the step kernel (the only kernel of the timed region).
 
     The FP64 kernel is bound by the FP64 pipe (HBM stays mostly idle); the mixed
-    kernel streams 62 B per particle-step (86 B where it keeps the acceleration) and
-    is compared with HBM."""
+    kernel is compared with HBM. Achieved bandwidth counts the method's 58 B (FP32) or
+    114 B (FP64) per particle-step; design_gbs counts what the kernel streams with its
+    caches (62 B, 86 B where it keeps the acceleration, 182 B in FP64)."""
     f = dict(KERNEL_FIGURES[precision])
     if precision == "mixed" and workload in MIXED_CACHED_ACCEL:
-        f["bytes"] += ACCEL_BYTES_MIXED
+        f["design_bytes"] += ACCEL_BYTES_MIXED
     sec = ms_per_launch / 1e3
     gbs = f["bytes"] * n / sec / 1e9
+    design_gbs = f["design_bytes"] * n / sec / 1e9
     hbm, hbm_src = _hbm_peak()
     dram = DRAM_PER_UNIT.get((workload, precision))
     traffic = None if dram is None else dram[0] * n
     common = {"kernel": "k_step", "units_per_launch": n, "unit_of_work": "particle-step",
               "ms_per_launch": ms_per_launch, "algorithmic_bytes_per_unit": f["bytes"],
+              "design_bytes_per_unit": f["design_bytes"], "design_gbs": design_gbs,
               "traffic_per_unit_measured_at_n": None if dram is None else dram[1]}
     if precision == "fp64":
         out = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
