@@ -111,13 +111,15 @@ typedef struct {
  * observable kinds measured in every one of its n_ap apertures. */
 typedef struct {
     int32_t geometry;              /* M2M_GEOM_* */
-    int32_t n_ap;                  /* annuli: number of annuli; pixels: must equal nx*ny */
+    int32_t n_ap;                  /* annuli: number of annuli; pixels: must equal nx*ny; shells:
+                                      number of grid radii */
     const double *edges;           /* host: annuli, n_ap+1 strictly increasing radii >= 0; shells, n_ap
                                       strictly increasing grid radii > 0 */
     int32_t nx, ny;                /* pixels only */
     double xlo, xhi, ylo, yhi;     /* pixels only */
     int32_t n_kinds;               /* 1..M2M_MAX_KINDS */
-    int32_t kinds[M2M_MAX_KINDS];  /* M2M_OBS_* */
+    int32_t kinds[M2M_MAX_KINDS];  /* M2M_OBS_*, each at most once; shells take only
+                                      M2M_OBS_ALM(l, m) kinds, the other geometries none of them */
     const double *Vp, *sp;         /* host, n_ap each: Gaussian parameters V_p, sigma_p of the target
                                       LOSVD per aperture (Sec. 3.3); required iff a GH kind is present */
 } m2m_obs_group;
