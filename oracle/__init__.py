@@ -131,6 +131,8 @@ def lib():
         L.or_smooth_penalty.argtypes = [C.c_int, C.c_int, _DP]
         L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
         L.or_smooth_grid.restype = C.c_int
+        L.or_smooth_gcv.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP]
+        L.or_smooth_gcv.restype = C.c_int
         L.or_ylm.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double]
         L.or_ylm.restype = C.c_double
         L.or_sph_bin.argtypes = [C.POINTER(SphGrid), C.c_double, C.c_double, C.c_double]
@@ -377,6 +379,16 @@ def smooth_grid(y, nE: int, nx: int, lam: float = 0.0):
     if rc != 0:
         raise RuntimeError(f"or_smooth_grid failed ({rc})")
     return f, lo.value
+
+
+def smooth_gcv(y, nE: int, nx: int, lam: float) -> float:
+    """The GCV score of the smoothed grid at lam > 0 (or_smooth_gcv)."""
+    y = np.ascontiguousarray(y, np.float64)
+    sc = C.c_double()
+    rc = lib().or_smooth_gcv(nE, nx, _dp(y), lam, C.byref(sc))
+    if rc != 0:
+        raise RuntimeError(f"or_smooth_gcv failed ({rc})")
+    return sc.value
 
 
 def from_workload(wl, target_particles=None):

@@ -772,6 +772,11 @@ static int smooth_at(const double *P, int n, const double *y, double lambda, dou
     return OR_OK;
 }
 
+/* GCV choice of lambda (Sec. 2.3.2): the minimum of the GCV score over t = log10 lambda in
+ * [-4, 6] by a plain golden-section search of 40 steps (interval 4e-8 decades), which
+ * assumes the score is unimodal there. Any lambda whose score equals the minimum to rounding
+ * is an equally valid choice: when the minimum is flat, codes that evaluate the score by
+ * other means may pick a different one. */
 int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, double *lambda_out)
 {
     if (nE < 3 || nx < 3) return OR_EARG;
@@ -784,15 +789,13 @@ int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, do
     if (rc == OR_OK) {
         or_smooth_penalty(nE, nx, P);
         if (!(lambda > 0.0)) {
-            /* golden-section search of the GCV score over t = log10 lambda in [-4, 6] */
             const double g = 0.5 * (sqrt(5.0) - 1.0);
             double a = -4.0, b = 6.0;
             double c = b - g * (b - a), d = a + g * (b - a), vc, vd;
             rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);
             if (rc == OR_OK) rc = smooth_at(P, n, y, pow(10.0, d), f, &vd, M, col);
-            for (int it = 0; rc == OR_OK && it < 30; ++it) {
-                /* scores within 1e-12 (relative) count as a tie, kept on the lower side */
-                if (vc <= vd + 1e-12 * fabs(vd)) {
+            for (int it = 0; rc == OR_OK && it < 40; ++it) {
+                if (vc <= vd) {
                     b = d; d = c; vd = vc;
                     c = b - g * (b - a);
                     rc = smooth_at(P, n, y, pow(10.0, c), f, &vc, M, col);
@@ -810,6 +813,27 @@ int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, do
     free(P);
     free(M);
     free(col);
+    return rc;
+}
+
+/* The GCV score n |y - f|^2 / (n - tr A)^2 of the fit f = A y = (I + lambda P)^-1 y. */
+int or_smooth_gcv(int nE, int nx, const double *y, double lambda, double *score)
+{
+    if (nE < 3 || nx < 3 || !(lambda > 0.0)) return OR_EARG;
+    int n = nE * nx;
+    double *P = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *M = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *col = (double *)malloc(sizeof(double) * (size_t)n);
+    double *f = (double *)malloc(sizeof(double) * (size_t)n);
+    int rc = (P && M && col && f) ? OR_OK : OR_EARG;
+    if (rc == OR_OK) {
+        or_smooth_penalty(nE, nx, P);
+        rc = smooth_at(P, n, y, lambda, f, score, M, col);
+    }
+    free(P);
+    free(M);
+    free(col);
+    free(f);
     return rc;
 }
 

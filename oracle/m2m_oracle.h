@@ -137,11 +137,13 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
 void or_smooth_penalty(int nE, int nx, double *P);
 /* Smoothed grid f minimising |y - f|^2 + lambda f.P.f, i.e. f = (I + lambda P)^-1 y. With
  * lambda <= 0 it is chosen by generalized cross validation: minimise n |(I-A) y|^2 / tr(I-A)^2,
- * A = (I + lambda P)^-1, by golden-section search over log10 lambda in [-4, 6] (30 steps, scores
- * within 1e-12 relative taken as a tie on the lower side, the middle of the last bracket).
- * lambda_out receives the weight used. Needs nE, nx >= 3.
+ * A = (I + lambda P)^-1, by a plain golden-section search over log10 lambda in [-4, 6] (40 steps,
+ * the middle of the last bracket). lambda_out receives the weight used. Needs nE, nx >= 3.
  * Returns OR_OK or OR_EARG. */
 int or_smooth_grid(int nE, int nx, const double *y, double lambda, double *f, double *lambda_out);
+/* The GCV score n |(I-A) y|^2 / tr(I-A)^2 at a given lambda > 0 (the quantity or_smooth_grid
+ * minimises), so that another code's choice of lambda can be judged by its score. */
+int or_smooth_gcv(int nE, int nx, const double *y, double lambda, double *score);
 
 /* ---- Diagnostics of a fitted particle model (Sec. 4.1; Sec. 5, Fig. res) ---- */
 

@@ -6,9 +6,10 @@
 // f_xx over the interior cells, f_Ex at the cell corners), and lambda is either fixed or
 // chosen by generalized cross validation: the minimum of
 // V(lambda) = n |(I - A) y|^2 / tr(I - A)^2, A = (I + lambda P)^-1, found by a
-// golden-section search over log10 lambda in [-4, 6] (30 steps, a resolution of 5e-6
-// decades; scores within 1e-12 relative are a tie kept on the lower side, so the choice
-// does not depend on rounding; lambda is the middle of the last bracket).
+// golden-section search over log10 lambda in [-4, 6] (48 steps, a bracket of 1e-9
+// decades; lambda is the middle of the last bracket). Where the minimum is flat to
+// rounding any lambda in it is an equally good choice; 48 steps also bring a minimum at
+// an end of the range to within 1e-9 decades of it.
 //
 // P depends on the grid shape only, so the host diagonalises it once per shape,
 // P = V D V^T (Householder reduction to tridiagonal form, then implicit symmetric QR
@@ -264,8 +265,8 @@ __global__ void __launch_bounds__(kSmoothThreads) k_smooth_a(const Model m, cons
         double a = -4.0, bb = 6.0;
         double c = bb - g * (bb - a), d = a + g * (bb - a);
         double vc = gcv_score(c, n, b.sz, b.sD, red), vd = gcv_score(d, n, b.sz, b.sD, red);
-        for (int it = 0; it < 30; ++it) {
-            if (vc <= vd + 1e-12 * fabs(vd)) {  // a tie within rounding keeps the lower side
+        for (int it = 0; it < 48; ++it) {
+            if (vc <= vd) {
                 bb = d;
                 d = c;
                 vd = vc;
