@@ -411,16 +411,37 @@ def _small_run(n=400, mode="mpr", **par):
     return obs, Y, sig, pri, p, model
 
 
-def test_fixed_point_when_data_are_the_models_own_observables():
-    """dt = 0 and Y = y(0): Delta = 0 and, with equal weights, what = w -> weights exactly unchanged."""
-    obs, _, sig, pri, p, model = _small_run()
+@pytest.mark.parametrize("mode", ["mpr", "gwr"])
+def test_fixed_point_when_data_are_the_models_own_observables(mode):
+    """At Y = y(0) with frozen orbits (dt = 0) the data term vanishes (Delta = 0), and
+    with equal weights of 2^-9 every cell mean equals the weight exactly, so the MPR
+    entropy term -ln(w/what) vanishes too: the force of change of eq. modFOC is exactly
+    zero for every particle after the first prior update. (With dt = 0 the update itself
+    is the identity whatever the force, so the force is checked directly.) GWR keeps its
+    -1 of eq. entropy and a flat prior W0/N = w: F = -mu exactly. A positive control
+    moves one target value by one sigma: the force is then non-zero."""
+    obs, _, sig, pri, p, model = _small_run(mode=mode)
+    n = len(model["w"])
+    model = dict(model, w=np.full(n, 2.0 ** -9))
     Y0 = O.observe(obs, O.ParticleSet(model))
     p.update(dt=0.0, eps=1.0, mu=5.0)
     run = O.Run(HERN, obs, Y0, sig, pri, p, model)
     w0 = run.w.copy()
-    assert run.step(30) == 0
-    assert np.array_equal(run.w, w0)
+    assert run.step(1) == 0  # t = 1: push (frozen), observe, priors
     assert run.chi2 == 0.0 and np.all(run.delta == 0.0)
+    if mode == "mpr":
+        assert np.all(run.what == 2.0 ** -9)
+    F = np.array([run.force(i) for i in range(n)])
+    assert np.all(F == (0.0 if mode == "mpr" else -5.0)), F[:5]
+    assert run.step(29) == 0
+    assert np.array_equal(run.w, w0)
+    # positive control: one observable off by one sigma
+    Y1 = Y0.copy()
+    Y1[3] += sig[3]
+    run1 = O.Run(HERN, obs, Y1, sig, pri, p, model)
+    assert run1.step(1) == 0
+    F1 = np.array([run1.force(i) for i in range(n)])
+    assert np.count_nonzero(F1 != F) > 0
 
 
 def test_renormalisation_preserves_total_weight():
