@@ -2,10 +2,10 @@
 
 Tolerances: FP64 mode within 1e-10 of the oracle on observables (measured as
 |y_gpu - y_ora| / max(|y_ora|, sigma_j)), weights, chi^2 and positions after
-100 steps. Mixed mode within 1e-4 element by element over the first steps, and
-over a full run in fit quality (time-averaged chi^2/J within 2 %, time-averaged
-observables within 1e-3 in the median). Integer results (prior cells and counts)
-must match exactly.
+100 steps. Mixed mode within 1e-4 element by element over the first steps; the
+full-run comparisons of mixed mode (fit quality within 1 %, observables within
+1e-4 after the full run) are in test_gpu_mixed_full_run.py. Integer results
+(prior cells and counts) must match exactly.
 """
 import math
 import os
@@ -306,36 +306,6 @@ def test_c1_mixed_first_steps(c1_targets):
         assert e["ytil"] < 1e-4 and e["yraw"] < 1e-4, e
         assert e["chi2"] < 1e-4, e
     pr.close()
-
-
-def test_c1_mixed_full_run(c1_targets):
-    """Mixed precision against the FP64 oracle over the full 2,000-step C1 run. FP32
-    state moves particles across aperture edges differently from FP64 (each crossing
-    changes an observable by ~1/N_j ~ 1e-3 at N = 20,000), so the full-run comparison
-    is of fit quality: chi^2/J averaged over the last 1,000 steps within 2 %, and the
-    observables averaged over the last 500 steps within 1e-3 in the median."""
-    wl = W.make("c1")
-    obs, Y, sig = c1_targets
-    ora = O.Run(wl.potential, obs, Y, sig, wl.prior, wl.params, wl.model)
-    fit = B.fit_from_workload(wl, Y, sig, obs.Vp, obs.sp, precision="mixed")
-    fit.load(wl.model)
-    c_o, c_g, y_o, y_g = [], [], [], []
-    for t in range(wl.steps):
-        assert ora.step(1) == 0
-        fit.step(1)
-        c_o.append(ora.chi2)
-        c_g.append(fit.chi2())
-        if t >= wl.steps - 500:
-            y_o.append(ora.ytil.copy())
-            y_g.append(fit.observables()[0])
-    fit.close()
-    c_o, c_g = np.array(c_o[-1000:]), np.array(c_g[-1000:])
-    rel = abs(c_g.mean() / c_o.mean() - 1)
-    e = obs_err(np.mean(y_g, 0), np.mean(y_o, 0), sig)
-    print(f"mixed C1 full run: <chi2/J> {c_g.mean() / 60:.5f} vs {c_o.mean() / 60:.5f} (rel {rel:.2e}); "
-          f"time-averaged obs err median {np.median(e):.2e} max {e.max():.2e}")
-    assert rel < 0.02
-    assert np.median(e) < 1e-3
 
 
 def test_c2_full_run_mixed_fit_quality_matches_fp64():
