@@ -14,12 +14,18 @@
 // The kernels bin either the fit's own particles (their state in the fit's precision,
 // with the weights as of the end of the last step) or particles the caller passes from
 // the host (a target realisation). Positions and velocities are taken to FP64 and every
-// bin is decided in FP64. The per-bin sums are FP64 atomics in global memory: they equal
-// an ordered sum up to rounding. The comparisons (moments, Delta_kin, Delta_grid, rms)
-// are a few thousand bins of host arithmetic.
+// bin is decided in FP64. The per-bin sums are exact integer sums in the two-word fixed
+// point of the step kernel (the integer part and the next 32 fraction bits of v * scale,
+// scale a power of two): each term is converted to integers once, and integer addition
+// does not depend on the order of the atomics, so the sums are bit-reproducible whatever
+// the launch shape or the order of the particles. The scales come from a first pass that
+// finds the largest |w| and |v|^2 (maxima, also order-independent), so that no bin sum
+// can leave the range. The comparisons (moments, Delta_kin, Delta_grid, rms) are a few
+// thousand bins of host arithmetic.
 #include "m2m_ctx.h"
 
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 using namespace m2m;
@@ -73,9 +79,57 @@ struct Particles {
     long long n;
 };
 
+// Fixed-point scales of the sums (powers of two): weights, w v and w v^2, and squared
+// deviations from the cell means.
+struct DiagScales {
+    double w, wv, wv2, dev;
+};
+
+// Adds v to the two-word fixed-point sum at h[0], h[1].
+__device__ __forceinline__ void fx_add(long long *h, double v, double scale)
+{
+    if (v == 0.0) return;
+    long long hi, lo;
+    fx2(v, scale, hi, lo);
+    red_add(h, hi);
+    if (lo) red_add(h + 1, lo);
+}
+
+// Largest |w| and |v|^2 (as ordered bit patterns of non-negative doubles) and a flag for
+// non-finite input.
 template <class T>
-__global__ void __launch_bounds__(kDiagThreads) k_kin_sums(const SphBins g, const Particles<T> p, double *sums,
-                                                           unsigned long long *counts)
+__global__ void __launch_bounds__(kDiagThreads) k_diag_stats(const Particles<T> p, unsigned long long *mx,
+                                                             unsigned *bad)
+{
+    double bw = 0.0, bv = 0.0;
+    unsigned flag = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double vx = double(p.vx[i]), vy = double(p.vy[i]), vz = double(p.vz[i]);
+        const double v2 = vx * vx + vy * vy + vz * vz, aw = fabs(p.w[i]);
+        if (!isfinite(v2) || !isfinite(aw) || !isfinite(double(p.x[i]) + double(p.y[i]) + double(p.z[i]))) {
+            flag = 1;
+            continue;
+        }
+        bw = fmax(bw, aw);
+        bv = fmax(bv, v2);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bw = fmax(bw, __shfl_xor_sync(0xffffffffu, bw, o));
+        bv = fmax(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+    }
+    flag = __reduce_or_sync(0xffffffffu, flag);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(mx, static_cast<unsigned long long>(__double_as_longlong(bw)));
+        atomicMax(mx + 1, static_cast<unsigned long long>(__double_as_longlong(bv)));
+        if (flag) atomicOr(bad, 1u);
+    }
+}
+
+// Per bin: sum w; sum w v_c; sum w v_c^2 (c = r, theta, phi), each two int64 words.
+template <class T>
+__global__ void __launch_bounds__(kDiagThreads) k_kin_sums(const SphBins g, const Particles<T> p, DiagScales sc,
+                                                           long long *sums, unsigned long long *counts)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -85,11 +139,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_kin_sums(const SphBins g, cons
         double v[3];
         sph_velocity(x, y, z, double(p.vx[i]), double(p.vy[i]), double(p.vz[i]), v);
         const double w = p.w[i];
-        double *o = sums + (long long)b * kKinSums;
-        atomicAdd(o, w);
+        long long *o = sums + (long long)b * (2 * kKinSums);
+        fx_add(o, w, sc.w);
         for (int c = 0; c < 3; ++c) {
-            atomicAdd(o + 1 + c, w * v[c]);
-            atomicAdd(o + 4 + c, w * v[c] * v[c]);
+            fx_add(o + 2 * (1 + c), w * v[c], sc.wv);
+            fx_add(o + 2 * (4 + c), w * v[c] * v[c], sc.wv2);
         }
         atomicAdd(counts + b, 1ull);
     }
@@ -98,29 +152,35 @@ __global__ void __launch_bounds__(kDiagThreads) k_kin_sums(const SphBins g, cons
 // First pass over the (E, x) grid: each particle's cell, the cell's weight and count.
 template <class T>
 __global__ void __launch_bounds__(kDiagThreads) k_grid_sums(const Model m, const Cst<double> k, const double *lcE,
-                                                            const Particles<T> p, int *cell, double *wsum,
-                                                            unsigned long long *counts)
+                                                            const Particles<T> p, DiagScales sc, int *cell,
+                                                            long long *wsum, unsigned long long *counts)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = prior_cell<double>(m, k, lcE, double(p.x[i]), double(p.y[i]), double(p.z[i]),
                                          double(p.vx[i]), double(p.vy[i]), double(p.vz[i]));
         cell[i] = c;
-        atomicAdd(wsum + c, p.w[i]);
+        fx_add(wsum + 2 * c, p.w[i], sc.w);
         atomicAdd(counts + c, 1ull);
     }
 }
 
-// Second pass: squared deviations from the cell means.
+// Value of a two-word fixed-point sum.
+__host__ __device__ inline double fx_value(const long long *h, double scale)
+{
+    return (double(h[0]) + double(h[1]) * (1.0 / 4294967296.0)) / scale;
+}
+
+// Second pass: squared deviations from the cell means (the means from the exact sums).
 __global__ void __launch_bounds__(kDiagThreads) k_grid_dev(long long n, const int *cell, const double *w,
-                                                           const double *wsum, const unsigned long long *counts,
-                                                           double *wdev2)
+                                                           const long long *wsum, const unsigned long long *counts,
+                                                           DiagScales sc, long long *wdev2)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int c = cell[i];
-        const double d = w[i] - wsum[c] / double(counts[c]);
-        atomicAdd(wdev2 + c, d * d);
+        const double d = w[i] - fx_value(wsum + 2 * c, sc.w) / double(counts[c]);
+        fx_add(wdev2 + 2 * c, d * d, sc.dev);
     }
 }
 
@@ -194,6 +254,45 @@ int grid_of(const m2m_ctx *ctx, long long n)
     return int(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
+double pow2_floor(double x)
+{
+    int e;
+    std::frexp(x, &e);  // x = f 2^e, f in [0.5, 1)
+    return std::ldexp(1.0, e - 1);
+}
+
+// Scales that keep every bin sum of np particles below 2^62 in magnitude: |sum w| <=
+// np max|w|, |sum w v| <= np max|w| max|v|, sum w v^2 <= np max|w| max v^2, sum of
+// squared deviations <= np max|w|^2. Maxima, not sums, so the scales (and with them the
+// results) do not depend on the order of the particles.
+m2m_status diag_scales(m2m_ctx *ctx, const Source &src, long long np, Scratch &S, DiagScales &sc)
+{
+    unsigned long long *d_mx = nullptr;
+    CU(S.get(&d_mx, 4));
+    CU(cudaMemsetAsync(d_mx, 0, sizeof(unsigned long long) * 4, ctx->stream));
+    unsigned *d_bad = reinterpret_cast<unsigned *>(d_mx + 2);
+    if (np > 0) {
+        if (src.kind == 2) k_diag_stats<float><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(src.f, d_mx, d_bad);
+        else k_diag_stats<double><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(src.d, d_mx, d_bad);
+        CU(cudaGetLastError());
+    }
+    unsigned long long h[3] = {0, 0, 0};
+    CU(cudaMemcpyAsync(h, d_mx, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (h[2] & 0xFFFFFFFFull) return fail(ctx, M2M_ERR_ARG, "particles must be finite");
+    double mw, mv2;
+    std::memcpy(&mw, &h[0], sizeof mw);
+    std::memcpy(&mv2, &h[1], sizeof mv2);
+    const double two62 = 4611686018427387904.0, N = double(np > 0 ? np : 1);
+    const double W = N * (mw > 0.0 ? mw : 1.0);
+    const double v1 = mv2 > 1.0 ? std::sqrt(mv2) : 1.0, v2 = mv2 > 1.0 ? mv2 : 1.0;
+    sc.w = pow2_floor(two62 / W);
+    sc.wv = pow2_floor(two62 / (W * v1));
+    sc.wv2 = pow2_floor(two62 / (W * v2));
+    sc.dev = pow2_floor(two62 / (W * (mw > 0.0 ? mw : 1.0)));
+    return M2M_OK;
+}
+
 }  // namespace
 
 extern "C" m2m_status m2m_diag_kinematics(m2m_ctx *ctx, const m2m_sph_grid *grid, int64_t n, const double *pos,
@@ -212,24 +311,31 @@ extern "C" m2m_status m2m_diag_kinematics(m2m_ctx *ctx, const m2m_sph_grid *grid
     Source src;
     m2m_status s = source(ctx, n, pos, vel, w, S, src);
     if (s != M2M_OK) return s;
-    double *d_sums = nullptr;
+    const long long np = src.kind == 2 ? src.f.n : src.d.n;
+    DiagScales sc;
+    s = diag_scales(ctx, src, np, S, sc);
+    if (s != M2M_OK) return s;
+    long long *d_sums = nullptr;
     unsigned long long *d_cnt = nullptr;
-    CU(S.get(&d_sums, size_t(nb) * kKinSums));
+    CU(S.get(&d_sums, size_t(nb) * 2 * kKinSums));
     CU(S.get(&d_cnt, size_t(nb)));
-    CU(cudaMemsetAsync(d_sums, 0, sizeof(double) * nb * kKinSums, ctx->stream));
+    CU(cudaMemsetAsync(d_sums, 0, sizeof(long long) * nb * 2 * kKinSums, ctx->stream));
     CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * nb, ctx->stream));
     const SphBins g{grid->n_r, grid->n_phi, grid->n_ct, grid->r_min, grid->r_max, std::log(grid->r_min),
                     std::log(grid->r_max) - std::log(grid->r_min)};
-    const long long np = src.kind == 2 ? src.f.n : src.d.n;
     if (np > 0) {
-        if (src.kind == 2) k_kin_sums<float><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.f, d_sums, d_cnt);
-        else k_kin_sums<double><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.d, d_sums, d_cnt);
+        if (src.kind == 2) k_kin_sums<float><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.f, sc, d_sums, d_cnt);
+        else k_kin_sums<double><<<grid_of(ctx, np), kDiagThreads, 0, ctx->stream>>>(g, src.d, sc, d_sums, d_cnt);
         CU(cudaGetLastError());
     }
-    CU(cudaMemcpyAsync(sums, d_sums, sizeof(double) * nb * kKinSums, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<long long> hs(size_t(nb) * 2 * kKinSums);
+    CU(cudaMemcpyAsync(hs.data(), d_sums, sizeof(long long) * hs.size(), cudaMemcpyDeviceToHost, ctx->stream));
     if (counts)
         CU(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    const double scl[kKinSums] = {sc.w, sc.wv, sc.wv, sc.wv, sc.wv2, sc.wv2, sc.wv2};
+    for (long long b = 0; b < nb; ++b)
+        for (int q = 0; q < kKinSums; ++q) sums[b * kKinSums + q] = fx_value(&hs[size_t(b * kKinSums + q) * 2], scl[q]);
     return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
 }
 
@@ -254,32 +360,40 @@ extern "C" m2m_status m2m_diag_grid(m2m_ctx *ctx, const m2m_prior_grid *grid, in
     m2m_status s = source(ctx, n, pos, vel, w, S, src);
     if (s != M2M_OK) return s;
     const long long np = src.kind == 2 ? src.f.n : src.d.n;
-    double *d_ws = nullptr, *d_wd = nullptr;
+    DiagScales sc;
+    s = diag_scales(ctx, src, np, S, sc);
+    if (s != M2M_OK) return s;
+    long long *d_ws = nullptr, *d_wd = nullptr;
     unsigned long long *d_cnt = nullptr;
     int *d_cell = nullptr;
-    CU(S.get(&d_ws, size_t(ncell)));
-    CU(S.get(&d_wd, size_t(ncell)));
+    CU(S.get(&d_ws, size_t(ncell) * 2));
+    CU(S.get(&d_wd, size_t(ncell) * 2));
     CU(S.get(&d_cnt, size_t(ncell)));
     CU(S.get(&d_cell, size_t(np)));
-    CU(cudaMemsetAsync(d_ws, 0, sizeof(double) * ncell, ctx->stream));
-    CU(cudaMemsetAsync(d_wd, 0, sizeof(double) * ncell, ctx->stream));
+    CU(cudaMemsetAsync(d_ws, 0, sizeof(long long) * 2 * ncell, ctx->stream));
+    CU(cudaMemsetAsync(d_wd, 0, sizeof(long long) * 2 * ncell, ctx->stream));
     CU(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * ncell, ctx->stream));
     if (np > 0) {
         const Cst<double> kd = make_cst<double>(m);
         const int gr = grid_of(ctx, np);
         if (src.kind == 2) {
-            k_grid_sums<float><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.f, d_cell, d_ws, d_cnt);
-            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.f.w, d_ws, d_cnt, d_wd);
+            k_grid_sums<float><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.f, sc, d_cell, d_ws, d_cnt);
+            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.f.w, d_ws, d_cnt, sc, d_wd);
         } else {
-            k_grid_sums<double><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.d, d_cell, d_ws, d_cnt);
-            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.d.w, d_ws, d_cnt, d_wd);
+            k_grid_sums<double><<<gr, kDiagThreads, 0, ctx->stream>>>(m, kd, ctx->d_lcE, src.d, sc, d_cell, d_ws, d_cnt);
+            k_grid_dev<<<gr, kDiagThreads, 0, ctx->stream>>>(np, d_cell, src.d.w, d_ws, d_cnt, sc, d_wd);
         }
         CU(cudaGetLastError());
     }
-    CU(cudaMemcpyAsync(wsum, d_ws, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
-    if (wdev2) CU(cudaMemcpyAsync(wdev2, d_wd, sizeof(double) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<long long> hw(size_t(ncell) * 2), hd(size_t(ncell) * 2);
+    CU(cudaMemcpyAsync(hw.data(), d_ws, sizeof(long long) * hw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(hd.data(), d_wd, sizeof(long long) * hd.size(), cudaMemcpyDeviceToHost, ctx->stream));
     if (counts) CU(cudaMemcpyAsync(counts, d_cnt, sizeof(int64_t) * ncell, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    for (int c = 0; c < ncell; ++c) {
+        wsum[c] = fx_value(&hw[size_t(c) * 2], sc.w);
+        if (wdev2) wdev2[c] = fx_value(&hd[size_t(c) * 2], sc.dev);
+    }
     return src.kind == 0 ? M2M_OK : check_device_errors(ctx);
 }
 

@@ -1,9 +1,10 @@
 """Diagnostics on the GPU (Sec. 4.1: intrinsic kinematics in spherical bins, Delta_grid;
 Sec. 5, Fig. res: weight rms in the (E, x) cells) against the oracle on the same particles.
 
-The device sums are FP64 atomics, so they match the oracle's ordered sums to rounding:
-counts exactly, sums within 1e-12 of the column scale. The host arithmetic (moments,
-Delta_kin, Delta_grid, rms) matches the oracle's to 1e-13."""
+The device sums are exact integer sums in a two-word fixed point, so they are
+bit-reproducible whatever the order of the particles, and they match the oracle's ordered
+FP64 sums to rounding: counts exactly, sums within 1e-12 of the column scale. The host
+arithmetic (moments, Delta_kin, Delta_grid, rms) matches the oracle's to 1e-13."""
 import numpy as np
 import pytest
 
@@ -141,6 +142,40 @@ def test_full_size_c2_diagnostics_match_oracle():
     mean, disp, valid = B.kin_moments(s, c, 200)
     assert valid.sum() > 100
     assert np.median(disp[valid, 0] / disp[valid, 1]) > 1.3
+
+
+def test_diagnostic_sums_do_not_depend_on_particle_order():
+    """The same particles in reversed and in shuffled order give bit-identical sums (FP64
+    atomics would differ in the last bits when the order of the additions changes)."""
+    wl = W.make("c2", n=300_000, n_target=100_000)
+    f = _fit(W.make("c1", n=2000), "fp64")
+    p = wl.model
+    rng = np.random.default_rng(3)
+    w = p["w"] * rng.uniform(0.2, 3.0, len(p["w"]))
+    base = dict(p, w=w)
+    s0, c0 = f.diag_kinematics(KG, particles=base)
+    g0 = f.diag_grid(wl.prior, particles=base)
+    for order in (np.arange(len(w))[::-1], rng.permutation(len(w))):
+        q = {k: np.ascontiguousarray(v[order]) for k, v in base.items()}
+        s1, c1 = f.diag_kinematics(KG, particles=q)
+        g1 = f.diag_grid(wl.prior, particles=q)
+        assert np.array_equal(c0, c1) and np.array_equal(s0, s1)
+        for a, b in zip(g0, g1):
+            assert np.array_equal(a, b)
+    so, _ = O.kin_sums(KG, O.ParticleSet(base))
+    _assert_sums_close(s0, so)
+    f.close()
+
+
+def test_diagnostics_reject_non_finite_particles():
+    wl = W.make("c1", n=2000)
+    f = _fit(wl, "fp64")
+    bad = dict(wl.model)
+    bad["vx"] = bad["vx"].copy()
+    bad["vx"][7] = np.nan
+    with pytest.raises(B.M2MError, match="finite"):
+        f.diag_kinematics(KG, particles=bad)
+    f.close()
 
 
 def test_diagnostics_argument_errors():
