@@ -283,6 +283,64 @@ m2m_status m2m_batch_model(m2m_ctx *batch, int32_t i, m2m_ctx **model);
 m2m_status m2m_batch_autotune(m2m_ctx *batch, int32_t steps, int32_t *block, int32_t *blocks_per_sm,
                               int64_t *segment);
 
+/* ---- One fit split over several processes ----
+ *
+ * The paper's fits run on "the parallel code NMAGIC" (Sec. 1, Sec. 2.1): every step is a
+ * sum over particles (eq. obs) followed by work on the sums alone (eqs. myts, delta, chi,
+ * the cell means of Sec. 2.3.1). A fit can therefore be split into shards, one per process
+ * (typically one per GPU), each holding a contiguous range of the particles. Every shard
+ * makes the pass over its own particles; the caller adds the shards' integer sums word by
+ * word (an all-reduce: int64 addition, e.g. NCCL's sum over ncclInt64); then every shard
+ * runs the same finalize on the same integers. The sums are exact integers, so the split
+ * fit is bit-identical to the unsplit one whatever the number of shards: each shard's
+ * observables, chi^2, priors and Delta are those of the whole fit, and the shards' weights
+ * and particles, concatenated in shard order, are the whole fit's.
+ *
+ * Protocol, on every shard (all shards use the same descriptors and options):
+ *   m2m_shard_bounds on the shard's particles; the caller sums w_sum and takes the maximum
+ *     of v2_bound over the shards; m2m_shard_set with those and the total particle count;
+ *   m2m_load_particles (its pass), exchange, m2m_step_end (completes the load);
+ *   per step: m2m_step_begin, exchange, m2m_step_end;
+ *   to read weights: m2m_shard_weights_begin, exchange, m2m_get_weights.
+ * "exchange" = replace every shard's words (m2m_shard_exchange) by their sum over the
+ * shards, ordered after the shard's stream work (on its stream, or synchronise first).
+ * The words are zero outside an exchange. m2m_step and checkpoints are rejected on a shard
+ * (M2M_ERR_STATE), and so are the diagnostics of the fit's own particles (pass them
+ * explicitly). Device errors are latched per shard and reported by that shard's next
+ * synchronising call. */
+
+/* Bounds a shard contributes (host arrays of n particles, layout of m2m_load_particles):
+ * the sum of its weights and the largest 2 (E - phi_min) of its particles in the fit's
+ * potential, i.e. the largest v^2 it can reach. Synchronous. */
+m2m_status m2m_shard_bounds(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel, const double *w,
+                            double *w_sum, double *v2_bound);
+
+/* Makes ctx one shard of a fit of n_total particles whose initial weights sum to w_total and
+ * whose v2 bound (maximum over the shards of m2m_shard_bounds) is v2_bound. Call it before
+ * loading; every shard must pass the same values. A shard whose own particles exceed
+ * v2_bound is rejected at load (M2M_ERR_ARG). */
+m2m_status m2m_shard_set(m2m_ctx *ctx, int64_t n_total, double w_total, double v2_bound);
+
+/* The device array of int64 words a shard exchanges and their count: the fixed-point sums of
+ * the observables, the total weight and the prior grid, one word of the deposited weight
+ * for the overflow check, and two words of the weight total for read-outs. Owned by ctx. */
+m2m_status m2m_shard_exchange(m2m_ctx *ctx, int64_t **words_dev, int64_t *count);
+
+/* One step's pass over the shard's particles (pending force of change, push, deposit,
+ * prior binning on update steps), asynchronous on the shard's stream; its sums are left in
+ * the exchange words. With timing on, the pass is what is timed. */
+m2m_status m2m_step_begin(m2m_ctx *ctx);
+
+/* The finalize of the step (or of the load) from the summed words: smoothing, Delta_j,
+ * chi^2, force-of-change coefficients and, on update steps, the priors. Asynchronous,
+ * except after a load. */
+m2m_status m2m_step_end(m2m_ctx *ctx);
+
+/* Applies the pending force of change to the shard's weights and leaves their total in the
+ * exchange words; after the exchange, m2m_get_weights renormalises them with the whole
+ * fit's total and returns them. */
+m2m_status m2m_shard_weights_begin(m2m_ctx *ctx);
+
 /* Write / read the full fit state (particles, weights, priors, smoothed
  * observables, step counter, pending update) to / from a file. A context
  * resumed from a file continues bit-identically to an uninterrupted run with
@@ -326,10 +384,13 @@ m2m_status m2m_build_targets(const m2m_observables *obs, int64_t n, const double
  * 320 KiB that every GPU loading this library holds until the process exits. The
  * array limits J to 8192 observables, the apertures to 8192 and the annulus edges
  * to 8192 in total; larger sets are rejected with M2M_ERR_ARG. The first call on a
- * device looks up the array's device address, so make that first call before any
- * stream capture. Every call reuses the array (its sums are cleared at the start
- * of each call), so calls that overlap on the GPU, on any streams, race: issue
- * them one after another. The call synchronises `stream` before returning.
+ * device looks up the array's device address (cudaGetSymbolAddress) and sets the
+ * library's constant tables on that device. Every call copies the aperture tables
+ * from host memory, reads its range statistics back into host memory and
+ * synchronises `stream` before returning, so no call of it may be made while a
+ * stream is being captured into a CUDA graph. Every call reuses the array (its sums
+ * are cleared at the start of each call), so calls that overlap on the GPU, on any
+ * streams, race: issue them one after another.
  * Errors go to m2m_last_error(NULL): M2M_ERR_ARG for invalid input, M2M_ERR_CUDA,
  * M2M_ERR_OVERFLOW if a deposit left the fixed-point range. */
 m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, const double *pos_dev,
@@ -345,8 +406,11 @@ m2m_status m2m_observe_static(const m2m_observables *obs, int64_t n, const doubl
  * The binning calls take either the fit's own particles (n = 0 and pos, vel, w all NULL:
  * the state in the fit's precision and the weights of m2m_get_weights), or n particles
  * from the caller's host arrays (pos, vel: 3n values each, x then y then z; w: n values),
- * for example a realisation of the target. Bins are decided in FP64. Sums are FP64
- * atomics: equal to an ordered sum up to rounding, not bit-reproducible. Outputs go to
+ * for example a realisation of the target. Bins are decided in FP64. Sums are exact integer
+ * sums in a two-word fixed point (the integer part and 32 fraction bits of v * 2^s, with s
+ * set from the largest |w| and |v|^2 of the particles), converted to FP64 at the end: they
+ * equal the FP64 sum to a relative 2^-90 of its bound and are bit-reproducible, whatever the
+ * order of the particles. Non-finite particles are rejected (M2M_ERR_ARG). Outputs go to
  * caller-owned host buffers. The calls synchronise the fit's stream. */
 
 /* Spherical polar bins of the intrinsic kinematics (Sec. 4.1): n_r shells, the first

@@ -131,8 +131,15 @@ def lib():
         L.m2m_delta_kin.argtypes = [C.c_int64, _DP, _I64P, _DP, _I64P, C.c_int64, _DP, _I64P]
         L.m2m_delta_grid.argtypes = [C.c_int32, _DP, _DP, _DP]
         L.m2m_weight_rms.argtypes = [C.c_int32, _DP, _I64P, C.c_int64, _DP]
+        L.m2m_shard_bounds.argtypes = [vp, C.c_int64, _DP, _DP, _DP, _DP, _DP]
+        L.m2m_shard_set.argtypes = [vp, C.c_int64, C.c_double, C.c_double]
+        L.m2m_shard_exchange.argtypes = [vp, C.POINTER(C.c_void_p), _I64P]
+        L.m2m_step_begin.argtypes = [vp]
+        L.m2m_step_end.argtypes = [vp]
+        L.m2m_shard_weights_begin.argtypes = [vp]
         for name in ("m2m_diag_kinematics", "m2m_diag_grid", "m2m_kin_moments", "m2m_delta_kin",
-                     "m2m_delta_grid", "m2m_weight_rms"):
+                     "m2m_delta_grid", "m2m_weight_rms", "m2m_shard_bounds", "m2m_shard_set",
+                     "m2m_shard_exchange", "m2m_step_begin", "m2m_step_end", "m2m_shard_weights_begin"):
             getattr(L, name).restype = C.c_int
         for name in ("m2m_create", "m2m_load_particles", "m2m_load_particles_device", "m2m_step",
                      "m2m_synchronize", "m2m_get_weights", "m2m_get_state", "m2m_get_observables",
@@ -415,6 +422,33 @@ class Fit:
         lam = C.c_double()
         self._ck(lib().m2m_get_prior_smoothing(self.h, _dp(raw), C.byref(lam)))
         return raw[:self.ncell], lam.value
+
+    # ---- one shard of a fit split over processes (m2m_shard_*)
+
+    def shard_bounds(self, particles: dict):
+        """(sum of weights, largest 2 (E - phi_min)) of these particles (m2m_shard_bounds)."""
+        n, pos, vel, w = _particles(particles)
+        ws, v2 = C.c_double(), C.c_double()
+        self._ck(lib().m2m_shard_bounds(self.h, n, _dp(pos), _dp(vel), _dp(w), C.byref(ws), C.byref(v2)))
+        return ws.value, v2.value
+
+    def shard_set(self, n_total: int, w_total: float, v2_bound: float):
+        self._ck(lib().m2m_shard_set(self.h, n_total, w_total, v2_bound))
+
+    def shard_exchange(self):
+        """(device address, count) of the int64 words to add over the shards."""
+        p, k = C.c_void_p(), C.c_int64()
+        self._ck(lib().m2m_shard_exchange(self.h, C.byref(p), C.byref(k)))
+        return p.value, k.value
+
+    def step_begin(self):
+        self._ck(lib().m2m_step_begin(self.h))
+
+    def step_end(self):
+        self._ck(lib().m2m_step_end(self.h))
+
+    def shard_weights_begin(self):
+        self._ck(lib().m2m_shard_weights_begin(self.h))
 
     def step_count(self) -> int:
         t = C.c_int64()

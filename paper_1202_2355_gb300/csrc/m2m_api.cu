@@ -521,7 +521,7 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMalloc(&ctx->d_lprior, sizeof(double) * (m.ncell + 1)));
     CU(cudaMemset(ctx->d_lprior, 0, sizeof(double) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_prior_count, sizeof(long long) * (m.ncell + 1)));
-    CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * m.hist_words));
+    CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * exchange_words(ctx)));
     CU(cudaMalloc(&ctx->d_acc, sizeof(long long) * 2));
     CU(cudaMalloc(&ctx->d_sc, sizeof(Scalars)));
     CU(cudaMemset(ctx->d_c, 0, sizeof(double) * m.J));
@@ -530,7 +530,7 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMemset(ctx->d_delta, 0, sizeof(double) * m.J));
     CU(cudaMemset(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1)));
     CU(cudaMemset(ctx->d_prior_count, 0, sizeof(long long) * (m.ncell + 1)));
-    CU(cudaMemset(ctx->d_hist, 0, sizeof(long long) * m.hist_words));
+    CU(cudaMemset(ctx->d_hist, 0, sizeof(long long) * exchange_words(ctx)));
     CU(cudaMemset(ctx->d_sc, 0, sizeof(Scalars)));
     return M2M_OK;
 }
@@ -633,7 +633,9 @@ static void launch_one(m2m_ctx *c, int push, int init)
 {
     if (c->precision == M2M_PREC_FP64) launch_step<double, 2>(c, push, init);
     else launch_step<float, 1>(c, push, init);
-    smooth_launch(c);
+    // a shard's sums wait for the caller's exchange; the finalize and smoothing follow it
+    if (c->m.shard) k_shard_pack<<<1, 32, 0, c->stream>>>(c->d_hist, c->m.hist_words, c->d_sc);
+    else smooth_launch(c);
 }
 
 template <class T, int WPS>
@@ -667,6 +669,8 @@ static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
     return M2M_OK;
 }
 
+static m2m_status place_window(m2m_ctx *ctx);
+
 // Sets the fixed-point scales from the loaded particles, then deposits y_0.
 static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, const double *dz,
                               const double *dvx, const double *dvy, const double *dvz,
@@ -691,6 +695,16 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     if (bad) return fail(ctx, M2M_ERR_ARG, "particles must be finite with weights >= 0");
     double v2max;
     std::memcpy(&v2max, &v2bits, sizeof v2max);
+    m.n_all = ctx->n;
+    if (ctx->shard) {
+        // every shard takes the whole fit's bounds, so that all shards add the same integers
+        if (v2max > ctx->shard_v2)
+            return fail(ctx, M2M_ERR_ARG, "this shard's particles reach v^2 = %g above the shard bound %g", v2max,
+                        ctx->shard_v2);
+        v2max = ctx->shard_v2;
+        W0_host = ctx->shard_w;
+        m.n_all = ctx->shard_n;
+    }
     // fixed-point ranges. Weights are deposited before renormalisation, so the total
     // may exceed W0 by the largest single-step growth exp(eps dt F): FP64 mode keeps
     // 2^24 W0 of range (the second word still resolves 2^-70 W0), mixed mode 2^12 W0
@@ -709,7 +723,7 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
         ctx->obs_iscale[j] = 1.0 / s;
     }
     CU(cudaMemcpyAsync(ctx->d_iscale, ctx->obs_iscale.data(), sizeof(double) * m.J, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemsetAsync(ctx->d_hist, 0, sizeof(long long) * m.hist_words, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_hist, 0, sizeof(long long) * exchange_words(ctx), ctx->stream));
     Scalars sc0{};
     sc0.Wrange = 9.2233720368547758e18 / m.fx_w;
     CU(cudaMemcpyAsync(ctx->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
@@ -721,6 +735,22 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     launch_one(ctx, 0, 1);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    if (ctx->shard) {  // y_0 needs every shard's sums: m2m_step_end completes the load
+        ctx->shard_pending = 1;
+        return M2M_OK;
+    }
+    return place_window(ctx);
+}
+
+// The aperture window of the global-deposit kernel on the densest range of the first
+// deposit (any placement gives the same sums; this one keeps most deposits block-shared).
+static m2m_status place_window(m2m_ctx *ctx)
+{
+    Model &m = ctx->m;
     if (ctx->global_dep && m.win_n > 0 && m.win_n < m.g[m.win_group].n_ap) {
         // place the aperture window on the densest range of the first deposit (any
         // placement gives the same sums; this one keeps most deposits block-shared)
@@ -737,10 +767,6 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
             }
         }
     }
-    if (ctx->graph) {
-        cudaGraphExecDestroy(ctx->graph);
-        ctx->graph = nullptr;
-    }
     ctx->loaded = true;
     return M2M_OK;
 }
@@ -754,6 +780,7 @@ static m2m_status load_common(m2m_ctx *ctx, int64_t n, const double *pos, const 
     ++ctx->load_gen;
     if (n > 0x7fffffffll * 64) return fail(ctx, M2M_ERR_ARG, "too many particles");
     ctx->loaded = false;
+    ctx->shard_pending = 0;
     m2m_status s = ensure_capacity(ctx, n);
     if (s != M2M_OK) return s;
     ctx->n = n;
@@ -834,6 +861,7 @@ extern "C" m2m_status m2m_step(m2m_ctx *ctx, int64_t nsteps)
 {
     if (!ctx) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return batch_step(ctx, nsteps);
+    if (ctx->shard) return fail(ctx, M2M_ERR_STATE, "a shard steps with m2m_step_begin and m2m_step_end");
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (nsteps < 0) return fail(ctx, M2M_ERR_ARG, "nsteps must be >= 0");
     if (ctx->timing) {
@@ -898,12 +926,176 @@ static void launch_materialize(m2m_ctx *c)
     k_scale<<<g, 256, 0, c->stream>>>(c->d_wout, c->n, c->d_acc, c->m, c->d_sc);
 }
 
+// ------------------------------------------------------------------ shards of one fit
+
+extern "C" m2m_status m2m_shard_bounds(m2m_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                                       const double *w, double *w_sum, double *v2_bound)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (n < 0 || (n > 0 && (!pos || !vel || !w)) || !w_sum || !v2_bound)
+        return fail(ctx, M2M_ERR_ARG, "n >= 0 and non-null arrays required");
+    double W = 0.0;
+    for (long long i = 0; i < n; ++i) W += w[i];
+    *w_sum = W;
+    *v2_bound = 0.0;
+    if (n == 0) return M2M_OK;
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * size_t(n);
+    CU(cudaMalloc(&d, bytes * 7 + 16));
+    unsigned long long *d_v2 = reinterpret_cast<unsigned long long *>(d + 7 * n);
+    unsigned *d_bad = reinterpret_cast<unsigned *>(d_v2 + 1);
+    cudaError_t e = cudaMemcpyAsync(d, pos, bytes * 3, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 3 * n, vel, bytes * 3, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + 6 * n, w, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_v2, 0, 16, ctx->stream);
+    if (e == cudaSuccess) {
+        k_load_stats<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(ctx->m, make_cst<double>(ctx->m), d, d + n, d + 2 * n,
+                                                            d + 3 * n, d + 4 * n, d + 5 * n, d + 6 * n, n, d_v2, d_bad);
+        e = cudaGetLastError();
+    }
+    unsigned long long h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_v2, 16, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ctx, M2M_ERR_CUDA, "shard bounds: %s", cudaGetErrorString(e));
+    if (h[1] & 0xFFFFFFFFull) return fail(ctx, M2M_ERR_ARG, "particles must be finite with weights >= 0");
+    std::memcpy(v2_bound, &h[0], sizeof(double));
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_shard_set(m2m_ctx *ctx, int64_t n_total, double w_total, double v2_bound)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (n_total < 0 || !(w_total > 0.0) || !std::isfinite(w_total) || !(v2_bound >= 0.0) || !std::isfinite(v2_bound))
+        return fail(ctx, M2M_ERR_ARG, "n_total >= 0, w_total > 0 and a finite v2_bound >= 0 required");
+    ctx->shard = true;
+    ctx->shard_n = n_total;
+    ctx->shard_w = w_total;
+    ctx->shard_v2 = v2_bound;
+    ctx->shard_pending = 0;
+    ctx->loaded = false;
+    ctx->m.shard = 1;
+    if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+    }
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_shard_exchange(m2m_ctx *ctx, int64_t **words_dev, int64_t *count)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (!ctx->shard) return fail(ctx, M2M_ERR_STATE, "not a shard (m2m_shard_set)");
+    if (!words_dev || !count) return fail(ctx, M2M_ERR_ARG, "null output");
+    *words_dev = reinterpret_cast<int64_t *>(ctx->d_hist);
+    *count = exchange_words(ctx);
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_step_begin(m2m_ctx *ctx)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (!ctx->shard) return fail(ctx, M2M_ERR_STATE, "not a shard: use m2m_step");
+    if (!ctx->loaded || ctx->shard_pending != 0)
+        return fail(ctx, M2M_ERR_STATE, "m2m_step_begin needs a loaded shard with no exchange pending");
+    cudaEvent_t *ev = nullptr;
+    if (ctx->timing) {
+        while (ctx->events.size() < 2 * (ctx->timed + 1)) {
+            cudaEvent_t e;
+            CU(cudaEventCreate(&e));
+            ctx->events.push_back(e);
+        }
+        ev = &ctx->events[2 * ctx->timed];
+        CU(cudaEventRecord(ev[0], ctx->stream));
+    }
+    if (ctx->precision == M2M_PREC_FP64) launch_step<double, 2>(ctx, 1, 0);
+    else launch_step<float, 1>(ctx, 1, 0);
+    if (ev) {
+        CU(cudaEventRecord(ev[1], ctx->stream));
+        ++ctx->timed;
+    }
+    k_shard_pack<<<1, 32, 0, ctx->stream>>>(ctx->d_hist, ctx->m.hist_words, ctx->d_sc);
+    CU(cudaGetLastError());
+    ctx->shard_pending = 2;
+    return M2M_OK;
+}
+
+extern "C" m2m_status m2m_step_end(m2m_ctx *ctx)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (!ctx->shard) return fail(ctx, M2M_ERR_STATE, "not a shard: use m2m_step");
+    if (ctx->shard_pending != 1 && ctx->shard_pending != 2)
+        return fail(ctx, M2M_ERR_STATE, "m2m_step_end follows a load or m2m_step_begin");
+    const int init = ctx->shard_pending == 1;
+    const int threads = ctx->block;  // the finalize block of m2m_step, so chi^2 adds in the same order
+    if (ctx->precision == M2M_PREC_FP64)
+        k_finalize<double, 2><<<1, threads, sizeof(double) * threads, ctx->stream>>>(ctx->m, buffers(ctx), init);
+    else
+        k_finalize<float, 1><<<1, threads, sizeof(double) * threads, ctx->stream>>>(ctx->m, buffers(ctx), init);
+    smooth_launch(ctx);
+    CU(cudaGetLastError());
+    ctx->shard_pending = 0;
+    if (!init) return M2M_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    return place_window(ctx);
+}
+
+extern "C" m2m_status m2m_shard_weights_begin(m2m_ctx *ctx)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (!ctx->shard) return fail(ctx, M2M_ERR_STATE, "not a shard");
+    if (!ctx->loaded || ctx->shard_pending != 0)
+        return fail(ctx, M2M_ERR_STATE, "m2m_shard_weights_begin needs a loaded shard with no exchange pending");
+    if (ctx->wout_cap < ctx->n || !ctx->d_wout) {
+        free_dev(ctx->d_wout);
+        CU(cudaMalloc(&ctx->d_wout, sizeof(double) * (ctx->n > 0 ? ctx->n : 1)));
+        ctx->wout_cap = ctx->n;
+    }
+    long long *acc = ctx->d_hist + ctx->m.hist_words + 1;
+    CU(cudaMemsetAsync(acc, 0, 2 * sizeof(long long), ctx->stream));
+    if (ctx->n > 0) {
+        const int g = ctx->nsm * 4;
+        if (ctx->precision == M2M_PREC_FP64)
+            k_materialize<double><<<g, 256, ctx->smem_mat, ctx->stream>>>(ctx->m, make_cst<double>(ctx->m),
+                                                                         state<double>(ctx), buffers(ctx), ctx->d_wout, acc);
+        else
+            k_materialize<float><<<g, 256, ctx->smem_mat, ctx->stream>>>(ctx->m, make_cst<float>(ctx->m),
+                                                                        state<float>(ctx), buffers(ctx), ctx->d_wout, acc);
+    }
+    CU(cudaGetLastError());
+    ctx->shard_pending = 3;
+    return M2M_OK;
+}
+
+// The shard's weights after the exchange of m2m_shard_weights_begin: renormalised with the
+// summed total of all shards.
+static m2m_status shard_weights_end(m2m_ctx *ctx, double *w)
+{
+    if (ctx->shard_pending != 3)
+        return fail(ctx, M2M_ERR_STATE, "a shard reads its weights after m2m_shard_weights_begin and the exchange");
+    long long *acc = ctx->d_hist + ctx->m.hist_words + 1;
+    if (ctx->n > 0) {
+        k_scale<<<ctx->nsm * 4, 256, 0, ctx->stream>>>(ctx->d_wout, ctx->n, acc, ctx->m, ctx->d_sc);
+        CU(cudaMemcpyAsync(w, ctx->d_wout, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CU(cudaMemsetAsync(acc, 0, 2 * sizeof(long long), ctx->stream));
+    ctx->shard_pending = 0;
+    return m2m_synchronize(ctx);
+}
+
 extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
 {
     if (!ctx) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
     if (n != ctx->n || (n > 0 && !w)) return fail(ctx, M2M_ERR_ARG, "n must equal the loaded count (%lld)", ctx->n);
+    if (ctx->shard) return shard_weights_end(ctx, w);
     if (n == 0) return m2m_synchronize(ctx);
     m2m_status s = current_weights(ctx);
     if (s != M2M_OK) return s;
@@ -913,6 +1105,8 @@ extern "C" m2m_status m2m_get_weights(m2m_ctx *ctx, double *w, int64_t n)
 
 m2m_status current_weights(m2m_ctx *ctx)
 {
+    if (ctx->shard)
+        return fail(ctx, M2M_ERR_STATE, "a shard's weights need the exchange of m2m_shard_weights_begin");
     if (ctx->wout_cap < ctx->n) {
         free_dev(ctx->d_wout);
         CU(cudaMalloc(&ctx->d_wout, sizeof(double) * ctx->n));
@@ -1062,6 +1256,7 @@ struct CkptHeader {
 
 extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 {
+    if (ctx && ctx->shard) return fail(ctx, M2M_ERR_STATE, "checkpoints of shards are not supported");
     if (!ctx || !path) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
@@ -1124,6 +1319,7 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 
 extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
 {
+    if (ctx && ctx->shard) return fail(ctx, M2M_ERR_STATE, "checkpoints of shards are not supported");
     if (!ctx || !path) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return not_a_fit(ctx);
     FILE *f = std::fopen(path, "rb");
@@ -1512,8 +1708,9 @@ static std::mutex g_static_mu;
 static void *g_static_addr[256];
 
 // Device address of the scratch array for the current device. The first call on a
-// device asks the runtime for it (cudaGetSymbolAddress) and sets the exp table, so
-// that call should not happen inside a stream capture.
+// device asks the runtime for it (cudaGetSymbolAddress) and sets the constant tables.
+// (m2m_observe_static as a whole synchronises its stream and reads back to host
+// memory, so it is never called inside a stream capture.)
 static m2m_status static_scratch(unsigned char **out)
 {
     int dev = 0;

@@ -70,7 +70,17 @@ struct m2m_ctx {
     m2m_ctx *parent = nullptr;   // the owning batch (a fit handle from m2m_batch_model)
     BatchState *bs = nullptr;    // launch configuration and device arrays of a batch
     long long load_gen = 0;      // incremented by every load of particles or state
+
+    // one shard of a fit split over processes (m2m_shard_set): the whole fit's particle
+    // count, total weight and v^2 bound; the phase waiting for the caller's exchange
+    bool shard = false;
+    long long shard_n = 0;
+    double shard_w = 0.0, shard_v2 = 0.0;
+    int shard_pending = 0;  // 0 none; 1 load pass, 2 step pass (m2m_step_end next); 3 weights
 };
+
+// int64 words a context exchanges (the fixed-point sums, the range word, two weight words)
+inline long long exchange_words(const m2m_ctx *c) { return (long long)c->m.hist_words + 3; }
 
 extern thread_local std::string g_create_error;
 

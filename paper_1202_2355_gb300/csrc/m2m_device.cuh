@@ -96,6 +96,11 @@ struct Model {
     // global-deposit kernel: apertures [win_lo, win_lo + win_n) of group win_group keep
     // block-shared sums (the densest range, placed at load); the rest deposit globally
     int win_group, win_lo, win_n;
+    // one shard of a fit split over processes: the step kernel leaves its integer sums for
+    // the caller to add over the shards, and k_finalize runs the finalize afterwards;
+    // n_all is the particle count of the whole fit (the local count when not sharded)
+    int shard;
+    long long n_all;
 };
 
 constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
@@ -1726,6 +1731,7 @@ __global__ void __launch_bounds__(kStepMaxThreads<T, GA>, (GA && sizeof(T) == 4)
     step_particles<T, GA, M0, M1, M2, M3>(m, k, P, b, S, f, push, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                                           P.n, (long long)gridDim.x * blockDim.x, err, wtot, wdep);
     block_flush<T, WPS, GA>(m, k, b, S, f.prior_step, err, wtot, wdep);
+    if (m.shard) return;  // the sums of all shards are added by the caller; k_finalize follows
     // last block to finish runs the finalize
     if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
@@ -1733,6 +1739,42 @@ __global__ void __launch_bounds__(kStepMaxThreads<T, GA>, (GA && sizeof(T) == 4)
         __threadfence();
         finalize_block<WPS>(m, b, P.n, init, f.prior_step, reinterpret_cast<double *>(smem));
     }
+}
+
+// ---------------------------------------------------------------- shards of one fit
+//
+// A fit whose particles are split over several processes (contiguous ranges, one per
+// shard) runs the per-particle pass of a step on every shard (k_step with Model::shard),
+// then the caller adds the shards' integer sums word by word (an all-reduce), and every
+// shard runs the same finalize on the same integers (k_finalize): the result is
+// bit-identical to the unsplit fit. The exchanged words are the fixed-point sums of
+// Model::hist_words, then one range word (the deposited weight in units of
+// Wrange 2^-40, for the overflow check) and two words of the total weight that a
+// weight read-out renormalises with.
+constexpr double kRangeUnit = 1.0 / 1099511627776.0;  // 2^-40
+
+// After a shard's pass: its floating-point deposited weight into the range word.
+static __global__ void k_shard_pack(long long *hist, int hist_words, Scalars *sc)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        hist[hist_words] = llrint(ceil(sc->Wcheck / (sc->Wrange * kRangeUnit)));
+        sc->Wcheck = 0.0;
+    }
+}
+
+// The finalize of a shard from the exchanged (summed) words. red: blockDim doubles.
+template <class T, int WPS>
+__global__ void k_finalize(const Model m, const Buffers b, int init)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const StepFlags<T> f = step_flags<T>(m, *b.sc, init);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        b.sc->Wcheck = double(b.hist[m.hist_words]) * (b.sc->Wrange * kRangeUnit);
+        b.hist[m.hist_words] = 0;
+    }
+    __syncthreads();
+    finalize_block<WPS>(m, b, m.n_all, init, f.prior_step, reinterpret_cast<double *>(smem));
 }
 
 // ---------------------------------------------------------------- batched step kernel
