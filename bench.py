@@ -1,14 +1,18 @@
 #!/usr/bin/env python
-"""M2M particle-steps/s on one GB300 (or N, one independent fit per GPU).
+"""M2M particle-steps/s on one GB300 (or N GPUs, one process each).
 
-A "step" is one full M2M step over all particles of one fit: the pending force
-of change, the leap-frog push, the observable deposit, the prior binning on
-update steps, and the finalize (smoothing, residuals, chi^2, priors). The
-default workload is the 1,000,000-particle FP64 Hernquist fit (60 surface-
-density annuli, 30 annuli of v2/h3/h4, 50 x 20 prior grid, dt 0.005).
+A "step" is one full M2M step over all particles: the pending force of change,
+the leap-frog push, the observable deposit, the prior binning on update steps,
+and the finalize (smoothing, residuals, chi^2, priors). The default workload is
+the batch of 96 independent mixed-precision fits (Hernquist + NFW potentials,
+5.2e7 particles in all, 150 observables and a 50 x 20 prior grid each, dt 0.005)
+advanced by one launch per step. `--workload c1..c4` selects a single fit
+(c2: the 1,000,000-particle FP64 Hernquist fit).
 
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
-recorded by the library on its stream; L2 is flushed (256 MiB write) between
+Timing: at least W untimed warm-up steps, continued until the next step is a
+prior-update step, then exactly K steps, each bracketed by CUDA events recorded
+by the library on its stream, so the timed window holds ceil(K / P) of the
+binning steps that come every P = 25 steps. L2 is flushed (256 MiB write) between
 timed steps, outside the timed events. Max over ranks. `e2e` repeats the run
 through the public API from pinned host buffers: load, K x (step, read chi^2),
 read the weights, wall clock. `--impl reference` times the CPU oracle.
@@ -56,12 +60,17 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 #   flops         FP64 flops the FP64 kernel executes (DFMA = 2, DADD/DMUL = 1: ncu
 #                 sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on.sum over
 #                 one step launch / N), including the iterative sqrt, division, log
-#                 and exp.
+#                 and exp;
+#   method_flops  operations the method itself asks for per particle-step on the
+#                 1M-particle FP64 workload (an FMA counts 2; a square root, a division,
+#                 an exp or a log counts 1): push 31, projection 6, aperture radius 3,
+#                 kernel values 21, force of change 23, weight 2, total weight 1, and the
+#                 prior binning of one step in 25 (40 / 25 = 1.6), rounded to 88.
 KERNEL_FIGURES = {
     # method: 7 x 8 B read and written, cell 2 B = 114 B; design: read x..vz, ln w,
     # ax..az (80 B), prior cell, cached apertures and cached exp(-nu^2/2) (2 + 2 + 8 B);
     # write 80 + 2 + 8 B
-    "fp64": {"bytes": 114, "design_bytes": 182, "flops": 151.37},
+    "fp64": {"bytes": 114, "design_bytes": 182, "flops": 151.37, "method_flops": 88},
     # method: 7 x 4 B read and written, cell 2 B = 58 B; design: read 6 coordinates + w
     # (28 B), prior cell and cached apertures (2 + 2 B); write 28 B + 2 B of apertures
     "mixed": {"bytes": 58, "design_bytes": 62, "flops": None},
@@ -133,6 +142,44 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def host_cpu() -> dict:
+    """Logical cores and CPU model of this host (the oracle's timings run here)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def align_to_prior_step(fit_or_batch, t: int, every: int, step) -> int:
+    """Untimed steps so that the next step is a prior-update step: priors are binned at
+    steps t = 1, 1 + P, 1 + 2P, ..., so after t completed steps the next one bins when
+    t is a multiple of P. Returns the number of steps taken."""
+    extra = (-t) % every
+    for _ in range(extra):
+        step()
+    return extra
+
+
+def prior_steps_in(t0: int, K: int, every: int) -> int:
+    """Prior-update steps among steps t0 + 1 .. t0 + K."""
+    return sum(1 for t in range(t0 + 1, t0 + K + 1) if (t - 1) % every == 0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -140,13 +187,15 @@ def _dist():
     return ws, rank, local
 
 
-def roofline(workload: str, precision: str, n: int, ms_per_launch: float) -> dict:
+def roofline(workload: str, precision: str, n: int, ms_per_launch: float, kernel: str = "k_step") -> dict:
     """Roofline of the step kernel (the only kernel of the timed region).
 
-    The FP64 kernel is bound by the FP64 pipe (HBM stays mostly idle); the mixed
-    kernel is compared with HBM. Achieved bandwidth counts the method's 58 B (FP32) or
-    114 B (FP64) per particle-step; design_gbs counts what the kernel streams with its
-    caches (62 B, 86 B where it keeps the acceleration, 182 B in FP64)."""
+    The headline is the HBM fraction at the method's state traffic: 58 B (FP32) or
+    114 B (FP64) per particle-step, the coordinates and the weight read and written
+    and the 2-byte prior cell read. design_gbs counts what the kernel streams with its
+    caches (62 B, 86 B where it keeps the acceleration, 182 B in FP64). The FP64 kernel
+    is bound by the FP64 pipe rather than HBM; its ALU fraction is given beside the
+    headline, from the method's own operation count per particle-step."""
     f = dict(KERNEL_FIGURES[precision])
     if precision == "mixed" and workload in MIXED_CACHED_ACCEL:
         f["design_bytes"] += ACCEL_BYTES_MIXED
@@ -156,22 +205,21 @@ def roofline(workload: str, precision: str, n: int, ms_per_launch: float) -> dic
     hbm, hbm_src = _hbm_peak()
     dram = DRAM_PER_UNIT.get((workload, precision))
     traffic = None if dram is None else dram[0] * n
-    common = {"kernel": "k_step", "units_per_launch": n, "unit_of_work": "particle-step",
-              "ms_per_launch": ms_per_launch, "algorithmic_bytes_per_unit": f["bytes"],
-              "design_bytes_per_unit": f["design_bytes"], "design_gbs": design_gbs,
-              "traffic_per_unit_measured_at_n": None if dram is None else dram[1]}
+    out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+           "traffic": traffic, "peak_source": hbm_src + " (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured"
+           else hbm_src,
+           "kernel": kernel, "units_per_launch": n, "unit_of_work": "particle-step",
+           "ms_per_launch": ms_per_launch, "algorithmic_bytes_per_unit": f["bytes"],
+           "design_bytes_per_unit": f["design_bytes"], "design_gbs": design_gbs,
+           "design_frac": design_gbs / hbm,
+           "traffic_per_unit_measured_at_n": None if dram is None else dram[1]}
     if precision == "fp64":
-        out = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": None,
-               "traffic": traffic, "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
-               "fp64_flops_per_unit": f["flops"],
-               "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": hbm_src}}
-        if f["flops"] is not None:
-            out["achieved"] = f["flops"] * n / sec / 1e12
-            out["frac"] = out["achieved"] / FP64_PEAK_TFLOPS
-    else:
-        out = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-               "traffic": traffic, "peak_source": hbm_src}
-    out.update(common)
+        method = f["method_flops"]
+        out["alu"] = {"bound_in_practice": "fp64 pipe", "method_flops_per_unit": method,
+                      "achieved_tflops": method * n / sec / 1e12, "peak_tflops": FP64_PEAK_TFLOPS,
+                      "frac": method * n / sec / 1e12 / FP64_PEAK_TFLOPS,
+                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz",
+                      "executed_flops_per_unit": f["flops"]}
     return out
 
 
@@ -223,7 +271,8 @@ def run_reference(args):
             "config": {"workload": wl.name, "sample_particles": n_sample,
                        "note": "CPU FP64 oracle, single thread, on the first particles of the workload"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n_sample} particles of {wl.name}, {args.steps} steps"},
+                             "sample": f"{n_sample} particles of {wl.name}, {args.steps} steps",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -284,8 +333,11 @@ def run_batch(args):
     K, Wm = args.steps, args.warmup
     n_all = W.batch_draws()[0]
     scale = 1.0 if args.n is None else args.n / float(n_all.sum())
-    # every rank runs its own copy of the batch: weak scaling, no collective on the data path
-    wls = W.make_batch(n_scale=scale)
+    # the 96 fits are split over the ranks by particle count (strong scaling: the job is
+    # fixed); each rank advances its share as one batch, with no collective on the data path
+    from paper_1202_2355_gb300 import dist as D
+    mine = D.split_fits(np.maximum(1, (n_all * scale).astype(np.int64)), ws)[rank]
+    wls = W.make_batch(n_scale=scale, fits=mine)
     descs = []
     for wl in wls:
         Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
@@ -299,10 +351,18 @@ def run_batch(args):
         f.load(wl.model)
     shape = batch.autotune(steps=2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    every = wls[0].prior["update_every"]
+
+    def one_step():
+        batch.step(1)
+        flush.fill_(1)
+
     with torch.cuda.stream(stream):
         for _ in range(Wm):
-            batch.step(1)
-            flush.fill_(1)
+            one_step()
+        batch.synchronize()
+        t_start = batch.fits[0].step_count()
+        t_start += align_to_prior_step(batch, t_start, every, one_step)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -319,12 +379,14 @@ def run_batch(args):
     batch.set_timing(False)
     assert nt == K
     chi2_per_J = float(np.mean([f.chi2() / f.J for f in batch.fits]))
+    n_job = int(np.maximum(1, (n_all * scale).astype(np.int64)).sum())
     if ws > 1:
         t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_ms = float(t[0])
         dist.barrier()
-    value = ws * ntot * K / (step_ms / 1e3)
+    # every rank's share of the job is done within the slowest rank's time
+    value = n_job * K / (step_ms / 1e3)
 
     e2e = None
     if not args.no_e2e:
@@ -356,7 +418,7 @@ def run_batch(args):
             t = torch.tensor([dt], dtype=torch.float64, device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t[0])
-        e2e = {"value": ws * ntot * K / dt, "unit": UNIT, "h2d_bytes_per_step": 7 * 8 * ntot / K,
+        e2e = {"value": n_job * K / dt, "unit": UNIT, "h2d_bytes_per_step": 7 * 8 * ntot / K,
                "d2h_bytes_per_step": 8 * len(wls) + 8 * ntot / K,
                "note": "every fit loaded from pinned host memory once, K x (batched step + every fit's chi^2 "
                        "read), every fit's weights read"}
@@ -370,17 +432,22 @@ def run_batch(args):
             v, dt, ns = cpu_baseline("c5", args.cpu_sample, args.cpu_steps)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {ns} particles of fit 0 of the c5 batch, {args.cpu_steps} steps, "
-                             f"{dt:.1f} s single-threaded FP64"}
+                             f"{dt:.1f} s single-threaded FP64",
+                   "host": host_cpu()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+i64", "data": "synthetic",
-            "config": {"workload": "c5_batch96_hernquist_nfw_mixed", "fits": len(wls), "n_particles": ntot,
+            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
+            "config": {"workload": "c5_batch96_hernquist_nfw_mixed", "fits": len(n_all), "n_particles": n_job,
+                       "fits_rank0": len(wls), "n_particles_rank0": ntot,
+                       "timed_window": f"starts at a prior-update step; {prior_steps_in(t_start, K, every)} of the "
+                                       f"{K} timed steps bin the priors (every {every})",
                        "observables_per_fit": wls[0].J, "prior_grid": "50x20 every 25", "dt": wls[0].params["dt"],
                        "precision": "mixed", "launch_shape": {"block": shape[0], "blocks_per_sm": shape[1],
                                                               "segment": shape[2]},
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
-                       "parallelism": f"{ws} independent batch(es) of {len(wls)} fits, one per GPU",
+                       "parallelism": f"the {len(n_all)} fits split over {ws} GPU(s) by particle count, "
+                                      f"one batch per GPU, no data-path collective",
                        "chi2_per_J_end_mean": chi2_per_J},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": K,  # one batched step kernel per step for all fits
@@ -389,6 +456,91 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_sharded(args):
+    """N > 1 GPUs on one single-fit workload: the fit split over the ranks by particles
+    (contiguous ranges), one NCCL all-reduce of the int64 exchange words per step between
+    each rank's pass and the finalize every rank runs on the same sums; bit-identical to
+    the whole fit on one GPU. Strong scaling: the job is the one fit."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_1202_2355_gb300 import binding as B
+    from paper_1202_2355_gb300 import build as BUILD
+    from paper_1202_2355_gb300 import dist as D
+    from paper_1202_2355_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    BUILD.build()
+    K, Wm = args.steps, args.warmup
+    wl = W.make(args.workload, n=args.n)
+    if args.precision:
+        wl.precision = args.precision
+    n = wl.n
+    Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
+    lo, hi = D.shard_range(n, rank, ws)
+    part = D.take_range(wl.model, lo, hi)
+    stream = torch.cuda.Stream()
+    fit = B.fit_from_workload(wl, Y, sig, Vp, sp, stream=stream.cuda_stream)
+    drv = D.ShardDriver(fit, D.nccl_exchange, D.torch_reduce)
+    drv.load(part, n)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    every = wl.prior["update_every"] if wl.prior["mode"] == "mpr" else 1
+
+    def one_step():
+        drv.step(1)
+        flush.fill_(1)
+
+    with torch.cuda.stream(stream):
+        for _ in range(Wm):
+            one_step()
+        t_start = fit.step_count()
+        t_start += align_to_prior_step(fit, t_start, every, one_step)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    # each step bracketed on the shard's stream: pass, exchange and finalize
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(K):
+                ev[k][0].record(stream)
+                drv.step(1)
+                ev[k][1].record(stream)
+                flush.fill_(1)
+        torch.cuda.synchronize()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    chi2 = fit.chi2()
+    t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms = float(t[0])
+    dist.barrier()
+    fit.close()
+    value = n * K / (step_ms / 1e3)
+    roof = roofline(args.workload, wl.precision, hi - lo, step_ms / K, kernel="k_step (shard) + all-reduce")
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f64" if wl.precision == "fp64" else "f32+i64", "data": "synthetic",
+            "config": {"workload": wl.name, "n_particles": n, "observables": wl.J,
+                       "prior_grid": f"{wl.prior['nE']}x{wl.prior['nx']} every {wl.prior['update_every']}",
+                       "dt": wl.params["dt"], "precision": wl.precision,
+                       "timed_window": f"starts at a prior-update step; {prior_steps_in(t_start, K, every)} of the "
+                                       f"{K} timed steps bin the priors (every {every})",
+                       "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                       "parallelism": f"one fit split over {ws} GPUs by particles, one NCCL all-reduce of "
+                                      f"the int64 sums per step", "chi2_per_J_end": chi2 / wl.J},
+            "roofline": roof, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": 2 * K,  # per step: the shard's pass and its finalize
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
     return 0
 
 
@@ -417,10 +569,18 @@ def run_ours(args):
     fit = B.fit_from_workload(wl, Y, sig, Vp, sp, stream=stream.cuda_stream)
     fit.load(wl.model)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    every = wl.prior["update_every"] if wl.prior["mode"] == "mpr" else 1
+
+    def one_step():
+        fit.step(1)
+        flush.fill_(1)
+
     with torch.cuda.stream(stream):
         for _ in range(Wm):
-            fit.step(1)
-            flush.fill_(1)
+            one_step()
+        fit.synchronize()
+        t_start = fit.step_count()
+        t_start += align_to_prior_step(fit, t_start, every, one_step)
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -458,7 +618,8 @@ def run_ours(args):
             v, dt, _ = cpu_baseline(args.workload, args.cpu_sample, args.cpu_steps)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"first {args.cpu_sample} particles of {wl.name}, {args.cpu_steps} steps, "
-                             f"{dt:.1f} s single-threaded FP64"}
+                             f"{dt:.1f} s single-threaded FP64",
+                   "host": host_cpu()}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -467,6 +628,8 @@ def run_ours(args):
             "config": {"workload": wl.name, "n_particles": n, "observables": wl.J,
                        "prior_grid": f"{wl.prior['nE']}x{wl.prior['nx']} every {wl.prior['update_every']}",
                        "dt": wl.params["dt"], "precision": wl.precision,
+                       "timed_window": f"starts at a prior-update step; {prior_steps_in(t_start, K, every)} of the "
+                                       f"{K} timed steps bin the priors (every {every})",
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                        "parallelism": f"{ws} independent fit(s), one per GPU", "chi2_per_J_end": chi2 / wl.J},
             "roofline": roof,
@@ -487,10 +650,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c5")
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--ref-sample", type=int, default=10_000)
@@ -505,6 +668,8 @@ def main():
         return run_reference(args)
     if args.workload == "c5":
         return run_batch(args)
+    if _dist()[0] > 1:
+        return run_sharded(args)
     return run_ours(args)
 
 
