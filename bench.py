@@ -67,29 +67,23 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
 #                 kernel values 21, force of change 23, weight 2, total weight 1, and the
 #                 prior binning of one step in 25 (40 / 25 = 1.6), rounded to 88.
 KERNEL_FIGURES = {
-    # method: 7 x 8 B read and written, cell 2 B = 114 B; design: read x..vz, ln w,
-    # ax..az (80 B), prior cell, cached apertures and cached exp(-nu^2/2) (2 + 2 + 8 B);
-    # write 80 + 2 + 8 B
-    "fp64": {"bytes": 114, "design_bytes": 182, "flops": 151.37, "method_flops": 88},
+    # method: 7 x 8 B read and written, cell 2 B = 114 B; design: read x..vz, ln w and the
+    # force factor (64 B), prior cell, cached apertures and cached exp(-nu^2/2) (2 + 2 + 8 B);
+    # write 64 + 2 + 8 B
+    "fp64": {"bytes": 114, "design_bytes": 150, "flops": 151.37, "method_flops": 88},
     # method: 7 x 4 B read and written, cell 2 B = 58 B; design: read 6 coordinates + w
     # (28 B), prior cell and cached apertures (2 + 2 B); write 28 B + 2 B of apertures
     "mixed": {"bytes": 58, "design_bytes": 62, "flops": None},
 }
-# Mixed-precision workloads in the Hernquist + NFW potential keep the acceleration
-# between steps as FP64 mode does: a_x, a_y, a_z read and written (24 B more).
+# Mixed-precision workloads in the Hernquist + NFW potential keep the force factor of the
+# acceleration between steps as FP64 mode does: 4 B read and 4 B written.
 MIXED_CACHED_ACCEL = {"c3", "c5"}
-ACCEL_BYTES_MIXED = 24
+ACCEL_BYTES_MIXED = 8
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one step launch / N, from an ncu
 # capture of the kernel as it stands, by (workload, precision): (bytes per unit, N of
-# the capture); absent: not captured. Most of a step's writes are still in the
-# 129 MB L2 when the kernel ends (written back during the next launch or the L2
-# flush), so the write count is below the algorithmic one.
-DRAM_PER_UNIT = {
-    ("c2", "fp64"): (121.5, 1_000_000),
-    ("c4", "mixed"): (54.9, 8_000_000),
-    ("c5", "mixed"): (85.2, 52_205_149),
-}
+# the capture); absent: not captured since the kernel last changed.
+DRAM_PER_UNIT = {}
 
 
 class ClockSampler:
@@ -193,7 +187,7 @@ def roofline(workload: str, precision: str, n: int, ms_per_launch: float, kernel
     The headline is the HBM fraction at the method's state traffic: 58 B (FP32) or
     114 B (FP64) per particle-step, the coordinates and the weight read and written
     and the 2-byte prior cell read. design_gbs counts what the kernel streams with its
-    caches (62 B, 86 B where it keeps the acceleration, 182 B in FP64). The FP64 kernel
+    caches (62 B, 70 B where it keeps the force factor, 150 B in FP64). The FP64 kernel
     is bound by the FP64 pipe rather than HBM; its ALU fraction is given beside the
     headline, from the method's own operation count per particle-step."""
     f = dict(KERNEL_FIGURES[precision])
@@ -336,7 +330,9 @@ def run_batch(args):
     # the 96 fits are split over the ranks by particle count (strong scaling: the job is
     # fixed); each rank advances its share as one batch, with no collective on the data path
     from paper_1202_2355_gb300 import dist as D
-    mine = D.split_fits(np.maximum(1, (n_all * scale).astype(np.int64)), ws)[rank]
+    pool = list(range(len(n_all))) if args.fits is None else [int(v) for v in args.fits.split(",")]
+    counts = np.maximum(1, (n_all[pool] * scale).astype(np.int64))
+    mine = [pool[i] for i in D.split_fits(counts, ws)[rank]]
     wls = W.make_batch(n_scale=scale, fits=mine)
     descs = []
     for wl in wls:
@@ -346,10 +342,12 @@ def run_batch(args):
         wl.target = None
     ntot = sum(wl.n for wl in wls)
     stream = torch.cuda.Stream()
-    batch = B.Batch(descs, precision="mixed", stream=stream.cuda_stream)
+    fixed = None if args.shape is None else [int(v) for v in args.shape.split(",")]
+    batch = B.Batch(descs, precision="mixed", stream=stream.cuda_stream,
+                    block=fixed[0] if fixed else 0, blocks_per_sm=fixed[1] if fixed else 0)
     for wl, f in zip(wls, batch.fits):
         f.load(wl.model)
-    shape = batch.autotune(steps=2)
+    shape = tuple(fixed) if fixed else batch.autotune(steps=2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     every = wls[0].prior["update_every"]
 
@@ -379,7 +377,7 @@ def run_batch(args):
     batch.set_timing(False)
     assert nt == K
     chi2_per_J = float(np.mean([f.chi2() / f.J for f in batch.fits]))
-    n_job = int(np.maximum(1, (n_all * scale).astype(np.int64)).sum())
+    n_job = int(counts.sum())
     if ws > 1:
         t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -438,7 +436,8 @@ def run_batch(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
-            "config": {"workload": "c5_batch96_hernquist_nfw_mixed", "fits": len(n_all), "n_particles": n_job,
+            "config": {"workload": "c5_batch96_hernquist_nfw_mixed" if args.fits is None else
+                       f"c5 fits {args.fits}", "fits": len(pool), "n_particles": n_job,
                        "fits_rank0": len(wls), "n_particles_rank0": ntot,
                        "timed_window": f"starts at a prior-update step; {prior_steps_in(t_start, K, every)} of the "
                                        f"{K} timed steps bin the priors (every {every})",
@@ -446,7 +445,7 @@ def run_batch(args):
                        "precision": "mixed", "launch_shape": {"block": shape[0], "blocks_per_sm": shape[1],
                                                               "segment": shape[2]},
                        "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
-                       "parallelism": f"the {len(n_all)} fits split over {ws} GPU(s) by particle count, "
+                       "parallelism": f"the {len(pool)} fits split over {ws} GPU(s) by particle count, "
                                       f"one batch per GPU, no data-path collective",
                        "chi2_per_J_end_mean": chi2_per_J},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -661,6 +660,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="override the particle count (profiling)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None, help="override (profiling)")
+    ap.add_argument("--fits", default=None, help="c5: comma-separated fit indices instead of all 96 (profiling)")
+    ap.add_argument("--shape", default=None, help="c5: block,blocks_per_sm,segment instead of the autotuner "
+                                                  "(profiling; the segment is the library default)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -274,6 +274,7 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.rec_len = 5 + (max_gh + 1);
     for (int g = 0; g < m.n_groups; ++g)  // shell records hold c_j of each a_lm
         if (m.g[g].geometry == M2M_GEOM_SHELLS) m.rec_len = std::max(m.rec_len, m.g[g].n_kinds);
+    m.rec_len = (m.rec_len + 3) / 4 * 4;  // 16-byte records in FP32 (vector loads in the force of change)
     ctx->Y.assign(J, 0.0);
     ctx->sig.assign(J, 1.0);
     if (obs->Y && obs->sigY) {
@@ -652,8 +653,8 @@ static void launch_step_timed(m2m_ctx *c, cudaEvent_t *ev)
 
 static size_t elem_size(const m2m_ctx *c) { return c->precision == M2M_PREC_FP64 ? 8 : 4; }
 
-// x, y, z, vx, vy, vz, w and, where the step keeps it, the acceleration
-static int state_arrays(const m2m_ctx *c) { return c->m.cache_accel ? 10 : 7; }
+// x, y, z, vx, vy, vz, w and, where the step keeps it, the force factor of the acceleration
+static int state_arrays(const m2m_ctx *c) { return c->m.cache_accel ? 8 : 7; }
 
 static m2m_status ensure_capacity(m2m_ctx *ctx, long long n)
 {

@@ -44,7 +44,7 @@ static const int kBatchGraphSteps = 16;
 template <class T, int WPS, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
 static void *batch_fn()
 {
-    return reinterpret_cast<void *>(k_step_batch<T, WPS, kMinBlocks<T>, M0, M1, M2, M3>);
+    return reinterpret_cast<void *>(k_step_batch<T, WPS, kMinBlocksBatch<T>, M0, M1, M2, M3>);
 }
 
 // The specialised kernel when every fit has the same observable shape and it is

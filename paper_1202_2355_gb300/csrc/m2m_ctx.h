@@ -33,7 +33,7 @@ struct m2m_ctx {
     // device buffers
     long long n = 0;
     long long capacity = 0;
-    void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and in FP64 mode ax, ay, az
+    void *st[10] = {nullptr};  // x, y, z, vx, vy, vz, w, and where the step keeps it the force factor
     uint16_t *cell = nullptr;
     uint16_t *ap = nullptr;  // cached apertures (Model::ap_cache)
     double *gx = nullptr;    // cached exp(-nu^2/2) (Model::gx_group, FP64 mode)
@@ -130,7 +130,7 @@ inline m2m::State<T> state(m2m_ctx *c)
     m2m::State<T> s;
     s.x = (T *)c->st[0]; s.y = (T *)c->st[1]; s.z = (T *)c->st[2];
     s.vx = (T *)c->st[3]; s.vy = (T *)c->st[4]; s.vz = (T *)c->st[5]; s.w = (T *)c->st[6];
-    s.ax = (T *)c->st[7]; s.ay = (T *)c->st[8]; s.az = (T *)c->st[9];
+    s.fa = (T *)c->st[7];
     s.cell = c->cell;
     s.ap = c->ap;
     s.gx = sizeof(T) == 8 ? reinterpret_cast<T *>(c->gx) : nullptr;
@@ -138,9 +138,13 @@ inline m2m::State<T> state(m2m_ctx *c)
     return s;
 }
 
-// Resident blocks per SM the step kernels are compiled for (register budget).
+// Resident blocks per SM the step kernels are compiled for (register budget). The
+// batched mixed-precision kernel runs best at 4 blocks of 256 (64 registers; 1.147 ms
+// against 1.176 ms at 5 blocks on the 96-fit workload), the single-fit one at 5.
 template <class T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 5;
+template <class T>
+constexpr int kMinBlocksBatch = sizeof(T) == 8 ? 2 : 4;
 
 // Compile-time shape bits of a group (see m2m::GP), for picking a specialised kernel.
 inline unsigned group_mask(const m2m::GroupDesc &G)

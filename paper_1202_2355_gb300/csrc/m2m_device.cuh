@@ -221,7 +221,7 @@ struct Scalars {
 template <class T>
 struct State {
     T *x, *y, *z, *vx, *vy, *vz, *w;
-    T *ax, *ay, *az;  // FP64 mode: acceleration at the current positions (null in mixed mode)
+    T *fa;            // force factor of the acceleration at the current positions (Model::cache_accel)
     uint16_t *cell;
     uint16_t *ap;     // cached apertures (Model::ap_cache), null without the cache
     T *gx;            // cached exp(-nu^2/2) of Model::gx_group (FP64 mode), else null
@@ -237,10 +237,13 @@ constexpr bool kLogWeights = sizeof(T) == 8;
 
 // The step can keep a(x_t) from the closing half-kick of one step for the opening
 // half-kick of the next (the same function of the same positions, so bit-identical
-// to recomputing it): 3 more state arrays read and written instead of one force
-// evaluation. FP64 mode always does (it is bound by the FP64 pipe, not by HBM);
-// mixed mode does where the force is dear (Model::cache_accel: the Hernquist + NFW
-// potential, whose halo term takes a logarithm and a division).
+// to recomputing it). Every potential here has a = -f (x, y, z) (spherical) or
+// f (x, y, z / q^2) (flattened log halo) with one scalar force factor f, so the factor
+// is kept (one state array read and written) and the components are rebuilt from it
+// with the same multiplications: bit-identical to keeping the three components, in a
+// third of the traffic. FP64 mode always does (it is bound by the FP64 pipe, not by
+// HBM); mixed mode does where the force is dear (Model::cache_accel: the Hernquist +
+// NFW potential, whose halo term takes a logarithm and a division).
 template <class T>
 constexpr bool kCacheAccel = sizeof(T) == 8;
 
@@ -339,33 +342,38 @@ __host__ __device__ __forceinline__ T nfw_mu(T qq)
 {
     if (qq < T(1e-3)) {
         T s = T(-10.0 / 11.0);
-        s = T(9.0 / 10.0) + qq * s;
-        s = T(-8.0 / 9.0) + qq * s;
-        s = T(7.0 / 8.0) + qq * s;
-        s = T(-6.0 / 7.0) + qq * s;
-        s = T(5.0 / 6.0) + qq * s;
-        s = T(-4.0 / 5.0) + qq * s;
-        s = T(3.0 / 4.0) + qq * s;
-        s = T(-2.0 / 3.0) + qq * s;
-        s = T(0.5) + qq * s;
+        s = fma(qq, s, T(9.0 / 10.0));
+        s = fma(qq, s, T(-8.0 / 9.0));
+        s = fma(qq, s, T(7.0 / 8.0));
+        s = fma(qq, s, T(-6.0 / 7.0));
+        s = fma(qq, s, T(5.0 / 6.0));
+        s = fma(qq, s, T(-4.0 / 5.0));
+        s = fma(qq, s, T(3.0 / 4.0));
+        s = fma(qq, s, T(-2.0 / 3.0));
+        s = fma(qq, s, T(0.5));
         return qq * qq * s;
     }
     return d_log1p(qq) - d_div(qq, T(1) + qq);
 }
 
 // FP32: ln(1+q) and mu(q) together without the library log1p. Below q = 1 both come
-// from the series in t = q/(1+q) < 1/2: ln(1+q) = sum_{k>=1} t^k/k (21 terms, relative
-// truncation below 1e-8) and mu = ln(1+q) - t = sum_{k>=2} t^k/k; above, ln(1+q) from the
-// hardware log2 (__logf: a few ulp) and mu = ln(1+q) - t >= 0.19 without cancellation.
+// from the series in s = q/(2+q) <= 1/3: ln(1+q) = 2 atanh(s) = 2 s sum_{k>=0} s^(2k)/(2k+1),
+// and, since 2s - q/(1+q) = s t exactly (t = q/(1+q)),
+//   mu = ln(1+q) - t = s t + 2 s^3 P(s^2),  P(u) = sum_{k>=0} u^k/(2k+3),
+// a sum of positive terms with no cancellation (8 terms of P, truncation below 1e-9
+// relative). Above, ln(1+q) from the hardware log2 (__logf: a few ulp) and
+// mu = ln(1+q) - t >= 0.19 without cancellation.
 __host__ __device__ __forceinline__ void nfw_logs(float q, float &l1, float &mu)
 {
     const float t = d_div(q, 1.f + q);
     if (q < 1.f) {
-        float s = 1.f / 22.f;
+        const float s = d_div(q, 2.f + q), u = s * s;
+        float P = 1.f / 17.f;
 #pragma unroll
-        for (int k = 21; k >= 2; --k) s = fmaf(t, s, 1.f / float(k));
-        mu = t * t * s;
-        l1 = t + mu;
+        for (int k = 6; k >= 0; --k) P = fmaf(u, P, 1.f / float(2 * k + 3));
+        const float s3P2 = 2.f * (s * u) * P;
+        l1 = fmaf(2.f, s, s3P2);
+        mu = fmaf(s, t, s3P2);
     } else {
         l1 = d_log(1.f + q);
         mu = l1 - t;
@@ -376,10 +384,10 @@ template <class T>
 __host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k, T x, T y, T z)
 {
     if (m.pot == 2) {
-        const T D = k.r0sq + x * x + y * y + d_div(z * z, k.q2);
+        const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
         return T(0.5) * k.v0sq * d_log(D);
     }
-    const T r = d_sqrt(x * x + y * y + z * z);
+    const T r = d_sqrt(fma(x, x, fma(y, y, z * z)));
     T phi = -d_div(k.GM, r + k.a);
     if (m.pot == 1) {
         if (!(r > T(0))) return phi + k.hn_phi0;
@@ -395,26 +403,20 @@ __host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k,
     return phi;
 }
 
+// Force factor f of the acceleration at (x, y, z): a = -f (x, y, z) in the spherical
+// potentials (f = g(r)/r with g = G M(<r)/r^2), a = f (x, y, z/q^2) in the flattened log
+// halo (f = -v0^2/D).
 template <class T>
-__host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay,
-                                               T &az)
+__host__ __device__ __forceinline__ T accel_factor(const Model &m, const Cst<T> &k, T x, T y, T z)
 {
     if (m.pot == 2) {
-        const T D = k.r0sq + x * x + y * y + d_div(z * z, k.q2);
-        const T f = -d_div(k.v0sq, D);
-        ax = f * x;
-        ay = f * y;
-        az = d_div(f * z, k.q2);
-        return;
+        const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
+        return -d_div(k.v0sq, D);
     }
-    const T r2 = x * x + y * y + z * z;
-    if (is_zero(r2)) {
-        ax = ay = az = T(0);
-        return;
-    }
+    const T r2 = fma(x, x, fma(y, y, z * z));
+    if (is_zero(r2)) return T(0);
     const T r = d_sqrt(r2);
     const T ra = r + k.a;
-    // -g(r)/r with g = G M(<r) / r^2
     T f = d_div(k.GM, ra * ra * r);
     if (m.pot == 1) {
         T mu;
@@ -426,27 +428,51 @@ __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, 
         }
         f += d_div(k.GMs * mu, r2 * r);
     }
+    return f;
+}
+
+// The acceleration from its force factor (see accel_factor).
+template <class T>
+__host__ __device__ __forceinline__ void accel_from(const Model &m, const Cst<T> &k, T f, T x, T y, T z, T &ax,
+                                                    T &ay, T &az)
+{
+    if (m.pot == 2) {
+        ax = f * x;
+        ay = f * y;
+        az = d_div(f * z, k.q2);
+        return;
+    }
     ax = -f * x;
     ay = -f * y;
     az = -f * z;
 }
 
-// One kick-drift-kick leap-frog step from a known acceleration at the start
-// position; returns the acceleration at the end position in (ax, ay, az).
+template <class T>
+__host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay,
+                                               T &az)
+{
+    accel_from(m, k, accel_factor(m, k, x, y, z), x, y, z, ax, ay, az);
+}
+
+// One kick-drift-kick leap-frog step from the force factor f at the start position;
+// returns the factor at the end position in f.
 template <class T>
 __device__ __forceinline__ void leapfrog_from(const Model &m, const Cst<T> &k, T &x, T &y, T &z, T &vx, T &vy, T &vz,
-                                              T &ax, T &ay, T &az)
+                                              T &f)
 {
-    vx += k.hdt * ax;
-    vy += k.hdt * ay;
-    vz += k.hdt * az;
-    x += k.dt * vx;
-    y += k.dt * vy;
-    z += k.dt * vz;
-    accel(m, k, x, y, z, ax, ay, az);
-    vx += k.hdt * ax;
-    vy += k.hdt * ay;
-    vz += k.hdt * az;
+    T ax, ay, az;
+    accel_from(m, k, f, x, y, z, ax, ay, az);
+    vx = fma(k.hdt, ax, vx);
+    vy = fma(k.hdt, ay, vy);
+    vz = fma(k.hdt, az, vz);
+    x = fma(k.dt, vx, x);
+    y = fma(k.dt, vy, y);
+    z = fma(k.dt, vz, z);
+    f = accel_factor(m, k, x, y, z);
+    accel_from(m, k, f, x, y, z, ax, ay, az);
+    vx = fma(k.hdt, ax, vx);
+    vy = fma(k.hdt, ay, vy);
+    vz = fma(k.hdt, az, vz);
 }
 
 // One kick-drift-kick leap-frog step.
@@ -455,16 +481,16 @@ __device__ __forceinline__ void leapfrog(const Model &m, const Cst<T> &k, T &x, 
 {
     T ax, ay, az;
     accel(m, k, x, y, z, ax, ay, az);
-    vx += k.hdt * ax;
-    vy += k.hdt * ay;
-    vz += k.hdt * az;
-    x += k.dt * vx;
-    y += k.dt * vy;
-    z += k.dt * vz;
+    vx = fma(k.hdt, ax, vx);
+    vy = fma(k.hdt, ay, vy);
+    vz = fma(k.hdt, az, vz);
+    x = fma(k.dt, vx, x);
+    y = fma(k.dt, vy, y);
+    z = fma(k.dt, vz, z);
     accel(m, k, x, y, z, ax, ay, az);
-    vx += k.hdt * ax;
-    vy += k.hdt * ay;
-    vz += k.hdt * az;
+    vx = fma(k.hdt, ax, vx);
+    vy = fma(k.hdt, ay, vy);
+    vz = fma(k.hdt, az, vz);
 }
 
 // ---------------------------------------------------------------- observables
@@ -474,8 +500,8 @@ __device__ __forceinline__ void leapfrog(const Model &m, const Cst<T> &k, T &x, 
 template <class T>
 __device__ __forceinline__ void project(const Cst<T> &k, T y, T z, T vy, T vz, T &Y, T &vlos)
 {
-    Y = y * k.cos_i - z * k.sin_i;
-    vlos = vy * k.sin_i + vz * k.cos_i;
+    Y = fma(y, k.cos_i, -(z * k.sin_i));
+    vlos = fma(vy, k.sin_i, vz * k.cos_i);
 }
 
 // Aperture of sky point (X, Y) in group G, or -1: half-open annuli
@@ -493,7 +519,7 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const double *esq, c
                                         double X, double Y)
 {
     if (!GP<M>::pixels(G)) {
-        const double R2 = X * X + Y * Y;
+        const double R2 = fma(X, X, Y * Y);
         const long long r = __double_as_longlong(R2);
         const double *e = esq + G.edge_off;
         if (r < __double_as_longlong(e[0]) || r >= __double_as_longlong(e[G.n_ap])) return -1;
@@ -526,7 +552,7 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const float *e2s, co
                                         float Y)
 {
     if (!GP<M>::pixels(G)) {
-        const float R2 = X * X + Y * Y;
+        const float R2 = fmaf(X, X, Y * Y);
         if (!(R2 >= G.e0sq_f) || !(R2 < G.ensq_f)) return -1;
         int b = __float2int_rd((__log2f(R2) - G.l0) * G.lscale);
         b = b < 0 ? 0 : (b >= G.lut_n ? G.lut_n - 1 : b);
@@ -597,7 +623,7 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
 #pragma unroll
         for (int n = 1; n < 6; ++n) {
             if (n < nmax) {
-                const T hn1 = T(2) * nu * h - T(2 * n) * hm1;
+                const T hn1 = fma(T(2) * nu, h, -(T(2 * n) * hm1));
                 hm1 = h;
                 h = hn1;
                 if (P::gh(G, n + 1))
@@ -613,21 +639,48 @@ __device__ __forceinline__ void group_kernels(const GroupDesc &G, const Tables<T
 // one record per aperture, r = [V_p, 1/sigma_p, q0, q1, q2, p0 .. p_nmax], and
 // sum_j K_j c_j = q0 + q1 nu + q2 nu^2 + exp(-nu^2/2) sum_n p_n nu^n
 // (groups without Gauss-Hermite kernels use V = 0, 1/sigma = 1, i.e. nu = v_los).
+// The first n values of a record (n <= 12), with 16-byte loads: records start on 16-byte
+// boundaries (Model::rec_len is a multiple of 4).
+__device__ __forceinline__ void load_record(const float *r, float *v, int n)
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        if (4 * q < n) {
+            const float4 a = reinterpret_cast<const float4 *>(r)[q];
+            v[4 * q] = a.x;
+            v[4 * q + 1] = a.y;
+            v[4 * q + 2] = a.z;
+            v[4 * q + 3] = a.w;
+        }
+}
+__device__ __forceinline__ void load_record(const double *r, double *v, int n)
+{
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if (2 * q < n) {
+            const double2 a = reinterpret_cast<const double2 *>(r)[q];
+            v[2 * q] = a.x;
+            v[2 * q + 1] = a.y;
+        }
+}
+
 template <unsigned M, class T>
 __device__ __forceinline__ T group_data(const Model &m, const GroupDesc &G, const Tables<T> &tb, const T *rec, int p,
                                         T vlos, const T *gexp = nullptr)
 {
-    const T *r = rec + (G.ap_off + p) * m.rec_len;
+    const T *rp = rec + (G.ap_off + p) * m.rec_len;
     const int nmax = GP<M>::max_gh(G);
-    if (!GP<M>::v2(G) && !GP<M>::v1(G) && nmax < 0) return r[2];  // surface mass only: a constant
+    if (!GP<M>::v2(G) && !GP<M>::v1(G) && nmax < 0) return rp[2];  // surface mass only: a constant
+    T r[12];
+    load_record(rp, r, 6 + nmax);
     const T nu = (vlos - r[0]) * r[1];
-    T d = r[2] + nu * (r[3] + nu * r[4]);
+    T d = fma(nu, fma(nu, r[4], r[3]), r[2]);
     if (nmax >= 0) {
         T poly = T(0);
 #pragma unroll
         for (int n = 6; n >= 0; --n)
-            if (n <= nmax) poly = poly * nu + r[5 + n];
-        d += (gexp ? *gexp : kexp(tb, T(-0.5) * nu * nu)) * poly;
+            if (n <= nmax) poly = fma(poly, nu, r[5 + n]);
+        d = fma(gexp ? *gexp : kexp(tb, T(-0.5) * nu * nu), poly, d);
     }
     return d;
 }
@@ -926,14 +979,14 @@ template <class T>
 __device__ __forceinline__ int prior_cell(const Model &m, const Cst<T> &k, const double *lcE, T x, T y, T z,
                                           T vx, T vy, T vz)
 {
-    const T E = T(0.5) * (vx * vx + vy * vy + vz * vz) + potential(m, k, x, y, z);
-    const T Lz = x * vy - y * vx;
+    const T E = fma(T(0.5), fma(vx, vx, fma(vy, vy, vz * vz)), potential(m, k, x, y, z));
+    const T Lz = fma(x, vy, -(y * vx));
     T L;
     if (m.signed_lz) {
         L = Lz;
     } else {
-        const T Lx = y * vz - z * vy, Ly = z * vx - x * vz;
-        L = d_sqrt(Lx * Lx + Ly * Ly + Lz * Lz);
+        const T Lx = fma(y, vz, -(z * vy)), Ly = fma(z, vx, -(x * vz));
+        L = d_sqrt(fma(Lx, Lx, fma(Ly, Ly, Lz * Lz)));
     }
     const T Lc = circular_L(m, k, lcE, E);
     T xc = (Lc > T(0)) ? d_div(L, Lc) : T(0);
@@ -996,34 +1049,8 @@ __device__ __forceinline__ void fx2(double v, double scale, long long &hi, long 
     }
 }
 
-// Mixed mode: round(v*scale) as three signed 32-bit limbs, computed with FP32 and
-// int32 operations only. With a = |v*scale| (exact power-of-two scaling),
-// hf = floor(a 2^-32) and lf = a - hf 2^32 are exact in FP32 (a below 2^24 gives
-// hf = 0, lf = a; a above 2^32 has an ulp of at least 2^9, so lf has at most 23
-// significant bits); u = rint(lf) < 2^32. The value is sign * (hf 2^32 + u).
-struct Limbs {
-    int hi, mid, lo;  // value = hi 2^32 + mid 2^16 + lo
-};
-
-__device__ __forceinline__ Limbs split(float v, float scale)
-{
-    const float t = v * scale;
-    const float a = fabsf(t);
-    const float hf = floorf(a * 2.3283064365386963e-10f);
-    const float lf = fmaf(-hf, 4294967296.0f, a);
-    const unsigned u = __float2uint_rn(lf);
-    Limbs r;
-    r.hi = __float2int_rz(hf);
-    r.mid = static_cast<int>(u >> 16);
-    r.lo = static_cast<int>(u & 0xFFFFu);
-    if (t < 0.f) {
-        r.hi = -r.hi;
-        r.mid = -r.mid;
-        r.lo = -r.lo;
-    }
-    return r;
-}
-
+// Mixed mode: round(v*scale) (the scaling by a power of two is exact) in one 64-bit
+// conversion, added to the block sums as three 32-bit limbs (see Acc<float>).
 __device__ __forceinline__ long long limbs_value(long long hi, long long mid, long long lo)
 {
     return hi * 4294967296ll + mid * 65536ll + lo;
@@ -1031,10 +1058,10 @@ __device__ __forceinline__ long long limbs_value(long long hi, long long mid, lo
 
 // Block-shared sums. FP64 mode: the two int64 words of each slot, added with
 // 64-bit shared atomics. Mixed mode: three int32 limbs per slot added with native
-// 32-bit shared atomics; at most kMaxParticlesPerBlock particles per block keep
-// |sum of mid| and |sum of lo| below 2^31 (each term below 2^16 in magnitude), and
-// |sum of hi| < 2^31 follows from the fixed-point range. The block flush
-// recombines the limbs into the int64 word exactly.
+// 32-bit shared atomics; at most kMaxParticlesPerBlock particles per block keep the
+// sums of mid and lo (each term in [0, 2^16)) below 2^31, and |sum of hi| < 2^31
+// follows from the fixed-point range. The block flush recombines the limbs into the
+// int64 word exactly.
 constexpr long long kMaxParticlesPerBlock = 32768;
 
 template <class T>
@@ -1066,14 +1093,18 @@ struct Acc<float> {
     {
         return sizeof(int) * (3 * size_t(m.J + 1 + m.ncell) + size_t(m.ncell)) + 8;
     }
+    // round(v*scale) as L = hi 2^32 + mid 2^16 + lo with mid, lo in [0, 2^16) and hi signed:
+    // the two's-complement fields of one 64-bit conversion. Per block the lo and mid sums
+    // stay below 32768 * 65535 < 2^31, and the hi sum within the fixed-point range.
     __device__ static void add(void *base, const Model &, int slot, float v, float scale)
     {
         if (v == 0.f) return;
-        const Limbs l = split(v, scale);
+        const long long L = __float2ll_rn(v * scale);
         int *h = static_cast<int *>(base) + 3 * slot;
-        if (l.hi) atomicAdd(h, l.hi);
-        atomicAdd(h + 1, l.mid);
-        atomicAdd(h + 2, l.lo);
+        const int hi = static_cast<int>(L >> 32);
+        if (hi) atomicAdd(h, hi);
+        atomicAdd(h + 1, static_cast<int>((L >> 16) & 0xFFFF));
+        atomicAdd(h + 2, static_cast<int>(L & 0xFFFF));
     }
     __device__ static void count(void *base, const Model &m, int c)
     {
@@ -1105,20 +1136,14 @@ struct Total<double> {
     __device__ long long word(int q, double) const { return q == 0 ? hi : lo; }
 };
 
-// Mixed mode: the limbs of every weight summed in registers (each thread handles far
-// fewer than kMaxParticlesPerBlock particles), so the total is the exact integer sum
-// and does not depend on how the particles are spread over threads and blocks.
+// Mixed mode: round(w * scale) of every weight summed in a 64-bit register, so the total
+// is the exact integer sum and does not depend on how the particles are spread over
+// threads and blocks.
 template <>
 struct Total<float> {
-    int hi = 0, mid = 0, lo = 0;
-    __device__ void add(float v, float scale)
-    {
-        const Limbs l = split(v, scale);
-        hi += l.hi;
-        mid += l.mid;
-        lo += l.lo;
-    }
-    __device__ long long word(int, float) const { return limbs_value(hi, mid, lo); }
+    long long s = 0;
+    __device__ void add(float v, float scale) { s += __float2ll_rn(v * scale); }
+    __device__ long long word(int, float) const { return s; }
 };
 
 template <int WPS>
@@ -1158,7 +1183,7 @@ __device__ __forceinline__ T foc_update(const Model &m, const Cst<T> &k, const T
     // term is dropped.
     T dS = iprior > T(0) ? -d_log(w * iprior) : T(0);
     if (m.mode == 0) dS -= T(1);
-    const T h = k.dteps * (k.mu * dS - data);
+    const T h = k.dteps * fma(k.mu, dS, -data);
     T wn;
     if (m.update_rule == 0) wn = w * d_exp(h);
     else wn = w * (T(1) + h);
@@ -1179,7 +1204,7 @@ __device__ __forceinline__ T foc_update_log(const Model &m, const Cst<T> &k, con
     // a prior that reads 0 (below the resolution of the cell sums) drops the entropy term
     T dS = !is_neg_inf(lprior) ? lprior - u : T(0);
     if (m.mode == 0) dS -= T(1);
-    const T h = k.dteps * (k.mu * dS - data);
+    const T h = k.dteps * fma(k.mu, dS, -data);
     T un;
     if (m.update_rule == 0) {
         un = u + h;
@@ -1496,8 +1521,7 @@ __device__ __forceinline__ void global_add(long long *hist, int slot, double v, 
 __device__ __forceinline__ void global_add(long long *hist, int slot, float v, float scale)
 {
     if (v == 0.f) return;
-    const Limbs l = split(v, scale);
-    red_add(hist + slot, limbs_value(l.hi, l.mid, l.lo));
+    red_add(hist + slot, __float2ll_rn(v * scale));
 }
 
 // Per-step flags of one fit, read from its scalars at the start of the step.
@@ -1563,13 +1587,15 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
     const bool cache = m.ap_cache != 0;
     const bool need_ap = cache && f.pending;
     const bool gxc = sizeof(T) == 8 && P.gx != nullptr;  // FP64, aperture cache, a Gauss-Hermite group
-    T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0), ngx = T(0);
+    const bool need_fa = (kCacheAccel<T> || m.cache_accel) && push;
+    T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0), ngx = T(0), nfa = T(0);
     int ncell = 0;
     unsigned nap = kApUncached;
     auto fetch = [&](long long j) {
         nx = P.x[j]; ny = P.y[j]; nz = P.z[j];
         nvx = P.vx[j]; nvy = P.vy[j]; nvz = P.vz[j];
         nw = P.w[j];
+        if (need_fa) nfa = P.fa[j];
         if (need_cell) ncell = P.cell[j];
         if (need_ap) nap = P.ap[j];
         if (need_ap && gxc) ngx = P.gx[j];
@@ -1582,6 +1608,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         const int cell = ncell;
         const unsigned code = nap;
         const T gin = ngx;
+        const T fa_in = nfa;
         const T *gp = gxc ? &gin : static_cast<const T *>(nullptr);
         if (i + stride < i1) fetch(i + stride);
         T w, u;
@@ -1601,14 +1628,14 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             u = w;
         }
         if (kCacheAccel<T> || m.cache_accel) {
-            T ax, ay, az;
+            T fa;
             if (push) {
-                ax = P.ax[i]; ay = P.ay[i]; az = P.az[i];
-                leapfrog_from(m, k, x, y, z, vx, vy, vz, ax, ay, az);
+                fa = fa_in;
+                leapfrog_from(m, k, x, y, z, vx, vy, vz, fa);
             } else {
-                accel(m, k, x, y, z, ax, ay, az);
+                fa = accel_factor(m, k, x, y, z);
             }
-            P.ax[i] = ax; P.ay[i] = ay; P.az[i] = az;
+            P.fa[i] = fa;
         } else {
             if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
         }
