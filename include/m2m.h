@@ -56,7 +56,9 @@ typedef enum {
 enum {
     M2M_POT_HERNQUIST = 0,     /* phi = -G M/(r+a)                                  (eq. her) */
     M2M_POT_HERNQUIST_NFW = 1, /* Hernquist + NFW halo phi_h = -G Ms ln(1+r/rs)/r   */
-    M2M_POT_LOG = 2            /* phi = v0^2/2 ln(r0^2 + R^2 + z^2/q^2)             (eq. log_halo) */
+    M2M_POT_LOG = 2,           /* phi = v0^2/2 ln(r0^2 + R^2 + z^2/q^2)             (eq. log_halo) */
+    M2M_POT_SCF = 3            /* phi = Upsilon phi_star + the log halo (Sec. 6): phi_star from the
+                                  particles themselves, see m2m_potential */
 };
 
 /* Aperture geometries: on the sky, or the 3-D radial grid of the density expansion. */
@@ -99,12 +101,35 @@ enum { M2M_DEPOSIT_AUTO = 0, M2M_DEPOSIT_SHARED = 1, M2M_DEPOSIT_GLOBAL = 2 };
 #define M2M_MAX_GROUPS 4
 #define M2M_MAX_KINDS 16
 
-/* Fixed potential. Unused fields are ignored. */
+/* The potential. Unused fields are ignored.
+ *
+ * M2M_POT_SCF (Sec. 6): the particles move in phi = Upsilon phi_star + phi_D, phi_D the
+ * flattened logarithmic halo (v0, r0, q; eq. log_halo) and phi_star the potential of the
+ * particles' own light, estimated by a spherical-harmonic expansion with a constant
+ * mass-to-light ratio Upsilon. The expansion lives on the grid radii scf_r[0..scf_n) with
+ * real harmonics Y_lm (as M2M_OBS_ALM) for l <= scf_lmax: each particle's weight (its
+ * luminosity) goes to its grid points with the cloud-in-cell weights of eq. alm, except
+ * that r < r_0 goes wholly to r_0 and r >= r_{n-1} wholly to r_{n-1}, so the grid carries
+ * thin shells of angular density sum_lm a_lm,k Y_lm, a_lm,k = sum_i w_i gamma_k Y_lm(theta_i,
+ * phi_i), and
+ *   phi_star(x) = -4 pi G sum_k sum_lm a_lm,k Y_lm(theta, phi) f_l(r, r_k) / (2l + 1),
+ *   f_l = r^l / r_k^(l+1) inside the shell (r < r_k), r_k^l / r^(l+1) outside.
+ * The expansion is rebuilt from the particles at the load and on the prior schedule (steps
+ * 1, 1 + P, ..., after that step's binning) and held fixed in between. With eps_ups > 0 the
+ * mass-to-light ratio is determined during the run (Sec. 6): at the same updates
+ * d ln Upsilon/dt = -eps_ups sum_j Delta_j/sigma_j D_j over the P steps to the next update,
+ * D_j = d y_j/d ln Upsilon when the velocities scale as Upsilon^(1/2) (the chi^2 gradient).
+ * Not available in batches or checkpoints. */
 typedef struct {
     int32_t kind;
     double G, M, a;        /* Hernquist mass and scale length */
     double Ms, rs;         /* NFW characteristic mass and scale radius */
     double v0, r0, q;      /* logarithmic halo: velocity scale, core radius, flattening */
+    int32_t scf_n;         /* M2M_POT_SCF: number of grid radii, 1..64 */
+    int32_t scf_lmax;      /* M2M_POT_SCF: highest harmonic degree, 0..6 */
+    const double *scf_r;   /* M2M_POT_SCF, host: scf_n strictly increasing grid radii > 0 (copied) */
+    double ups;            /* M2M_POT_SCF: initial mass-to-light ratio Upsilon > 0 */
+    double eps_ups;        /* M2M_POT_SCF: rate of the mass-to-light update, >= 0 (0: Upsilon fixed) */
 } m2m_potential;
 
 /* One group of apertures sharing a geometry; each group carries n_kinds
@@ -231,6 +256,12 @@ m2m_status m2m_get_priors(m2m_ctx *ctx, double *grid_mean, int64_t *counts, int3
 /* Prior smoothing on: the raw cell means of the last update (nE*nx, may be NULL) and the
  * smoothing weight used (may be NULL). M2M_ERR_STATE when smoothing is off. */
 m2m_status m2m_get_prior_smoothing(m2m_ctx *ctx, double *raw_means, double *lambda);
+
+/* Self-consistent potential (M2M_POT_SCF): the current mass-to-light ratio (may be NULL) and
+ * the coefficients a_lm,k of the last expansion (scf_n * (scf_lmax+1)^2 values, grid point
+ * major, index l (l+1) + m within a point; may be NULL), the luminosity of the weights as
+ * renormalised. M2M_ERR_STATE for other potentials. */
+m2m_status m2m_get_scf(m2m_ctx *ctx, double *ups, double *coeffs, int32_t ncoeffs);
 
 /* Number of steps taken since the last load. */
 m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t);

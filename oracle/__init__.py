@@ -18,7 +18,7 @@ _lib = None
 
 MAX_GROUPS = 4
 MAX_KINDS = 16
-POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
+POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2, "scf": 3}
 GEOM = {"annuli": 0, "pixels": 1, "shells": 2}
 MODE = {"gwr": 0, "mpr": 1}
 ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
@@ -54,7 +54,9 @@ def build(force: bool = False) -> str:
 class Potential(C.Structure):
     _fields_ = [("kind", C.c_int), ("G", C.c_double), ("M", C.c_double), ("a", C.c_double),
                 ("Ms", C.c_double), ("rs", C.c_double), ("v0", C.c_double), ("r0", C.c_double),
-                ("q", C.c_double)]
+                ("q", C.c_double), ("scf_n", C.c_int), ("scf_lmax", C.c_int),
+                ("scf_r", C.POINTER(C.c_double)), ("scf_a", C.POINTER(C.c_double)),
+                ("scf_ups", C.POINTER(C.c_double))]
 
 
 class Group(C.Structure):
@@ -78,7 +80,7 @@ class Prior(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("eps", C.c_double), ("mu", C.c_double),
                 ("alpha", C.c_double), ("renormalize", C.c_int), ("update_rule", C.c_int),
-                ("n_relax", C.c_long)]
+                ("n_relax", C.c_long), ("eps_ups", C.c_double)]
 
 
 _DP = C.POINTER(C.c_double)
@@ -132,6 +134,10 @@ def lib():
         L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
         L.or_smooth_grid.restype = C.c_int
         L.or_smooth_gcv.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP]
+        L.or_scf_coeffs.argtypes = [C.POINTER(Potential), C.POINTER(Particles), _DP]
+        L.or_scf_phi.argtypes = [C.POINTER(Potential), C.c_double, C.c_double, C.c_double, _DP]
+        L.or_scf_phi.restype = C.c_double
+        L.or_observe_dlnups.argtypes = [C.POINTER(Obs), C.POINTER(Particles), _DP]
         L.or_smooth_gcv.restype = C.c_int
         L.or_ylm.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double]
         L.or_ylm.restype = C.c_double
@@ -162,9 +168,45 @@ def _dp(a: np.ndarray):
 # ---------------------------------------------------------------------------
 
 def potential(d: dict) -> Potential:
-    return Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0),
-                     d.get("Ms", 0.0), d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0),
-                     d.get("q", 1.0))
+    """The C descriptor of a potential dict. The self-consistent kind ("scf") carries its
+    grid radii scf_r, scf_lmax and the initial ups (mass-to-light ratio); its coefficient
+    array and Upsilon are owned by the returned object (attributes a and ups)."""
+    P = Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0),
+                  d.get("Ms", 0.0), d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0),
+                  d.get("q", 1.0))
+    if d["kind"] == "scf":
+        r = np.ascontiguousarray(d["scf_r"], np.float64)
+        L = int(d["scf_lmax"])
+        P._keep = (r, np.zeros(len(r) * (L + 1) ** 2), np.array([float(d.get("ups", 1.0))]))
+        P.scf_n, P.scf_lmax = len(r), L
+        P.scf_r, P.scf_a, P.scf_ups = _dp(P._keep[0]), _dp(P._keep[1]), _dp(P._keep[2])
+    return P
+
+
+def scf_coeffs(pot: dict, particles: dict) -> np.ndarray:
+    """a_lm,k of the particles' weights on the grid of a self-consistent potential
+    (or_scf_coeffs), shape (n, (lmax+1)^2)."""
+    P = potential(pot)
+    a = np.zeros((P.scf_n, (P.scf_lmax + 1) ** 2))
+    lib().or_scf_coeffs(C.byref(P), C.byref(ParticleSet(particles).s), _dp(a))
+    return a
+
+
+def scf_field(pot: dict, a: np.ndarray, x, y, z):
+    """(phi_star, grad phi_star) at a point from coefficients a (or_scf_phi, without Upsilon)."""
+    P = potential(pot)
+    a = np.ascontiguousarray(a, np.float64)
+    P.scf_a = _dp(a)
+    g = np.zeros(3)
+    phi = lib().or_scf_phi(C.byref(P), x, y, z, _dp(g))
+    return phi, g
+
+
+def observe_dlnups(obs, ps) -> np.ndarray:
+    """D_j = d y_j / d ln Upsilon with velocities scaling as Upsilon^(1/2) (or_observe_dlnups)."""
+    D = np.zeros(obs.J)
+    lib().or_observe_dlnups(C.byref(obs.o), C.byref(ps.s), _dp(D))
+    return D
 
 
 class ObsSet:
@@ -207,7 +249,7 @@ def prior(d: dict) -> Prior:
 
 def params(d: dict) -> Params:
     return Params(d["dt"], d["eps"], d["mu"], d["alpha"], d["renormalize"], RULE[d["update_rule"]],
-                  d["n_relax"])
+                  d["n_relax"], d.get("eps_ups", 0.0))
 
 
 class ParticleSet:
@@ -310,7 +352,8 @@ class Run:
         self.Y = np.ascontiguousarray(Y, np.float64)
         self.sig = np.ascontiguousarray(sig, np.float64)
         self.G = prior(pri)
-        self.par = params(par)
+        # the rate of the mass-to-light update travels with the self-consistent potential
+        self.par = params(dict(par, eps_ups=pot.get("eps_ups", 0.0)))
         self.ps = ParticleSet(particles)
         n = self.ps.s.n
         J = obs.J
@@ -346,6 +389,16 @@ class Run:
     @property
     def W0(self) -> float:
         return self.st.W0
+
+    @property
+    def ups(self) -> float:
+        """Mass-to-light ratio of a self-consistent potential."""
+        return float(self.P._keep[2][0])
+
+    @property
+    def scf_a(self) -> np.ndarray:
+        """Current expansion coefficients of a self-consistent potential, (n, (lmax+1)^2)."""
+        return self.P._keep[1].reshape(self.P.scf_n, -1)
 
     @property
     def lam(self) -> float:

@@ -55,8 +55,27 @@ static double nfw_mu(double q)
     return log1p(q) - q / (1.0 + q);
 }
 
+static double log_halo_phi(const or_potential *p, double x, double y, double z)
+{
+    double D = p->r0 * p->r0 + x * x + y * y + z * z / (p->q * p->q);
+    return 0.5 * p->v0 * p->v0 * log(D);
+}
+
+static void log_halo_accel(const or_potential *p, double x, double y, double z, double *ax, double *ay,
+                           double *az)
+{
+    double q2 = p->q * p->q;
+    double D = p->r0 * p->r0 + x * x + y * y + z * z / q2;
+    double v2 = p->v0 * p->v0;
+    *ax = -v2 * x / D;
+    *ay = -v2 * y / D;
+    *az = -v2 * z / (q2 * D);
+}
+
 double or_phi(const or_potential *p, double x, double y, double z)
 {
+    if (p->kind == OR_POT_SCF)
+        return *p->scf_ups * or_scf_phi(p, x, y, z, NULL) + log_halo_phi(p, x, y, z);
     if (p->kind == OR_POT_LOG) {
         double D = p->r0 * p->r0 + x * x + y * y + z * z / (p->q * p->q);
         return 0.5 * p->v0 * p->v0 * log(D);
@@ -75,6 +94,15 @@ double or_phi(const or_potential *p, double x, double y, double z)
 void or_accel(const or_potential *p, double x, double y, double z,
               double *ax, double *ay, double *az)
 {
+    if (p->kind == OR_POT_SCF) {
+        double g[3];
+        or_scf_phi(p, x, y, z, g);
+        log_halo_accel(p, x, y, z, ax, ay, az);
+        *ax -= *p->scf_ups * g[0];
+        *ay -= *p->scf_ups * g[1];
+        *az -= *p->scf_ups * g[2];
+        return;
+    }
     if (p->kind == OR_POT_LOG) {
         double q2 = p->q * p->q;
         double D = p->r0 * p->r0 + x * x + y * y + z * z / q2;
@@ -335,9 +363,170 @@ static double circ_energy(const or_potential *p, double R)
  * bisection on E_c(R) = E. Returns 0 when no circular orbit has energy E
  * (E at or below the potential minimum, or E >= 0 in a potential that
  * vanishes at infinity). */
+/* ------------------------------------------------------------------ */
+/* Self-consistent stellar potential (Sec. 6)                          */
+/* ------------------------------------------------------------------ */
+
+/* Associated Legendre function without the Condon-Shortley phase, P_m^m = (2m-1)!!
+ * (1-x^2)^(m/2); 0 outside 0 <= m <= l. */
+static double plm(int l, int m, double x)
+{
+    if (l < 0 || m < 0 || m > l) return 0.0;
+    double s = sqrt(fmax(0.0, 1.0 - x * x));
+    double pmm = 1.0;
+    for (int i = 1; i <= m; ++i) pmm *= (2.0 * i - 1.0) * s;
+    if (l == m) return pmm;
+    double p0 = pmm, p1 = x * (2.0 * m + 1.0) * pmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        double p2 = (x * (2.0 * ll - 1.0) * p1 - (ll + m - 1.0) * p0) / (ll - m);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+/* Factor of Y_lm: N_lm, times sqrt2 for m != 0. */
+static double ylm_factor(int l, int m)
+{
+    int am = m < 0 ? -m : m;
+    double ratio = 1.0;
+    for (int i = l - am + 1; i <= l + am; ++i) ratio /= i;
+    double N = sqrt((2.0 * l + 1.0) / (4.0 * OR_PI) * ratio);
+    return m == 0 ? N : sqrt(2.0) * N;
+}
+
+void or_scf_coeffs(const or_potential *p, const or_particles *s, double *a)
+{
+    int n = p->scf_n, nlm = (p->scf_lmax + 1) * (p->scf_lmax + 1);
+    for (int q = 0; q < n * nlm; ++q) a[q] = 0.0;
+    for (long i = 0; i < s->n; ++i) {
+        double x = s->x[i], y = s->y[i], z = s->z[i];
+        double r = sqrt(x * x + y * y + z * z);
+        int k0;
+        double g0, g1;
+        if (r < p->scf_r[0]) {
+            k0 = 0; g0 = 1.0; g1 = 0.0;
+        } else if (r >= p->scf_r[n - 1]) {
+            k0 = n - 1; g0 = 1.0; g1 = 0.0;
+        } else {
+            k0 = 0;
+            while (!(r < p->scf_r[k0 + 1])) ++k0;
+            double d = p->scf_r[k0 + 1] - p->scf_r[k0];
+            g0 = (p->scf_r[k0 + 1] - r) / d;
+            g1 = (r - p->scf_r[k0]) / d;
+        }
+        double ct = r > 0.0 ? z / r : 1.0;
+        double ph = atan2(y, x);
+        for (int l = 0; l <= p->scf_lmax; ++l)
+            for (int m = -l; m <= l; ++m) {
+                double Y = or_ylm(l, m, ct, ph);
+                int idx = l * (l + 1) + m;
+                a[k0 * nlm + idx] += s->w[i] * g0 * Y;
+                if (g1 != 0.0) a[(k0 + 1) * nlm + idx] += s->w[i] * g1 * Y;
+            }
+    }
+}
+
+double or_scf_phi(const or_potential *p, double x, double y, double z, double *grad)
+{
+    int n = p->scf_n, L = p->scf_lmax, nlm = (L + 1) * (L + 1);
+    double r = sqrt(x * x + y * y + z * z);
+    double R = sqrt(x * x + y * y);
+    double ct = r > 0.0 ? z / r : 1.0, st = r > 0.0 ? R / r : 0.0;
+    double ph = atan2(y, x), cp = R > 0.0 ? x / R : 1.0, sp = R > 0.0 ? y / R : 0.0;
+    double phi = 0.0, gr = 0.0, gt = 0.0, gp = 0.0;  /* dphi/dr, (1/r) dphi/dtheta, (1/(r sin)) dphi/dphi */
+    for (int k = 0; k < n; ++k) {
+        double rk = p->scf_r[k];
+        for (int l = 0; l <= L; ++l) {
+            /* radial function of a thin shell and its derivative */
+            double f, df;
+            if (r < rk) {
+                f = pow(r, l) / pow(rk, l + 1);
+                df = l > 0 ? l * pow(r, l - 1) / pow(rk, l + 1) : 0.0;
+            } else {
+                f = pow(rk, l) / pow(r, l + 1);
+                df = -(l + 1) * pow(rk, l) / pow(r, l + 2);
+            }
+            double C = -4.0 * OR_PI * p->G / (2.0 * l + 1.0);
+            for (int m = -l; m <= l; ++m) {
+                double coef = C * p->scf_a[k * nlm + l * (l + 1) + m];
+                if (coef == 0.0) continue;
+                int am = m < 0 ? -m : m;
+                double N = ylm_factor(l, m);
+                double T = m > 0 ? cos(am * ph) : (m < 0 ? sin(am * ph) : 1.0);
+                double dT = m > 0 ? -am * sin(am * ph) : (m < 0 ? am * cos(am * ph) : 0.0);
+                double P = plm(l, am, ct);
+                phi += coef * N * P * T * f;
+                if (!grad || r == 0.0) continue;
+                /* dP_l^m(cos t)/dt = ((l+m)(l-m+1) P_l^(m-1) - P_l^(m+1)) / 2, and -P_l^1 for m = 0 */
+                double dP = am == 0 ? -plm(l, 1, ct)
+                                    : 0.5 * ((l + am) * (l - am + 1.0) * plm(l, am - 1, ct) - plm(l, am + 1, ct));
+                /* P_l^m / sin t = (P_(l-1)^(m+1) + (l+m-1)(l+m) P_(l-1)^(m-1)) / (2m), m >= 1 */
+                double Ps = am == 0 ? 0.0
+                                    : (plm(l - 1, am + 1, ct) + (l + am - 1.0) * (l + am) * plm(l - 1, am - 1, ct)) /
+                                          (2.0 * am);
+                gr += coef * N * P * T * df;
+                gt += coef * N * dP * T * f / r;
+                gp += coef * N * Ps * dT * f / r;
+            }
+        }
+    }
+    if (grad) {
+        if (r == 0.0) {
+            grad[0] = grad[1] = grad[2] = 0.0;
+        } else {
+            /* e_r = (st cp, st sp, ct), e_theta = (ct cp, ct sp, -st), e_phi = (-sp, cp, 0) */
+            grad[0] = gr * st * cp + gt * ct * cp - gp * sp;
+            grad[1] = gr * st * sp + gt * ct * sp + gp * cp;
+            grad[2] = gr * ct - gt * st;
+        }
+    }
+    (void)ph;
+    return phi;
+}
+
+/* dK/dv_los of one kernel at line-of-sight velocity v in aperture p of group G (0 for the
+ * surface mass and the a_lm). The Gauss-Hermite kernel is c_n H_n(nu) e^(-nu^2/2) with
+ * c_n = 2 sqrt(pi) (2^(n+1) pi n!)^(-1/2) and nu = (v - V_p)/sigma_p, and
+ * d/dnu [H_n e^(-nu^2/2)] = (2n H_(n-1) - nu H_n) e^(-nu^2/2). */
+static double kernel_dv(const or_group *G, int kind, int p, double v)
+{
+    if (kind == OR_V2) return 2.0 * v;
+    if (kind >= OR_GH0 && kind <= OR_GH0 + 6) {
+        int nn = kind - OR_GH0;
+        double nfact = 1.0;
+        for (int k = 2; k <= nn; ++k) nfact *= k;
+        double c = 2.0 * sqrt(OR_PI) / sqrt(pow(2.0, nn + 1) * OR_PI * nfact);
+        double nu = (v - G->Vp[p]) / G->sp[p];
+        double Hn = or_hermite(nn, nu), Hm = nn > 0 ? or_hermite(nn - 1, nu) : 0.0;
+        return c * (2.0 * nn * Hm - nu * Hn) * exp(-0.5 * nu * nu) / G->sp[p];
+    }
+    return 0.0;
+}
+
+void or_observe_dlnups(const or_obs *o, const or_particles *s, double *D)
+{
+    int J = or_num_obs(o);
+    for (int j = 0; j < J; ++j) D[j] = 0.0;
+    for (long i = 0; i < s->n; ++i) {
+        double X, Y, v;
+        project(o->incl_deg, s->x[i], s->y[i], s->z[i], s->vy[i], s->vz[i], &X, &Y, &v);
+        int off = 0;
+        for (int g = 0; g < o->n_groups; ++g) {
+            const or_group *G = &o->g[g];
+            double area;
+            int p = G->geometry == OR_SHELLS ? -1 : aperture(G, X, Y, &area);
+            if (p >= 0)
+                for (int q = 0; q < G->n_kinds; ++q)
+                    D[off + q * G->n_ap + p] += 0.5 * s->w[i] * v * kernel_dv(G, G->kinds[q], p, v);
+            off += G->n_kinds * G->n_ap;
+        }
+    }
+}
+
 double or_circular_L(const or_potential *p, double E)
 {
-    if (p->kind != OR_POT_LOG && E >= 0.0) return 0.0;
+    if (p->kind != OR_POT_LOG && p->kind != OR_POT_SCF && E >= 0.0) return 0.0;
     if (E <= circ_energy(p, 0.0)) return 0.0;
     double hi = 1.0;
     while (circ_energy(p, hi) <= E && hi < 1e15) hi *= 2.0;
@@ -459,6 +648,16 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
         if (!gsum) return OR_EARG;
     }
     int status = OR_OK;
+    double *D = NULL;
+    if (p->kind == OR_POT_SCF) {
+        D = (double *)malloc(sizeof(double) * (size_t)(J > 0 ? J : 1));
+        if (!D) {
+            free(gsum);
+            return OR_EARG;
+        }
+        /* the expansion of the initial particles moves them in the first step */
+        if (st->t == 0) or_scf_coeffs(p, s, p->scf_a);
+    }
     for (long step = 0; step < nsteps; ++step) {
         long t = st->t + 1;
         /* 1. push */
@@ -496,6 +695,20 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
             }
             for (long i = 0; i < s->n; ++i) st->what[i] = st->grid_mean[st->cell[i]];
         }
+        /* 5b. self-consistent potential (Sec. 6): on the same schedule as the priors, the
+         * mass-to-light ratio follows the chi^2 gradient (velocities scaling as
+         * Upsilon^(1/2)), d ln Upsilon/dt = -eps_ups sum_j Delta_j/sigma_j D_j, over the
+         * update_every steps to the next update; then the expansion is rebuilt from the
+         * particles as they are now. Both act from the next step on. */
+        if (p->kind == OR_POT_SCF && (t - 1) % g->update_every == 0) {
+            if (par->eps_ups > 0.0) {
+                or_observe_dlnups(o, s, D);
+                double G = 0.0;
+                for (int j = 0; j < J; ++j) G += st->delta[j] / sig[j] * D[j];
+                *p->scf_ups *= exp(-par->eps_ups * g->update_every * par->dt * G);
+            }
+            or_scf_coeffs(p, s, p->scf_a);
+        }
         /* 6. force of change */
         if (t > par->n_relax) {
             for (long i = 0; i < s->n; ++i) {
@@ -522,6 +735,7 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
         if (status != OR_OK) break;
     }
     free(gsum);
+    free(D);
     return status;
 }
 

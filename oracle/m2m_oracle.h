@@ -22,7 +22,9 @@ extern "C" {
 #define OR_MAX_GROUPS 4
 #define OR_MAX_KINDS 16
 
-enum { OR_POT_HERNQUIST = 0, OR_POT_HERNQUIST_NFW = 1, OR_POT_LOG = 2 };
+/* OR_POT_SCF: phi = Upsilon phi_star + phi_D (Sec. 6): phi_star the multipole expansion of the
+ * particles' own luminosity (their weights) on a radial grid, phi_D the flattened log halo */
+enum { OR_POT_HERNQUIST = 0, OR_POT_HERNQUIST_NFW = 1, OR_POT_LOG = 2, OR_POT_SCF = 3 };
 /* apertures: annuli or pixels on the sky; or the 3-D radial grid of the spherical-harmonic
  * density coefficients (eq. alm), with cloud-in-cell weights between grid radii */
 enum { OR_ANNULI = 0, OR_PIXELS = 1, OR_SHELLS = 2 };
@@ -41,6 +43,15 @@ typedef struct {
     double G, M, a;     /* Hernquist: phi = -G M/(r+a) (eq. her) */
     double Ms, rs;      /* NFW: phi = -G Ms ln(1+r/rs)/r */
     double v0, r0, q;   /* flattened log halo (eq. log_halo) */
+    /* OR_POT_SCF: the expansion of the stellar potential on scf_n grid radii scf_r (increasing,
+     * > 0) with harmonics l <= scf_lmax; scf_a (scf_n (scf_lmax+1)^2 values, caller-owned,
+     * rewritten by or_run at every update) holds a_lm,k of the luminosity weights (see
+     * or_scf_coeffs); *scf_ups is the mass-to-light ratio Upsilon (caller-owned, updated by
+     * or_run when eps_ups > 0). */
+    int scf_n, scf_lmax;
+    const double *scf_r;
+    double *scf_a;
+    double *scf_ups;
 } or_potential;
 
 typedef struct {
@@ -77,6 +88,7 @@ typedef struct {
     int renormalize;
     int update_rule;    /* OR_UPDATE_EXP or OR_UPDATE_EULER */
     long n_relax;
+    double eps_ups;     /* OR_POT_SCF: rate of the mass-to-light update (0: Upsilon fixed) */
 } or_params;
 
 typedef struct {
@@ -121,6 +133,26 @@ int or_kernel_row(const or_obs *o, double x, double y, double z,
 void or_kernel_matrix(const or_obs *o, const or_particles *s, double *K);
 void or_observe(const or_obs *o, const or_particles *s, double *y);
 double or_circular_L(const or_potential *p, double E);
+
+/* ---- Self-consistent stellar potential (Sec. 6) ----
+ *
+ * The stellar mass is Upsilon times the luminosity the weights carry. Its potential is
+ * the multipole expansion on the grid radii r_0 < ... < r_{n-1}: every particle's
+ * luminosity is shared between its grid points by the cloud-in-cell weights gamma_k of
+ * eq. alm, except that r < r_0 goes wholly to point 0 and r >= r_{n-1} wholly to point
+ * n-1 (all the mass counts in a potential), giving thin shells of angular density
+ * sum_lm a_lm,k Y_lm with a_lm,k = sum_i w_i gamma_k(r_i) Y_lm(theta_i, phi_i). A shell of
+ * radius r_k contributes -4 pi G a_lm,k Y_lm / (2l + 1) times r^l / r_k^(l+1) inside it and
+ * r_k^l / r^(l+1) outside, so
+ *   phi_star(x) = -4 pi G sum_k sum_lm a_lm,k Y_lm(theta, phi) f_l(r, r_k) / (2l + 1).
+ * Index of (l, m): l (l + 1) + m. */
+void or_scf_coeffs(const or_potential *p, const or_particles *s, double *a);
+/* phi_star (without Upsilon) and its gradient at (x, y, z); grad may be NULL. */
+double or_scf_phi(const or_potential *p, double x, double y, double z, double *grad);
+/* Derivative of the raw observables with respect to ln Upsilon when the velocities scale
+ * as Upsilon^(1/2) at fixed positions: D_j = 1/2 sum_i w_i v_los,i dK_j/dv_los (0 for the
+ * surface mass and the a_lm). */
+void or_observe_dlnups(const or_obs *o, const or_particles *s, double *D);
 int or_cell(const or_potential *p, const or_prior *g, double x, double y, double z,
             double vx, double vy, double vz, double *E_out, double *xc_out);
 double or_force(const or_obs *o, const or_params *par, int mode, double w_i, double what_i,

@@ -17,7 +17,7 @@ _lib = None
 
 MAX_GROUPS = 4
 MAX_KINDS = 16
-POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2}
+POT = {"hernquist": 0, "hernquist_nfw": 1, "log": 2, "scf": 3}
 GEOM = {"annuli": 0, "pixels": 1, "shells": 2}
 MODE = {"gwr": 0, "mpr": 1}
 ESPACING = {"logneg": 0, "exp": 1, "linear": 2}
@@ -52,7 +52,8 @@ _DP = C.POINTER(C.c_double)
 class Potential(C.Structure):
     _fields_ = [("kind", C.c_int32), ("G", C.c_double), ("M", C.c_double), ("a", C.c_double),
                 ("Ms", C.c_double), ("rs", C.c_double), ("v0", C.c_double), ("r0", C.c_double),
-                ("q", C.c_double)]
+                ("q", C.c_double), ("scf_n", C.c_int32), ("scf_lmax", C.c_int32), ("scf_r", _DP),
+                ("ups", C.c_double), ("eps_ups", C.c_double)]
 
 
 class ObsGroup(C.Structure):
@@ -137,6 +138,8 @@ def lib():
         L.m2m_step_begin.argtypes = [vp]
         L.m2m_step_end.argtypes = [vp]
         L.m2m_shard_weights_begin.argtypes = [vp]
+        L.m2m_get_scf.argtypes = [vp, _DP, _DP, C.c_int32]
+        L.m2m_get_scf.restype = C.c_int
         for name in ("m2m_diag_kinematics", "m2m_diag_grid", "m2m_kin_moments", "m2m_delta_kin",
                      "m2m_delta_grid", "m2m_weight_rms", "m2m_shard_bounds", "m2m_shard_set",
                      "m2m_shard_exchange", "m2m_step_begin", "m2m_step_end", "m2m_shard_weights_begin"):
@@ -165,8 +168,15 @@ def _check(status: int, ctx=None):
 
 
 def potential(d: dict) -> Potential:
-    return Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0), d.get("Ms", 0.0),
-                     d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0), d.get("q", 1.0))
+    """The C descriptor of a potential dict; the self-consistent kind ("scf") takes scf_r (grid
+    radii), scf_lmax, ups (initial mass-to-light ratio) and eps_ups, and the log-halo fields."""
+    P = Potential(POT[d["kind"]], d.get("G", 1.0), d.get("M", 1.0), d.get("a", 1.0), d.get("Ms", 0.0),
+                  d.get("rs", 1.0), d.get("v0", 0.0), d.get("r0", 1.0), d.get("q", 1.0))
+    if d["kind"] == "scf":
+        P._r = np.ascontiguousarray(d["scf_r"], np.float64)
+        P.scf_n, P.scf_lmax, P.scf_r = len(P._r), int(d["scf_lmax"]), _dp(P._r)
+        P.ups, P.eps_ups = float(d.get("ups", 1.0)), float(d.get("eps_ups", 0.0))
+    return P
 
 
 class ObsDesc:
@@ -321,6 +331,7 @@ class Fit:
             self.h = handle
             return
         P = potential(potential_desc)
+        self._pot = P
         G = prior_grid(prior)
         opt = Options(PREC[precision], params["dt"], params["renormalize"], RULE[params["update_rule"]],
                       params["n_relax"], stream, block, blocks_per_sm, DEPOSIT[deposit])
@@ -449,6 +460,14 @@ class Fit:
 
     def shard_weights_begin(self):
         self._ck(lib().m2m_shard_weights_begin(self.h))
+
+    def scf(self):
+        """(Upsilon, a_lm,k of the last expansion (n, (lmax+1)^2)) of a self-consistent potential."""
+        P = self._pot
+        a = np.zeros((P.scf_n, (P.scf_lmax + 1) ** 2))
+        u = C.c_double()
+        self._ck(lib().m2m_get_scf(self.h, C.byref(u), _dp(a), a.size))
+        return u.value, a
 
     def step_count(self) -> int:
         t = C.c_int64()

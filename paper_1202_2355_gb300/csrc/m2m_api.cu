@@ -102,17 +102,48 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
 {
     Model &m = ctx->m;
     if (!pot || !obs || !pg || !opt) return fail(ctx, M2M_ERR_ARG, "null descriptor");
-    if (pot->kind < 0 || pot->kind > 2) return fail(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot->kind);
+    if (pot->kind < 0 || pot->kind > 3) return fail(ctx, M2M_ERR_ARG, "unknown potential kind %d", pot->kind);
     m.pot = pot->kind;
     m.G = pot->G; m.M = pot->M; m.a = pot->a; m.Ms = pot->Ms; m.rs = pot->rs;
     m.v0 = pot->v0; m.r0 = pot->r0; m.q = pot->q;
-    if (m.pot != 2 && !(m.a > 0 && m.G >= 0 && m.M >= 0))
+    if (m.pot < 2 && !(m.a > 0 && m.G >= 0 && m.M >= 0))
         return fail(ctx, M2M_ERR_ARG, "Hernquist needs a > 0, G >= 0, M >= 0");
     if (m.pot == 1 && !(m.rs > 0 && m.Ms >= 0)) return fail(ctx, M2M_ERR_ARG, "NFW needs rs > 0, Ms >= 0");
-    if (m.pot == 2 && !(m.r0 > 0 && m.q > 0)) return fail(ctx, M2M_ERR_ARG, "log halo needs r0 > 0, q > 0");
+    if (m.pot >= 2 && !(m.r0 > 0 && m.q > 0)) return fail(ctx, M2M_ERR_ARG, "log halo needs r0 > 0, q > 0");
     if (m.pot == 0) m.phi_min = -m.G * m.M / m.a;
     else if (m.pot == 1) m.phi_min = -m.G * m.M / m.a - m.G * m.Ms / m.rs;
-    else m.phi_min = m.v0 * m.v0 * std::log(m.r0);
+    else if (m.pot == 2) m.phi_min = m.v0 * m.v0 * std::log(m.r0);
+    else m.phi_min = -1e300;  // the stellar well is known only once the expansion is built
+    m.scf_n = m.scf_lmax = m.scf_nlm = 0;
+    m.eps_ups = 0.0;
+    if (m.pot == 3) {
+        if (pot->scf_n < 1 || pot->scf_n > kScfMaxRadii || pot->scf_lmax < 0 || pot->scf_lmax > kScfLmax ||
+            !pot->scf_r)
+            return fail(ctx, M2M_ERR_ARG, "the self-consistent potential needs 1..%d grid radii and 0 <= lmax <= %d",
+                        kScfMaxRadii, kScfLmax);
+        for (int k = 0; k < pot->scf_n; ++k)
+            if (!std::isfinite(pot->scf_r[k]) || !(pot->scf_r[k] > 0) || (k > 0 && !(pot->scf_r[k] > pot->scf_r[k - 1])))
+                return fail(ctx, M2M_ERR_ARG, "self-consistent potential: grid radii must be > 0 and increasing");
+        if (!(pot->ups > 0) || !std::isfinite(pot->ups) || !(pot->eps_ups >= 0) || !std::isfinite(pot->eps_ups) ||
+            !(m.G >= 0))
+            return fail(ctx, M2M_ERR_ARG, "self-consistent potential: Upsilon > 0, eps_ups >= 0 and G >= 0 required");
+        m.scf_n = pot->scf_n;
+        m.scf_lmax = pot->scf_lmax;
+        m.scf_nlm = (m.scf_lmax + 1) * (m.scf_lmax + 1);
+        m.eps_ups = pot->eps_ups;
+        ctx->scf_ups0 = pot->ups;
+        ctx->scf_r.assign(pot->scf_r, pot->scf_r + m.scf_n);
+        for (int l = 0; l <= m.scf_lmax; ++l)
+            for (int mm = -l; mm <= l; ++mm) {
+                const int am = mm < 0 ? -mm : mm;
+                double ratio = 1.0;
+                for (int i = l - am + 1; i <= l + am; ++i) ratio /= i;
+                double nrm = std::sqrt((2.0 * l + 1.0) / (4.0 * 3.14159265358979323846) * ratio);
+                if (mm != 0) nrm *= std::sqrt(2.0);
+                m.scf_norm[l * (l + 1) + mm] = nrm;
+                m.scf_norm_f[l * (l + 1) + mm] = float(nrm);
+            }
+    }
 
     const double inc = obs->incl_deg * 3.14159265358979323846 / 180.0;
     m.sin_i = std::sin(inc);
@@ -318,7 +349,9 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     // circular orbits
     m.lc_closed = (m.pot == 0) ? 1 : 0;
     ctx->lcE.clear();
-    if (!m.lc_closed) {
+    if (m.pot == 3) {  // Lc(E) by bisection in the current expansion (see circular_L)
+        m.lc_n = 0;
+    } else if (!m.lc_closed) {
         const int n = 4096;
         m.lc_n = n;
         m.lc_lnr0 = std::log(1e-6);
@@ -347,7 +380,7 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
         return fail(ctx, M2M_ERR_ARG, "unknown precision");
     ctx->precision = opt->precision;
     m.wps = ctx->precision == M2M_PREC_FP64 ? 2 : 1;
-    m.cache_accel = (ctx->precision == M2M_PREC_FP64 || m.pot == 1) ? 1 : 0;
+    m.cache_accel = m.pot != 3 && (ctx->precision == M2M_PREC_FP64 || m.pot == 1) ? 1 : 0;
     m.off_total = m.J * m.wps;
     m.off_grid = (m.J + 1) * m.wps;
     // aperture cache: one 16-bit code per particle (two small groups or one group)
@@ -361,7 +394,13 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     m.gx_group = -1;
     for (int g = 0; m.ap_cache && m.gx_group < 0 && g < m.n_groups; ++g)
         if (m.g[g].max_gh >= 0) m.gx_group = g;
-    m.off_count = (m.J + 1 + m.ncell) * m.wps;
+    // slots of the sums: observables, total weight, prior grid, then (self-consistent
+    // potential) the expansion and the derivatives for the mass-to-light ratio
+    m.off_scf = m.J + 1 + m.ncell;
+    m.off_dups = m.off_scf + m.scf_n * m.scf_nlm;
+    m.n_dups = (m.pot == 3 && m.eps_ups > 0.0) ? m.J : 0;
+    m.nslots = m.off_dups + m.n_dups;
+    m.off_count = m.nslots * m.wps;
     m.hist_words = m.off_count + m.ncell;
 
     // descriptor hash (for checkpoint compatibility)
@@ -497,6 +536,23 @@ static m2m_status upload_tables(m2m_ctx *ctx)
         }
     }
     if ((s = up(ctx->d_lcE, ctx->lcE)) != M2M_OK) return s;
+    if (m.pot == 3) {
+        if ((s = up(ctx->d_scf_r, ctx->scf_r)) != M2M_OK) return s;
+        const size_t nt = size_t(m.scf_n + 1) * m.scf_nlm * 2;
+        free_dev(ctx->d_scf_tab);
+        free_dev(ctx->d_scf_tabf);
+        free_dev(ctx->d_scf_coef);
+        CU(cudaMalloc(&ctx->d_scf_tab, sizeof(double) * nt));
+        CU(cudaMalloc(&ctx->d_scf_tabf, sizeof(float) * nt));
+        CU(cudaMalloc(&ctx->d_scf_coef, sizeof(double) * size_t(m.scf_n) * m.scf_nlm));
+        CU(cudaMemset(ctx->d_scf_tab, 0, sizeof(double) * nt));
+        CU(cudaMemset(ctx->d_scf_tabf, 0, sizeof(float) * nt));
+        CU(cudaMemset(ctx->d_scf_coef, 0, sizeof(double) * size_t(m.scf_n) * m.scf_nlm));
+        ctx->m.scf_r = ctx->d_scf_r;
+        ctx->m.scf_tab = ctx->d_scf_tab;
+        ctx->m.scf_tabf = ctx->d_scf_tabf;
+        ctx->m.scf_coef = ctx->d_scf_coef;
+    }
     if ((s = up(ctx->d_Y, ctx->Y)) != M2M_OK) return s;
     if ((s = up(ctx->d_sig, ctx->sig)) != M2M_OK) return s;
     if ((s = up(ctx->d_post, ctx->obs_post)) != M2M_OK) return s;
@@ -706,6 +762,11 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
         W0_host = ctx->shard_w;
         m.n_all = ctx->shard_n;
     }
+    if (m.pot == 3) {
+        // the particles' own well is not built yet: its depth is below G Upsilon W / r_0
+        const double W = (ctx->shard ? ctx->shard_w : W0_host) > 0 ? (ctx->shard ? ctx->shard_w : W0_host) : 1.0;
+        v2max += 2.0 * ctx->scf_ups0 * m.G * W / ctx->scf_r[0];
+    }
     // fixed-point ranges. Weights are deposited before renormalisation, so the total
     // may exceed W0 by the largest single-step growth exp(eps dt F): FP64 mode keeps
     // 2^24 W0 of range (the second word still resolves 2^-70 W0), mixed mode 2^12 W0
@@ -717,6 +778,13 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     m.fx_w = pow2_floor(two62 / Wb);
     m.fx_v2 = pow2_floor(two62 / (Wb * (m.v2max > 1.0 ? m.v2max : 1.0)));
     m.fx_gh = pow2_floor(two62 / (Wb * 1.5));  // |2 sqrt(pi) u_n| <= sqrt(2) (Cramer's inequality)
+    // derivatives for the mass-to-light ratio: |1/2 v c_n (2n H_(n-1) - nu H_n) e^(-nu^2/2)/sigma_p|
+    // <= 1.5 |v| / sigma_p (n <= 6)
+    {
+        double isp_max = 1.0;
+        for (double v : ctx->isp) isp_max = std::max(isp_max, v);
+        m.fx_dv = pow2_floor(two62 / (Wb * 1.5 * std::sqrt(m.v2max) * isp_max + Wb));
+    }
     ctx->obs_iscale.resize(m.J);
     for (int j = 0; j < m.J; ++j) {
         const int k = ctx->obs_kind[j];
@@ -727,6 +795,7 @@ static m2m_status finish_load(m2m_ctx *ctx, const double *dx, const double *dy, 
     CU(cudaMemsetAsync(ctx->d_hist, 0, sizeof(long long) * exchange_words(ctx), ctx->stream));
     Scalars sc0{};
     sc0.Wrange = 9.2233720368547758e18 / m.fx_w;
+    sc0.ups = ctx->scf_ups0;
     CU(cudaMemcpyAsync(ctx->d_sc, &sc0, sizeof(Scalars), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemsetAsync(ctx->d_prior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->d_iprior, 0, sizeof(double) * (m.ncell + 1), ctx->stream));
@@ -1200,6 +1269,19 @@ extern "C" m2m_status m2m_get_prior_smoothing(m2m_ctx *ctx, double *raw_means, d
     return m2m_synchronize(ctx);
 }
 
+extern "C" m2m_status m2m_get_scf(m2m_ctx *ctx, double *ups, double *coeffs, int32_t ncoeffs)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (!ctx->sub.empty()) return not_a_fit(ctx);
+    if (ctx->m.pot != 3) return fail(ctx, M2M_ERR_STATE, "not a self-consistent potential");
+    if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
+    const int nc = ctx->m.scf_n * ctx->m.scf_nlm;
+    if (coeffs && ncoeffs != nc) return fail(ctx, M2M_ERR_ARG, "ncoeffs must be scf_n (lmax+1)^2 = %d", nc);
+    if (coeffs) CU(cudaMemcpyAsync(coeffs, ctx->d_scf_coef, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ups) CU(cudaMemcpyAsync(ups, &ctx->d_sc->ups, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return m2m_synchronize(ctx);
+}
+
 extern "C" m2m_status m2m_get_step_count(m2m_ctx *ctx, int64_t *t)
 {
     if (!ctx || !t) return M2M_ERR_ARG;
@@ -1258,6 +1340,8 @@ struct CkptHeader {
 extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 {
     if (ctx && ctx->shard) return fail(ctx, M2M_ERR_STATE, "checkpoints of shards are not supported");
+    if (ctx && ctx->m.pot == 3)
+        return fail(ctx, M2M_ERR_STATE, "checkpoints of a self-consistent potential are not supported");
     if (!ctx || !path) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return not_a_fit(ctx);
     if (!ctx->loaded) return fail(ctx, M2M_ERR_STATE, "no particles loaded");
@@ -1321,6 +1405,8 @@ extern "C" m2m_status m2m_save_state(m2m_ctx *ctx, const char *path)
 extern "C" m2m_status m2m_load_state(m2m_ctx *ctx, const char *path)
 {
     if (ctx && ctx->shard) return fail(ctx, M2M_ERR_STATE, "checkpoints of shards are not supported");
+    if (ctx && ctx->m.pot == 3)
+        return fail(ctx, M2M_ERR_STATE, "checkpoints of a self-consistent potential are not supported");
     if (!ctx || !path) return M2M_ERR_ARG;
     if (!ctx->sub.empty()) return not_a_fit(ctx);
     FILE *f = std::fopen(path, "rb");
@@ -1662,6 +1748,7 @@ void destroy_impl(m2m_ctx *ctx)
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     free_state(ctx);
     free_dev(ctx->d_edges); free_dev(ctx->d_Vp); free_dev(ctx->d_isp); free_dev(ctx->d_Vpf); free_dev(ctx->d_ispf); free_dev(ctx->d_lcE); free_dev(ctx->d_lut);
+    free_dev(ctx->d_scf_r); free_dev(ctx->d_scf_tab); free_dev(ctx->d_scf_tabf); free_dev(ctx->d_scf_coef);
     free_dev(ctx->d_Y); free_dev(ctx->d_sig); free_dev(ctx->d_post); free_dev(ctx->d_iscale);
     free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_recf); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
     free_dev(ctx->d_ytil);

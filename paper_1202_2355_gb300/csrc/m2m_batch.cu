@@ -322,9 +322,12 @@ extern "C" m2m_status m2m_create_batch(int32_t nmodels, const m2m_potential *pot
         return fail(nullptr, M2M_ERR_ARG, "nmodels >= 1 and non-null descriptor arrays required");
     if (opt->deposit == M2M_DEPOSIT_GLOBAL)
         return fail(nullptr, M2M_ERR_ARG, "batches use the block-shared deposit");
-    for (int i = 0; i < nmodels; ++i)
+    for (int i = 0; i < nmodels; ++i) {
         if (priors[i].smoothing != M2M_SMOOTH_NONE)
             return fail(nullptr, M2M_ERR_ARG, "fit %d: prior smoothing is not available in batches", i);
+        if (pots[i].kind == M2M_POT_SCF)
+            return fail(nullptr, M2M_ERR_ARG, "fit %d: the self-consistent potential is not available in batches", i);
+    }
     if (opt->precision != M2M_PREC_FP64 && opt->precision != M2M_PREC_MIXED)
         return fail(nullptr, M2M_ERR_ARG, "unknown precision %d", opt->precision);
     m2m_ctx *ctx = new (std::nothrow) m2m_ctx();

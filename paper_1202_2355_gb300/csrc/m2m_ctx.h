@@ -25,7 +25,7 @@ struct m2m_ctx {
     size_t smem_step = 0, smem_mat = 0;
 
     // host copies of the descriptors
-    std::vector<double> edges, Vp, isp, Y, sig, obs_post, obs_iscale, area_of_obs, lcE;
+    std::vector<double> edges, Vp, isp, Y, sig, obs_post, obs_iscale, area_of_obs, lcE, scf_r;
     std::vector<int> obs_kind;
     std::vector<unsigned short> lut;
     uint64_t config_hash = 0;
@@ -51,6 +51,10 @@ struct m2m_ctx {
     double *d_spart = nullptr, *d_sz = nullptr, *d_ss = nullptr;
     int smooth_ch = 1;
     m2m::Scalars *d_sc = nullptr;
+    // self-consistent potential: grid radii, interval tables (FP64, FP32), coefficients
+    double *d_scf_r = nullptr, *d_scf_tab = nullptr, *d_scf_coef = nullptr;
+    float *d_scf_tabf = nullptr;
+    double scf_ups0 = 1.0;
     double *d_wout = nullptr;
     long long wout_cap = 0;
     bool loaded = false;

@@ -101,6 +101,21 @@ struct Model {
     // n_all is the particle count of the whole fit (the local count when not sharded)
     int shard;
     long long n_all;
+    // self-consistent stellar potential (pot 3, Sec. 6): phi = Upsilon phi_star + log halo,
+    // phi_star the multipole expansion of the particles' luminosity on scf_n grid radii with
+    // harmonics l <= scf_lmax (scf_nlm = (scf_lmax + 1)^2, index l (l + 1) + m). Its sums
+    // are the slots [off_scf, off_scf + scf_n scf_nlm), deposited on update steps; with the
+    // mass-to-light fit (eps_ups > 0) the derivatives D_j of the observables are the slots
+    // [off_dups, off_dups + n_dups). nslots counts every slot of the sums.
+    int scf_n, scf_lmax, scf_nlm, off_scf, off_dups, n_dups, nslots;
+    double eps_ups, fx_dv;
+    const double *scf_r;   // device: grid radii
+    double *scf_tab;       // device: per interval j = 0..scf_n, (TA_lm, TB_lm), Upsilon and
+                           // -4 pi G/(2l+1) folded in (see scf_field)
+    float *scf_tabf;       // FP32 copy
+    double *scf_coef;      // device: a_lm,k of the last expansion (scf_n x scf_nlm)
+    double scf_norm[49];   // factor of Y_lm (N_lm, sqrt2 N_lm for m != 0) by index
+    float scf_norm_f[49];
 };
 
 constexpr unsigned kApNone8 = 0xFFu, kApNone16 = 0xFFFFu;
@@ -171,11 +186,13 @@ __device__ __forceinline__ void each_group(const Model &m, F &&f)
     if constexpr (sizeof...(Rest) > 0) each_group<G0 + 1, Rest...>(m, f);
 }
 
-// Model constants in the state type, so that the FP32 path runs no FP64 operation.
+// Model constants in the state type, so that the FP32 path runs no FP64 operation. The
+// batched kernel copies a fit's constants into shared memory in 8-byte words: the struct is
+// kept a multiple of 16 bytes so that every element of an array of them is 8-byte aligned.
 template <class T>
-struct Cst {
+struct alignas(16) Cst {
     T GM, a, GMs, rs, v0sq, r0sq, q2, phi_min, hn_phi0, sin_i, cos_i;
-    T dt, hdt, dteps, mu, v2max, fx_w, fx_v2, fx_gh;
+    T dt, hdt, dteps, mu, v2max, fx_w, fx_v2, fx_gh, fx_dv;
     T s_lo, s_den, e_scale, nE, nx;
     T lc_lnr0, lc_dlnr, lc_r0, lc_rmax;
 };
@@ -189,7 +206,7 @@ inline Cst<T> make_cst(const Model &m)
     k.phi_min = T(m.phi_min); k.hn_phi0 = T(m.rs > 0 ? -m.G * m.Ms / m.rs : 0.0);
     k.sin_i = T(m.sin_i); k.cos_i = T(m.cos_i);
     k.dt = T(m.dt); k.hdt = T(0.5 * m.dt); k.dteps = T(m.dt * m.eps); k.mu = T(m.mu);
-    k.v2max = T(m.v2max); k.fx_w = T(m.fx_w); k.fx_v2 = T(m.fx_v2); k.fx_gh = T(m.fx_gh);
+    k.v2max = T(m.v2max); k.fx_w = T(m.fx_w); k.fx_v2 = T(m.fx_v2); k.fx_gh = T(m.fx_gh); k.fx_dv = T(m.fx_dv);
     k.s_lo = T(m.s_lo); k.s_den = T(m.s_den);
     k.e_scale = T(m.G * m.M > 0 ? m.a / (m.G * m.M) : 0.0);
     k.nE = T(m.nE); k.nx = T(m.nx);
@@ -216,6 +233,7 @@ struct Scalars {
     int smooth_pending;    // new raw cell means wait for the prior smoothing kernels
     unsigned smooth_blocks;   // blocks of the running smoothing kernel that have finished
     double smooth_lambda;  // smoothing weight of the last prior update
+    double ups;            // mass-to-light ratio of the self-consistent potential
 };
 
 template <class T>
@@ -246,6 +264,14 @@ constexpr bool kLogWeights = sizeof(T) == 8;
 // NFW potential, whose halo term takes a logarithm and a division).
 template <class T>
 constexpr bool kCacheAccel = sizeof(T) == 8;
+
+// The self-consistent potential is not of the force-factor form: its acceleration is
+// evaluated at both ends of the step.
+template <class T>
+__host__ __device__ __forceinline__ bool keeps_accel(const Model &m)
+{
+    return m.pot != 3 && (kCacheAccel<T> || m.cache_accel);
+}
 
 struct Buffers {
     const double *edges, *Vp, *isp;  // per group edges, per aperture V_p and 1/sigma_p
@@ -380,9 +406,146 @@ __host__ __device__ __forceinline__ void nfw_logs(float q, float &l1, float &mu)
     }
 }
 
+// ---------------------------------------------------------------- self-consistent potential
+//
+// The stellar potential of pot 3 (Sec. 6) is the multipole expansion of the particles'
+// luminosity on grid radii r_0 < ... < r_{n-1} (thin shells, see the host's description
+// at m2m_potential). At r in the interval j (r_{j-1} <= r < r_j, r_{-1} = 0, r_n = infinity):
+//   phi_star(x) = sum_lm [TA_lm(j) r^-(2l+1) + TB_lm(j)] R_lm(x),
+// with R_lm = r^l Y_lm the regular solid harmonic, TA_lm(j) = C_l sum_{k<j} a_lm,k r_k^l (the
+// shells inside) and TB_lm(j) = C_l sum_{k>=j} a_lm,k r_k^-(l+1) (the shells outside),
+// C_l = -4 pi G Upsilon/(2l+1); the finalize builds these tables on update steps. R_lm =
+// N_lm T_lm(z, r^2) Re or Im (x + iy)^m, where T_mm = (2m-1)!!, T_{m+1,m} = (2m+1) z T_mm and
+// (l-m) T_lm = (2l-1) z T_{l-1,m} - (l+m-1) r^2 T_{l-2,m} (the recurrences of the associated
+// Legendre functions times r^(l-m)); the gradient follows the same recurrences, carried as
+// derivatives in z and r^2, with d(x + iy)^m = m (x + iy)^(m-1) (dx + i dy).
+constexpr int kScfLmax = 6;
+constexpr int kScfMaxRadii = 64;
+
+template <class T>
+__device__ __forceinline__ const T *scf_table(const Model &m);
+template <>
+__device__ __forceinline__ const double *scf_table<double>(const Model &m) { return m.scf_tab; }
+template <>
+__device__ __forceinline__ const float *scf_table<float>(const Model &m) { return m.scf_tabf; }
+
+// Number of grid radii with r_k^2 <= r2: the interval j of the point.
+template <class T>
+__device__ __forceinline__ int scf_interval(const Model &m, T r2)
+{
+    int lo = 0, hi = m.scf_n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const T rk = T(__ldg(m.scf_r + mid));
+        if (rk * rk <= r2) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// phi_star (Upsilon included) at (x, y, z) and, if g is not null, its gradient.
+template <class T>
+__device__ T scf_field(const Model &m, T x, T y, T z, T *g)
+{
+    const T r2 = fma(x, x, fma(y, y, z * z));
+    const int j = scf_interval(m, r2);
+    const T *tab = scf_table<T>(m) + size_t(j) * m.scf_nlm * 2;
+    const bool inner = j > 0;  // then r >= r_0 > 0
+    const T ir2 = inner ? T(1) / r2 : T(0);
+    const T ir = inner ? d_sqrt(ir2) : T(0);
+    const int L = m.scf_lmax;
+    T phi = T(0), gx = T(0), gy = T(0), gz = T(0);
+    T cm = T(1), sm = T(0), cm1 = T(0), sm1 = T(0);  // (x + iy)^m and (x + iy)^(m-1)
+    T dfac = T(1);                                  // (2m-1)!!
+    T irm = ir;                                     // r^-(2m+1)
+    for (int mm = 0; mm <= L; ++mm) {
+        T t1 = dfac, t1z = T(0), t1r = T(0);  // T_l and its z, r^2 derivatives, l = mm
+        T t0 = T(0), t0z = T(0), t0r = T(0);  // T_(l-1)
+        T irl = irm;
+        for (int l = mm; l <= L; ++l) {
+            if (l > mm) {  // the recurrence in l
+                const T a = T(2 * l - 1), bq = T(l + mm - 1), il = T(1) / T(l - mm);
+                const T tn = (a * z * t1 - bq * r2 * t0) * il;
+                const T tnz = (a * (t1 + z * t1z) - bq * r2 * t0z) * il;
+                const T tnr = (a * z * t1r - bq * (t0 + r2 * t0r)) * il;
+                t0 = t1; t0z = t1z; t0r = t1r;
+                t1 = tn; t1z = tnz; t1r = tnr;
+                irl *= ir2;
+            }
+            for (int v = 0; v < (mm > 0 ? 2 : 1); ++v) {
+                const int idx = l * (l + 1) + (v == 0 ? mm : -mm);
+                const T ta = tab[2 * idx], tb = tab[2 * idx + 1];
+                const T N = sizeof(T) == 8 ? T(m.scf_norm[idx]) : T(m.scf_norm_f[idx]);
+                const T P = v == 0 ? cm : sm;
+                const T R = N * t1 * P;
+                const T coef = fma(ta, irl, tb);
+                phi = fma(coef, R, phi);
+                if (g) {
+                    // grad P: cos (m C_(m-1), -m S_(m-1), 0); sin (m S_(m-1), m C_(m-1), 0)
+                    const T fm = T(mm);
+                    const T px = v == 0 ? fm * cm1 : fm * sm1, py = v == 0 ? -fm * sm1 : fm * cm1;
+                    const T gRx = N * fma(T(2) * x * t1r, P, t1 * px);
+                    const T gRy = N * fma(T(2) * y * t1r, P, t1 * py);
+                    const T gRz = N * (t1z + T(2) * z * t1r) * P;
+                    const T rad = ta * T(2 * l + 1) * irl * ir2 * R;  // d r^-(2l+1) / dx_c = -(2l+1) r^-(2l+3) x_c
+                    gx = fma(coef, gRx, gx) - rad * x;
+                    gy = fma(coef, gRy, gy) - rad * y;
+                    gz = fma(coef, gRz, gz) - rad * z;
+                }
+            }
+        }
+        cm1 = cm;
+        sm1 = sm;
+        const T cn = fma(cm, x, -(sm * y));
+        sm = fma(cm, y, sm * x);
+        cm = cn;
+        dfac *= T(2 * mm + 1);
+        irm *= ir2;
+    }
+    if (g) {
+        g[0] = gx;
+        g[1] = gy;
+        g[2] = gz;
+    }
+    return phi;
+}
+
+// Potential and acceleration of the flattened logarithmic halo (eq. log_halo).
+template <class T>
+__host__ __device__ __forceinline__ T log_halo_phi(const Cst<T> &k, T x, T y, T z)
+{
+    const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
+    return T(0.5) * k.v0sq * d_log(D);
+}
+
+template <class T>
+__device__ __forceinline__ T scf_potential(const Model &m, const Cst<T> &k, T x, T y, T z)
+{
+#ifdef __CUDA_ARCH__
+    return scf_field<T>(m, x, y, z, nullptr) + log_halo_phi(k, x, y, z);
+#else
+    return T(0);
+#endif
+}
+
+template <class T>
+__device__ __forceinline__ void scf_accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay, T &az)
+{
+    T g[3];
+    scf_field<T>(m, x, y, z, g);
+    const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
+    const T f = -d_div(k.v0sq, D);
+    ax = fma(f, x, -g[0]);
+    ay = fma(f, y, -g[1]);
+    az = d_div(f * z, k.q2) - g[2];
+}
+
 template <class T>
 __host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k, T x, T y, T z)
 {
+#ifdef __CUDA_ARCH__
+    if (m.pot == 3) return scf_potential(m, k, x, y, z);
+#endif
     if (m.pot == 2) {
         const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
         return T(0.5) * k.v0sq * d_log(D);
@@ -451,6 +614,12 @@ template <class T>
 __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay,
                                                T &az)
 {
+#ifdef __CUDA_ARCH__
+    if (m.pot == 3) {
+        scf_accel(m, k, x, y, z, ax, ay, az);
+        return;
+    }
+#endif
     accel_from(m, k, accel_factor(m, k, x, y, z), x, y, z, ax, ay, az);
 }
 
@@ -851,6 +1020,89 @@ __device__ __forceinline__ T data_term_cached(const Model &m, const Tables<T> &t
     return data;
 }
 
+// ---- deposits of the self-consistent potential
+
+// emit(slot, w gamma_k Y_lm) of the expansion (Sec. 6): the particle's luminosity on its
+// one or two grid points, cloud-in-cell weights as eq. alm except that r < r_0 goes wholly to
+// point 0 and r >= r_{n-1} wholly to point n-1; Y_lm from the associated-Legendre recurrences
+// in cos(theta) and the powers of cos(phi) + i sin(phi).
+template <class T, class F>
+__device__ __forceinline__ void scf_deposit(const Model &m, T x, T y, T z, T w, F &&emit)
+{
+    const T r2 = fma(x, x, fma(y, y, z * z));
+    const int j = scf_interval(m, r2);
+    int k0;
+    T g0 = T(1), g1 = T(0);
+    if (j == 0) {
+        k0 = 0;
+    } else if (j == m.scf_n) {
+        k0 = m.scf_n - 1;
+    } else {
+        const T r = d_sqrt(r2), ra = T(__ldg(m.scf_r + j - 1)), rb = T(__ldg(m.scf_r + j));
+        k0 = j - 1;
+        g0 = d_div(rb - r, rb - ra);
+        g1 = d_div(r - ra, rb - ra);
+    }
+    T ct, st, cp, sp;
+    shell_angles(x, y, z, ct, st, cp, sp);
+    const int L = m.scf_lmax, nlm = m.scf_nlm;
+    const int s0 = m.off_scf + k0 * nlm;
+    T cm = T(1), sm = T(0), pmm = T(1);
+    for (int mm = 0; mm <= L; ++mm) {
+        T p0 = T(0), p1 = pmm;
+        for (int l = mm; l <= L; ++l) {
+            if (l > mm) {
+                const T p2 = d_div(fma(ct * T(2 * l - 1), p1, -(T(l + mm - 1) * p0)), T(l - mm));
+                p0 = p1;
+                p1 = p2;
+            }
+            for (int v = 0; v < (mm > 0 ? 2 : 1); ++v) {
+                const int idx = l * (l + 1) + (v == 0 ? mm : -mm);
+                const T N = sizeof(T) == 8 ? T(m.scf_norm[idx]) : T(m.scf_norm_f[idx]);
+                const T Y = N * p1 * (v == 0 ? cm : sm);
+                const T wy = w * Y;
+                emit(s0 + idx, g0 * wy);
+                if (g1 != T(0)) emit(s0 + nlm + idx, g1 * wy);
+            }
+        }
+        const T cn = fma(cm, cp, -(sm * sp));
+        sm = fma(sm, cp, cm * sp);
+        cm = cn;
+        pmm *= T(2 * mm + 1) * st;
+    }
+}
+
+// emit(observable, D, class) of the derivatives of the kinematic kernels of group G at
+// aperture p with respect to ln Upsilon when the velocities scale as Upsilon^(1/2):
+// D = 1/2 w v_los dK/dv_los; w v_los^2 for v_los^2 (class kClassVel), and for b_n, with
+// K_n = c_n H_n(nu) e^(-nu^2/2), 1/2 w v_los c_n (2n H_(n-1) - nu H_n) e^(-nu^2/2)/sigma_p
+// (class kClassDv).
+constexpr int kClassDv = 3;
+template <unsigned M, class T, class F>
+__device__ __forceinline__ void group_dkernels(const GroupDesc &G, const Tables<T> &tb, int p, T vlos, T w, F &&emit)
+{
+    using P = GP<M>;
+    const int base = G.obs_off + p;
+    if (P::v2(G)) emit(base + G.k_v2 * G.n_ap, w * vlos * vlos, kClassVel);
+    const int nmax = P::max_gh(G);
+    if (nmax >= 0) {
+        const T is = tb.isp[G.ap_off + p];
+        const T nu = (vlos - tb.vp[G.ap_off + p]) * is;
+        const T half = T(0.5) * w * vlos * is * kexp(tb, T(-0.5) * nu * nu);
+        T hm1 = T(0), h = T(1);  // H_(n-1), H_n at n = 0
+#pragma unroll
+        for (int n = 0; n <= 6; ++n) {
+            if (n <= nmax) {
+                if (P::gh(G, n)) emit(base + G.k_gh[n] * G.n_ap, T(gh_c(n)) * half * fma(T(2 * n), hm1, -(nu * h)),
+                                      kClassDv);
+                const T hn1 = fma(T(2) * nu, h, -(T(2 * n) * hm1));
+                hm1 = h;
+                h = hn1;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- priors
 
 // v_c^2 = R |a(R)| and the potential at radius R on the x axis (R >= 0), for the
@@ -860,7 +1112,7 @@ __device__ __forceinline__ T data_term_cached(const Model &m, const Tables<T> &t
 template <class T>
 __host__ __device__ __forceinline__ void circ_terms(const Model &m, const Cst<T> &k, T R, T &vc2, T &phi)
 {
-    if (m.pot == 2) {
+    if (m.pot >= 2) {
         T ax, ay, az;
         accel(m, k, R, T(0), T(0), ax, ay, az);
         vc2 = -R * ax;
@@ -904,7 +1156,7 @@ __host__ __device__ __forceinline__ T circ_energy(const Model &m, const Cst<T> &
 template <class T>
 __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
 {
-    if (m.pot != 2 && !(E < T(0))) return T(0);
+    if (m.pot < 2 && !(E < T(0))) return T(0);
     if (m.lc_closed) {
         const T e = E * k.e_scale;
         if (!(e > T(-1))) return T(0);
@@ -917,6 +1169,26 @@ __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
     const int n = m.lc_n;
     int lo = 0, hi = n - 1;
     T R;
+    if (m.pot == 3) {
+        // The self-consistent potential need not be lowest at the centre (its l > 0 terms can
+        // lower it off the axis), and its thin shells put kinks in E_c(R) at the grid radii,
+        // so E_c(R) = E may have no root below phi(0) and is not smooth: Lc(E) by plain
+        // bisection, from [0, 1] doubled until it brackets the root (no circular orbit
+        // below E_c(0) = phi(0)).
+        if (!(E > circ_energy(m, k, T(0)))) return T(0);
+        T hi = T(1), lo = T(0);
+        while (hi < T(1e15) && circ_energy(m, k, hi) <= E) hi *= T(2);
+        for (int it = 0; it < 400; ++it) {
+            const T mid = T(0.5) * (lo + hi);
+            if (!(mid > lo) || !(mid < hi)) break;
+            if (circ_energy(m, k, mid) <= E) lo = mid;
+            else hi = mid;
+        }
+        R = T(0.5) * (lo + hi);
+        T vc2, phi;
+        circ_terms(m, k, R, vc2, phi);
+        return R * d_sqrt(vc2);
+    }
     if (!(E > T(__ldg(lcE)))) {
         R = k.lc_r0;
     } else if (!(E < T(__ldg(lcE + n - 1)))) {
@@ -1091,7 +1363,7 @@ template <>
 struct Acc<float> {
     static __host__ __device__ size_t bytes(const Model &m)
     {
-        return sizeof(int) * (3 * size_t(m.J + 1 + m.ncell) + size_t(m.ncell)) + 8;
+        return sizeof(int) * (3 * size_t(m.nslots) + size_t(m.ncell)) + 8;
     }
     // round(v*scale) as L = hi 2^32 + mid 2^16 + lo with mid, lo in [0, 2^16) and hi signed:
     // the two's-complement fields of one 64-bit conversion. Per block the lo and mid sums
@@ -1108,12 +1380,12 @@ struct Acc<float> {
     }
     __device__ static void count(void *base, const Model &m, int c)
     {
-        atomicAdd(static_cast<int *>(base) + 3 * (m.J + 1 + m.ncell) + c, 1);
+        atomicAdd(static_cast<int *>(base) + 3 * m.nslots + c, 1);
     }
     __device__ static long long word(const void *base, const Model &m, int k)
     {
         const int *h = static_cast<const int *>(base);
-        if (k >= m.off_count) return static_cast<long long>(h[3 * (m.J + 1 + m.ncell) + (k - m.off_count)]);
+        if (k >= m.off_count) return static_cast<long long>(h[3 * m.nslots + (k - m.off_count)]);
         const int *q = h + 3 * k;
         return limbs_value(q[0], q[1], q[2]);
     }
@@ -1398,10 +1670,65 @@ __device__ __forceinline__ void block_fold(double *red)
     }
 }
 
+// The self-consistent potential at an update (Sec. 6), in the finalize: the mass-to-light
+// ratio follows the chi^2 gradient, d ln Upsilon/dt = -eps_ups sum_j Delta_j/sigma_j D_j over
+// the update_every steps to the next update (not at the load); then the interval tables
+// TA, TB of scf_field from the new coefficients a_lm,k and Upsilon. red: blockDim doubles.
+template <int WPS>
+__device__ void scf_finalize(const Model &m, const Buffers &b, double s_ren, int init, double *red)
+{
+    Scalars &sc = *b.sc;
+    if (!init && m.n_dups > 0) {
+        double part = 0.0;
+        for (int j = threadIdx.x; j < m.J; j += blockDim.x) {
+            const int kind = b.obs_kind[j];
+            const double sj = kind == kKindV2 ? m.fx_v2 : ((kind >= kKindGH0 && kind <= kKindGH0 + 6) ? m.fx_dv : 0.0);
+            if (sj == 0.0) continue;
+            const double D = fx_read<WPS>(b.hist, m.off_dups + j) / sj * s_ren;
+            part += b.delta[j] / b.sig[j] * D;
+        }
+        red[threadIdx.x] = part;
+        __syncthreads();
+        block_fold(red);
+        if (threadIdx.x == 0) sc.ups *= exp(-m.eps_ups * double(m.update_every) * m.dt * red[0]);
+        __syncthreads();
+    }
+    const double ups = sc.ups;
+    const int n = m.scf_n, nlm = m.scf_nlm;
+    for (int idx = threadIdx.x; idx < nlm; idx += blockDim.x) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= idx) ++l;
+        const double C = -4.0 * 3.14159265358979323846 * m.G * ups / double(2 * l + 1);
+        double A = 0.0;  // sum over the shells inside
+        for (int j = 0; j <= n; ++j) {
+            m.scf_tab[(size_t(j) * nlm + idx) * 2] = C * A;
+            if (j < n) {
+                const double a = fx_read<WPS>(b.hist, m.off_scf + j * nlm + idx) / m.fx_gh * s_ren;
+                m.scf_coef[size_t(j) * nlm + idx] = a;
+                A += a * pow(m.scf_r[j], l);
+            }
+        }
+        double B = 0.0;  // sum over the shells outside
+        for (int j = n; j >= 0; --j) {
+            if (j < n) {
+                const double a = fx_read<WPS>(b.hist, m.off_scf + j * nlm + idx) / m.fx_gh * s_ren;
+                B += a * pow(m.scf_r[j], -(l + 1));
+            }
+            m.scf_tab[(size_t(j) * nlm + idx) * 2 + 1] = C * B;
+        }
+        for (int j = 0; j <= n; ++j) {
+            const size_t q = (size_t(j) * nlm + idx) * 2;
+            m.scf_tabf[q] = float(m.scf_tab[q]);
+            m.scf_tabf[q + 1] = float(m.scf_tab[q + 1]);
+        }
+    }
+    __syncthreads();
+}
+
 // update steps, and clears the sums for the next step. red: blockDim doubles.
 template <int WPS>
 __device__ void finalize_block(const Model &m, const Buffers &b, long long n, int init, int prior_step,
-                               double *red)
+                               double *red, int scf_step = 0)
 {
     // other blocks updated the sums and scalars with atomics: read them from L2
     Scalars &sc = *b.sc;
@@ -1432,6 +1759,9 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
     __syncthreads();
     build_records(m, b);
     block_fold(red);
+    const double chi2 = red[0];
+    __syncthreads();
+    if (scf_step) scf_finalize<WPS>(m, b, s_ren, init, red);
     if (prior_step) {
         for (int c = threadIdx.x; c < m.ncell; c += blockDim.x) {
             const long long cnt = __ldcg(b.hist + m.off_count + c);
@@ -1448,14 +1778,14 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
         }
     }
     __syncthreads();
-    const int words = prior_step ? m.hist_words : m.off_grid;
+    const int words = (prior_step || scf_step) ? m.hist_words : m.off_grid;
     for (int k = threadIdx.x; k < words; k += blockDim.x) b.hist[k] = 0;
     if (threadIdx.x == 0) {
         // the integer sums wrap beyond their range: the floating-point check sum catches it
         if (!(__ldcg(&sc.Wcheck) <= 0.5 * __ldcg(&sc.Wrange))) atomicOr(&sc.err, kErrOverflow);
         sc.Wcheck = 0.0;
         sc.Wsum = U;
-        sc.chi2 = red[0];
+        sc.chi2 = chi2;
         if (!init) sc.t = t;
         sc.wscale = s_ren;
         sc.lwscale = log(s_ren);
@@ -1527,7 +1857,7 @@ __device__ __forceinline__ void global_add(long long *hist, int slot, float v, f
 // Per-step flags of one fit, read from its scalars at the start of the step.
 template <class T>
 struct StepFlags {
-    int pending, prior_step;
+    int pending, prior_step, scf_step;
     T wscale, lwscale, iwhat_flat;
 };
 
@@ -1538,6 +1868,8 @@ __device__ __forceinline__ StepFlags<T> step_flags(const Model &m, const Scalars
     const long long t = sc.t + 1;
     f.pending = init ? 0 : sc.pending;
     f.prior_step = !init && m.mode == 1 && ((t - 1) % m.update_every) == 0;
+    // the self-consistent potential is rebuilt at the load and on the prior schedule
+    f.scf_step = m.pot == 3 && (init || ((t - 1) % m.update_every) == 0);
     f.wscale = init ? T(1) : T(sc.wscale);
     f.lwscale = init ? T(0) : T(sc.lwscale);
     f.iwhat_flat = kLogWeights<T> ? T(sc.lwhat_flat) : (sc.what_flat > 0.0 ? T(1.0 / sc.what_flat) : T(0));
@@ -1587,7 +1919,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
     const bool cache = m.ap_cache != 0;
     const bool need_ap = cache && f.pending;
     const bool gxc = sizeof(T) == 8 && P.gx != nullptr;  // FP64, aperture cache, a Gauss-Hermite group
-    const bool need_fa = (kCacheAccel<T> || m.cache_accel) && push;
+    const bool need_fa = keeps_accel<T>(m) && push;
     T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0), ngx = T(0), nfa = T(0);
     int ncell = 0;
     unsigned nap = kApUncached;
@@ -1627,7 +1959,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             }
             u = w;
         }
-        if (kCacheAccel<T> || m.cache_accel) {
+        if (keeps_accel<T>(m)) {
             T fa;
             if (push) {
                 fa = fa_in;
@@ -1674,8 +2006,14 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                             }
                         },
                         gxc && g == m.gx_group ? &gout : nullptr);
+                    if (f.scf_step && m.n_dups > 0)  // derivatives for the mass-to-light ratio (Sec. 6)
+                        group_dkernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
+                            deposit(m.off_dups + j, v, cls == kClassVel ? k.fx_v2 : k.fx_dv);
+                        });
                 }
             });
+            if (f.scf_step)  // the particle's luminosity in the expansion of the stellar potential
+                scf_deposit(m, x, y, z, w, [&](int slot, T v) { deposit(slot, v, k.fx_gh); });
             if (cache) P.ap[i] = static_cast<uint16_t>(code_out);
             if (gxc) P.gx[i] = gout;
             wtot.add(w, k.fx_w);
@@ -1698,7 +2036,8 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
 // sums and scalars. Called by every thread of the block.
 template <class T, int WPS, bool GA>
 __device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, const Buffers &b, const Smem<T> &S,
-                                            int prior_step, unsigned err, const Total<T> &wtot, T wdep)
+                                            int prior_step, unsigned err, const Total<T> &wtot, T wdep,
+                                            int scf_step = 0)
 {
     if (err) atomicOr(&b.sc->err, err);
     // the total weight went into registers: one global atomic per warp and word
@@ -1723,7 +2062,7 @@ __device__ __forceinline__ void block_flush(const Model &m, const Cst<T> &k, con
             if (v != 0) red_add(b.hist + WPS * j + wd, v);
         }
     }
-    const int words = GA ? 0 : (prior_step ? m.hist_words : m.off_grid);
+    const int words = GA ? 0 : ((prior_step || scf_step) ? m.hist_words : m.off_grid);
     for (int q = threadIdx.x; q < words; q += blockDim.x) {
         if (q >= WPS * m.J && q < WPS * (m.J + 1)) continue;  // the total is already global
         const long long v = Acc<T>::word(S.h, m, q);
@@ -1757,14 +2096,14 @@ __global__ void __launch_bounds__(kStepMaxThreads<T, GA>, (GA && sizeof(T) == 4)
     T wdep = T(0);  // floating-point twin of wtot, for the fixed-point range check
     step_particles<T, GA, M0, M1, M2, M3>(m, k, P, b, S, f, push, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                                           P.n, (long long)gridDim.x * blockDim.x, err, wtot, wdep);
-    block_flush<T, WPS, GA>(m, k, b, S, f.prior_step, err, wtot, wdep);
+    block_flush<T, WPS, GA>(m, k, b, S, f.prior_step, err, wtot, wdep, f.scf_step);
     if (m.shard) return;  // the sums of all shards are added by the caller; k_finalize follows
     // last block to finish runs the finalize
     if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (am_last) {
         __threadfence();
-        finalize_block<WPS>(m, b, P.n, init, f.prior_step, reinterpret_cast<double *>(smem));
+        finalize_block<WPS>(m, b, P.n, init, f.prior_step, reinterpret_cast<double *>(smem), f.scf_step);
     }
 }
 
@@ -1801,7 +2140,7 @@ __global__ void k_finalize(const Model m, const Buffers b, int init)
         b.hist[m.hist_words] = 0;
     }
     __syncthreads();
-    finalize_block<WPS>(m, b, m.n_all, init, f.prior_step, reinterpret_cast<double *>(smem));
+    finalize_block<WPS>(m, b, m.n_all, init, f.prior_step, reinterpret_cast<double *>(smem), f.scf_step);
 }
 
 // ---------------------------------------------------------------- batched step kernel
@@ -1831,6 +2170,10 @@ struct BatchArgs {
     const int *seg_off;      // block b walks seg[seg_off[b] .. seg_off[b+1])
     const unsigned *nseg;    // per model: its number of segments
 };
+
+// the batched kernel copies Model and Cst<T> into shared memory in 8-byte words
+static_assert(sizeof(Model) % 8 == 0 && sizeof(Cst<float>) % 8 == 0 && sizeof(Cst<double>) % 8 == 0,
+              "descriptor copies need whole 8-byte words");
 
 template <class T, int WPS, int MINB, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
 __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a)
@@ -1874,12 +2217,12 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a)
         T wdep = T(0);
         step_particles<T, false, M0, M1, M2, M3>(m, k, P, b, S, f, 1, sg.begin + threadIdx.x, sg.end, blockDim.x,
                                                  err, wtot, wdep);
-        block_flush<T, WPS, false>(m, k, b, S, f.prior_step, err, wtot, wdep);
+        block_flush<T, WPS, false>(m, k, b, S, f.prior_step, err, wtot, wdep, f.scf_step);
         if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == a.nseg[cur] - 1;
         __syncthreads();
         if (am_last) {
             __threadfence();
-            finalize_block<WPS>(m, b, P.n, 0, f.prior_step, reinterpret_cast<double *>(smem));
+            finalize_block<WPS>(m, b, P.n, 0, f.prior_step, reinterpret_cast<double *>(smem), f.scf_step);
             cur = -1;  // the finalize used the shared memory: reload before the next segment
         }
     }
@@ -1979,7 +2322,10 @@ static __global__ void k_load_stats(const Model m, const Cst<double> k, const do
     unsigned flag = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double v2 = vx[i] * vx[i] + vy[i] * vy[i] + vz[i] * vz[i];
-        const double e = v2 + 2.0 * (potential<double>(m, k, x[i], y[i], z[i]) - m.phi_min);
+        // the self-consistent potential bounds only its halo here (its stellar well is added
+        // on the host)
+        const double pmin = m.pot == 3 ? m.v0 * m.v0 * log(m.r0) : m.phi_min;
+        const double e = v2 + 2.0 * (potential<double>(m, k, x[i], y[i], z[i]) - pmin);
         const double val = e > v2 ? e : v2;
         if (!isfinite(val) || !isfinite(x[i] + y[i] + z[i]) || !isfinite(w[i]) || w[i] < 0.0) flag = 1;
         else if (val > best) best = val;
