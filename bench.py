@@ -347,7 +347,9 @@ def run_batch(args):
                     block=fixed[0] if fixed else 0, blocks_per_sm=fixed[1] if fixed else 0)
     for wl, f in zip(wls, batch.fits):
         f.load(wl.model)
-    shape = tuple(fixed) if fixed else batch.autotune(steps=2)
+    if fixed and len(fixed) != 2:
+        raise SystemExit("--shape takes block,blocks_per_sm")
+    shape = (fixed[0], fixed[1], "library default") if fixed else batch.autotune(steps=2)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     every = wls[0].prior["update_every"]
 
@@ -661,7 +663,7 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="override the particle count (profiling)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default=None, help="override (profiling)")
     ap.add_argument("--fits", default=None, help="c5: comma-separated fit indices instead of all 96 (profiling)")
-    ap.add_argument("--shape", default=None, help="c5: block,blocks_per_sm,segment instead of the autotuner "
+    ap.add_argument("--shape", default=None, help="c5: block,blocks_per_sm instead of the autotuner "
                                                   "(profiling; the segment is the library default)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -433,6 +433,8 @@ static typename StepKernel<T>::Fn step_fn() { return k_step<T, WPS, kMinBlocks<T
 template <class T, int WPS, bool GA>
 static typename StepKernel<T>::Fn pick_step(const Model &m)
 {
+    // the self-consistent potential is compiled into the generic kernel only
+    if (m.pot == 3) return step_fn<T, WPS, GA, kDyn, kDyn, kDyn, kDyn>();
     unsigned mk[4] = {0, 0, 0, 0};
     for (int g = 0; g < m.n_groups; ++g) mk[g] = group_mask(m.g[g]);
     constexpr unsigned kin1 = kBitV2 | bit_gh(4), kin2 = kBitV2 | bit_gh(3) | bit_gh(4);

@@ -540,11 +540,16 @@ __device__ __forceinline__ void scf_accel(const Model &m, const Cst<T> &k, T x, 
     az = d_div(f * z, k.q2) - g[2];
 }
 
-template <class T>
+// SCF: whether the code of the self-consistent potential is compiled in (only the generic
+// step kernel and the helpers around it need it; the kernels specialised to an observable
+// shape run the other potentials without its registers).
+template <class T, bool SCF = true>
 __host__ __device__ __forceinline__ T potential(const Model &m, const Cst<T> &k, T x, T y, T z)
 {
 #ifdef __CUDA_ARCH__
-    if (m.pot == 3) return scf_potential(m, k, x, y, z);
+    if constexpr (SCF) {
+        if (m.pot == 3) return scf_potential(m, k, x, y, z);
+    }
 #endif
     if (m.pot == 2) {
         const T D = fma(x, x, fma(y, y, k.r0sq)) + d_div(z * z, k.q2);
@@ -610,14 +615,16 @@ __host__ __device__ __forceinline__ void accel_from(const Model &m, const Cst<T>
     az = -f * z;
 }
 
-template <class T>
+template <class T, bool SCF = true>
 __host__ __device__ __forceinline__ void accel(const Model &m, const Cst<T> &k, T x, T y, T z, T &ax, T &ay,
                                                T &az)
 {
 #ifdef __CUDA_ARCH__
-    if (m.pot == 3) {
-        scf_accel(m, k, x, y, z, ax, ay, az);
-        return;
+    if constexpr (SCF) {
+        if (m.pot == 3) {
+            scf_accel(m, k, x, y, z, ax, ay, az);
+            return;
+        }
     }
 #endif
     accel_from(m, k, accel_factor(m, k, x, y, z), x, y, z, ax, ay, az);
@@ -645,18 +652,18 @@ __device__ __forceinline__ void leapfrog_from(const Model &m, const Cst<T> &k, T
 }
 
 // One kick-drift-kick leap-frog step.
-template <class T>
+template <class T, bool SCF = true>
 __device__ __forceinline__ void leapfrog(const Model &m, const Cst<T> &k, T &x, T &y, T &z, T &vx, T &vy, T &vz)
 {
     T ax, ay, az;
-    accel(m, k, x, y, z, ax, ay, az);
+    accel<T, SCF>(m, k, x, y, z, ax, ay, az);
     vx = fma(k.hdt, ax, vx);
     vy = fma(k.hdt, ay, vy);
     vz = fma(k.hdt, az, vz);
     x = fma(k.dt, vx, x);
     y = fma(k.dt, vy, y);
     z = fma(k.dt, vz, z);
-    accel(m, k, x, y, z, ax, ay, az);
+    accel<T, SCF>(m, k, x, y, z, ax, ay, az);
     vx = fma(k.hdt, ax, vx);
     vy = fma(k.hdt, ay, vy);
     vz = fma(k.hdt, az, vz);
@@ -1109,14 +1116,14 @@ __device__ __forceinline__ void group_dkernels(const GroupDesc &G, const Tables<
 // spherical potentials without the square root of R^2 and with one logarithm for the
 // NFW halo (shared by its potential and its enclosed mass); the flattened log halo
 // through accel and potential.
-template <class T>
+template <class T, bool SCF = true>
 __host__ __device__ __forceinline__ void circ_terms(const Model &m, const Cst<T> &k, T R, T &vc2, T &phi)
 {
     if (m.pot >= 2) {
         T ax, ay, az;
-        accel(m, k, R, T(0), T(0), ax, ay, az);
+        accel<T, SCF>(m, k, R, T(0), T(0), ax, ay, az);
         vc2 = -R * ax;
-        phi = potential(m, k, R, T(0), T(0));
+        phi = potential<T, SCF>(m, k, R, T(0), T(0));
         return;
     }
     const T ra = R + k.a;
@@ -1142,18 +1149,18 @@ __host__ __device__ __forceinline__ void circ_terms(const Model &m, const Cst<T>
 }
 
 // Energy of the circular orbit of radius R in the equatorial plane: phi(R) + v_c^2/2.
-template <class T>
+template <class T, bool SCF = true>
 __host__ __device__ __forceinline__ T circ_energy(const Model &m, const Cst<T> &k, T R)
 {
     T vc2, phi;
-    circ_terms(m, k, R, vc2, phi);
+    circ_terms<T, SCF>(m, k, R, vc2, phi);
     return phi + T(0.5) * vc2;
 }
 
 // Lc(E): closed form for the Hernquist potential (E_c = -(u+1)/(2u^2) GM/a with
 // u = R/a + 1), otherwise the host table of E_c(ln R) bracketed by binary search,
 // interpolated, and refined by secant steps on E_c(R) = E.
-template <class T>
+template <class T, bool SCF = true>
 __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
 {
     if (m.pot < 2 && !(E < T(0))) return T(0);
@@ -1169,24 +1176,24 @@ __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
     const int n = m.lc_n;
     int lo = 0, hi = n - 1;
     T R;
-    if (m.pot == 3) {
+    if (SCF && m.pot == 3) {
         // The self-consistent potential need not be lowest at the centre (its l > 0 terms can
         // lower it off the axis), and its thin shells put kinks in E_c(R) at the grid radii,
         // so E_c(R) = E may have no root below phi(0) and is not smooth: Lc(E) by plain
         // bisection, from [0, 1] doubled until it brackets the root (no circular orbit
         // below E_c(0) = phi(0)).
-        if (!(E > circ_energy(m, k, T(0)))) return T(0);
+        if (!(E > circ_energy<T, SCF>(m, k, T(0)))) return T(0);
         T hi = T(1), lo = T(0);
-        while (hi < T(1e15) && circ_energy(m, k, hi) <= E) hi *= T(2);
+        while (hi < T(1e15) && circ_energy<T, SCF>(m, k, hi) <= E) hi *= T(2);
         for (int it = 0; it < 400; ++it) {
             const T mid = T(0.5) * (lo + hi);
             if (!(mid > lo) || !(mid < hi)) break;
-            if (circ_energy(m, k, mid) <= E) lo = mid;
+            if (circ_energy<T, SCF>(m, k, mid) <= E) lo = mid;
             else hi = mid;
         }
         R = T(0.5) * (lo + hi);
         T vc2, phi;
-        circ_terms(m, k, R, vc2, phi);
+        circ_terms<T, SCF>(m, k, R, vc2, phi);
         return R * d_sqrt(vc2);
     }
     if (!(E > T(__ldg(lcE)))) {
@@ -1227,10 +1234,10 @@ __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
             // secant refinement, starting from the table segment's slope
             const T Ra = d_exp(k.lc_lnr0 + T(lo) * k.lc_dlnr);
             const T Rb = d_exp(k.lc_lnr0 + T(hi) * k.lc_dlnr);
-            T r0 = R, f0 = circ_energy(m, k, r0) - E;
+            T r0 = R, f0 = circ_energy<T, SCF>(m, k, r0) - E;
             T r1 = r0 - f0 * d_div(Rb - Ra, e1 - e0);
             for (int it = 0; it < 3; ++it) {
-                const T f1 = circ_energy(m, k, r1) - E;
+                const T f1 = circ_energy<T, SCF>(m, k, r1) - E;
                 if (f1 == f0) break;
                 const T r2 = r1 - f1 * d_div(r1 - r0, f1 - f0);
                 r0 = r1;
@@ -1241,17 +1248,17 @@ __device__ T circular_L(const Model &m, const Cst<T> &k, const double *lcE, T E)
         }
     }
     T vc2, phi;
-    circ_terms(m, k, R, vc2, phi);
+    circ_terms<T, SCF>(m, k, R, vc2, phi);
     return R * d_sqrt(vc2);
 }
 
 // Cell k*nx + l of a particle: E bin from the chosen spacing (clamped), circularity
 // bin from x = L/Lc(E) (x = Lz/Lc(E) on [-1, 1] for the signed variant, clamped).
-template <class T>
+template <class T, bool SCF = true>
 __device__ __forceinline__ int prior_cell(const Model &m, const Cst<T> &k, const double *lcE, T x, T y, T z,
                                           T vx, T vy, T vz)
 {
-    const T E = fma(T(0.5), fma(vx, vx, fma(vy, vy, vz * vz)), potential(m, k, x, y, z));
+    const T E = fma(T(0.5), fma(vx, vx, fma(vy, vy, vz * vz)), potential<T, SCF>(m, k, x, y, z));
     const T Lz = fma(x, vy, -(y * vx));
     T L;
     if (m.signed_lz) {
@@ -1260,7 +1267,7 @@ __device__ __forceinline__ int prior_cell(const Model &m, const Cst<T> &k, const
         const T Lx = fma(y, vz, -(z * vy)), Ly = fma(z, vx, -(x * vz));
         L = d_sqrt(fma(Lx, Lx, fma(Ly, Ly, Lz * Lz)));
     }
-    const T Lc = circular_L(m, k, lcE, E);
+    const T Lc = circular_L<T, SCF>(m, k, lcE, E);
     T xc = (Lc > T(0)) ? d_div(L, Lc) : T(0);
     const T xmin = m.signed_lz ? T(-1) : T(0);
     xc = xc < xmin ? xmin : (xc > T(1) ? T(1) : xc);
@@ -1908,6 +1915,8 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                                                const Smem<T> &S, const StepFlags<T> &f, int push, long long i0,
                                                long long i1, long long stride, unsigned &err, Total<T> &wtot, T &wdep)
 {
+    // the self-consistent potential runs in the generic kernel only (the host picks it)
+    constexpr bool kScf = M0 == kDyn;
     const Tables<T> tb{S.esq, S.lut, GA ? global_vp<T>(b) : S.vp, GA ? global_isp<T>(b) : S.isp, S.e2};
     const T *rec = GA ? global_records<T>(b) : S.c;
     auto deposit = [&](int slot, T v, T scale) {
@@ -1969,7 +1978,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
             }
             P.fa[i] = fa;
         } else {
-            if (push) leapfrog(m, k, x, y, z, vx, vy, vz);
+            if (push) leapfrog<T, kScf>(m, k, x, y, z, vx, vy, vz);
         }
         if (!is_zero(w)) {
             T Y, vlos;
@@ -2006,21 +2015,25 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                             }
                         },
                         gxc && g == m.gx_group ? &gout : nullptr);
-                    if (f.scf_step && m.n_dups > 0)  // derivatives for the mass-to-light ratio (Sec. 6)
-                        group_dkernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
-                            deposit(m.off_dups + j, v, cls == kClassVel ? k.fx_v2 : k.fx_dv);
-                        });
+                    if constexpr (kScf) {
+                        if (f.scf_step && m.n_dups > 0)  // derivatives for the mass-to-light ratio (Sec. 6)
+                            group_dkernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
+                                deposit(m.off_dups + j, v, cls == kClassVel ? k.fx_v2 : k.fx_dv);
+                            });
+                    }
                 }
             });
-            if (f.scf_step)  // the particle's luminosity in the expansion of the stellar potential
-                scf_deposit(m, x, y, z, w, [&](int slot, T v) { deposit(slot, v, k.fx_gh); });
+            if constexpr (kScf) {
+                if (f.scf_step)  // the particle's luminosity in the expansion of the stellar potential
+                    scf_deposit(m, x, y, z, w, [&](int slot, T v) { deposit(slot, v, k.fx_gh); });
+            }
             if (cache) P.ap[i] = static_cast<uint16_t>(code_out);
             if (gxc) P.gx[i] = gout;
             wtot.add(w, k.fx_w);
             wdep += w;
         }
         if (f.prior_step) {
-            const int c = prior_cell(m, k, b.lcE, x, y, z, vx, vy, vz);
+            const int c = prior_cell<T, kScf>(m, k, b.lcE, x, y, z, vx, vy, vz);
             deposit(m.J + 1 + c, w, k.fx_w);
             if constexpr (GA) red_add(b.hist + m.off_count + c, 1);
             else Acc<T>::count(S.h, m, c);
