@@ -74,7 +74,8 @@ class Obs(C.Structure):
 class Prior(C.Structure):
     _fields_ = [("mode", C.c_int), ("nE", C.c_int), ("nx", C.c_int), ("e_spacing", C.c_int),
                 ("signed_lz", C.c_int), ("update_every", C.c_int), ("Emin", C.c_double),
-                ("Emax", C.c_double), ("smoothing", C.c_int), ("lam", C.c_double)]
+                ("Emax", C.c_double), ("smoothing", C.c_int), ("lam", C.c_double),
+                ("window_E", C.c_int), ("window_x", C.c_int)]
 
 
 class Params(C.Structure):
@@ -130,6 +131,7 @@ def lib():
                               C.POINTER(State)]
         L.or_run.argtypes = [C.POINTER(Potential), C.POINTER(Obs), _DP, _DP, C.POINTER(Prior),
                              C.POINTER(Params), C.POINTER(Particles), C.POINTER(State), C.c_long]
+        L.or_window_means.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _DP, C.POINTER(C.c_long), _DP]
         L.or_smooth_penalty.argtypes = [C.c_int, C.c_int, _DP]
         L.or_smooth_grid.argtypes = [C.c_int, C.c_int, _DP, C.c_double, _DP, _DP]
         L.or_smooth_grid.restype = C.c_int
@@ -243,8 +245,10 @@ class ObsSet:
 
 
 def prior(d: dict) -> Prior:
+    wE, wx = d.get("window", (0, 0))
     return Prior(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
-                 d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)), float(d.get("lambda", 0.0)))
+                 d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)), float(d.get("lambda", 0.0)),
+                 int(wE), int(wx))
 
 
 def params(d: dict) -> Params:
@@ -414,6 +418,16 @@ class Run:
         return lib().or_force(C.byref(self.obs.o), C.byref(self.par), self.G.mode, a["w"][i],
                               self.what[i], a["x"][i], a["y"][i], a["z"][i], a["vx"][i],
                               a["vy"][i], a["vz"][i], _dp(self.delta), _dp(self.sig))
+
+
+def window_means(wsum, count, hE: int, hx: int) -> np.ndarray:
+    """Moving-window means of a (nE, nx) grid of weight sums and counts (or_window_means)."""
+    wsum = np.ascontiguousarray(wsum, np.float64)
+    count = np.ascontiguousarray(count, np.int64)
+    nE, nx = wsum.shape
+    out = np.zeros((nE, nx))
+    lib().or_window_means(nE, nx, hE, hx, _dp(wsum), count.ctypes.data_as(C.POINTER(C.c_long)), _dp(out))
+    return out
 
 
 def smooth_penalty(nE: int, nx: int) -> np.ndarray:

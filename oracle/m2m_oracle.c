@@ -612,6 +612,23 @@ static void residuals(int J, const double *Y, const double *sig, or_state *st)
     st->chi2 = c2;
 }
 
+void or_window_means(int nE, int nx, int hE, int hx, const double *sum, const long *count,
+                     double *mean)
+{
+    for (int k = 0; k < nE; ++k)
+        for (int l = 0; l < nx; ++l) {
+            double ws = 0.0;
+            long nc = 0;
+            for (int k2 = k - hE; k2 <= k + hE; ++k2)
+                for (int l2 = l - hx; l2 <= l + hx; ++l2) {
+                    if (k2 < 0 || k2 >= nE || l2 < 0 || l2 >= nx) continue;
+                    ws += sum[k2 * nx + l2];
+                    nc += count[k2 * nx + l2];
+                }
+            mean[k * nx + l] = nc > 0 ? ws / (double)nc : 0.0;
+        }
+}
+
 void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior *g,
              const or_particles *s, or_state *st)
 {
@@ -647,6 +664,11 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
         gsum = (double *)malloc(sizeof(double) * (size_t)ncell);
         if (!gsum) return OR_EARG;
     }
+    if (g->mode == OR_MPR && (g->window_E < 0 || g->window_x < 0 ||
+                              (g->smoothing && (g->window_E > 0 || g->window_x > 0)))) {
+        free(gsum);
+        return OR_EARG;
+    }
     int status = OR_OK;
     double *D = NULL;
     if (p->kind == OR_POT_SCF) {
@@ -681,8 +703,10 @@ int or_run(const or_potential *p, const or_obs *o, const double *Y, const double
                 gsum[c] += s->w[i];
                 st->grid_count[c] += 1;
             }
-            for (int c = 0; c < ncell; ++c)
-                st->grid_mean[c] = st->grid_count[c] > 0 ? gsum[c] / (double)st->grid_count[c] : 0.0;
+            /* Sec. 2.3.1: the mean weight of the cell; Sec. 7 (grid-less variant): the mean
+             * weight of the particles in the window of cells centred on the particle's own */
+            or_window_means(g->nE, g->nx, g->window_E, g->window_x, gsum, st->grid_count,
+                            st->grid_mean);
             if (g->smoothing) {
                 /* Sec. 2.3.2: the priors are the spline fit of the grid of cell means */
                 if (st->grid_raw)

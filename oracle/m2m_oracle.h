@@ -81,6 +81,8 @@ typedef struct {
     double Emin, Emax;
     int smoothing;      /* 0: raw cell means; 1: penalised spline fit of the grid (Sec. 2.3.2) */
     double lambda;      /* smoothing weight; <= 0: chosen by generalized cross validation */
+    int window_E, window_x; /* grid-less variant (Sec. 7): half widths, in cells, of the window
+                               centred on each particle's cell; 0, 0: the cell means */
 } or_prior;
 
 typedef struct {
@@ -162,6 +164,12 @@ void or_init(const or_obs *o, const double *Y, const double *sig, const or_prior
              const or_particles *s, or_state *st);
 int or_run(const or_potential *p, const or_obs *o, const double *Y, const double *sig,
            const or_prior *g, const or_params *par, or_particles *s, or_state *st, long nsteps);
+/* Moving-window means (the grid-less cumulative variant of Sec. 7): for every cell (k, l) the
+ * summed weight of the cells (k', l') with |k'-k| <= hE, |l'-l| <= hx (cut at the grid's edges)
+ * over their summed particle count; 0 where that count is 0. hE = hx = 0 gives the cell means
+ * of Sec. 2.3.1. */
+void or_window_means(int nE, int nx, int hE, int hx, const double *sum, const long *count,
+                     double *mean);
 /* Finite-difference penalty of the prior grid (Sec. 2.3.2, eq. smooth_grid): P such that
  * f.P.f = sum of (f_EE)^2 + 2 (f_Ex)^2 + (f_xx)^2 with second differences in units of one
  * bin, f_EE at cells 1..nE-2 of each column, f_xx at cells 1..nx-2 of each row, f_Ex at the
