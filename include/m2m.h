@@ -177,6 +177,15 @@ typedef struct {
                                       spline fit of the grid of cell means (Sec. 2.3.2, eq. smooth_grid) */
     double lambda;                 /* smoothing weight; 0: chosen at every update by generalized cross
                                       validation (golden-section search of log10 lambda in [-4, 6]) */
+    int32_t window_E, window_x;    /* grid-less variant (Sec. 7 outlook): >= 0 half widths in cells.
+                                      The prior of a particle in cell (k, l) is the mean weight of
+                                      the particles in the cells |k'-k| <= window_E, |l'-l| <=
+                                      window_x (cut at the grid's edges): a window centred on the
+                                      particle's own cell instead of a fixed cell, which tends to
+                                      the grid-less window mean as the grid is refined at a fixed
+                                      window width. The window sums come from cumulative sums of
+                                      the exact integer cell sums. 0, 0: the cell mean of Sec.
+                                      2.3.1. Excludes smoothing. */
 } m2m_prior_grid;
 
 /* Prior smoothing (Sec. 2.3.2): f minimises |y - f|^2 + lambda sum_cells (f_EE^2 + 2 f_Ex^2

@@ -71,7 +71,8 @@ class Observables(C.Structure):
 class PriorGrid(C.Structure):
     _fields_ = [("mode", C.c_int32), ("nE", C.c_int32), ("nx", C.c_int32), ("e_spacing", C.c_int32),
                 ("signed_lz", C.c_int32), ("update_every", C.c_int32), ("Emin", C.c_double),
-                ("Emax", C.c_double), ("smoothing", C.c_int32), ("lam", C.c_double)]
+                ("Emax", C.c_double), ("smoothing", C.c_int32), ("lam", C.c_double),
+                ("window_E", C.c_int32), ("window_x", C.c_int32)]
 
 
 DEPOSIT = {"auto": 0, "shared": 1, "global": 2}
@@ -283,7 +284,7 @@ def weight_rms(wdev2, counts, min_count: int = 50) -> float:
 def prior_grid(d: dict) -> PriorGrid:
     return PriorGrid(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
                      d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)),
-                     float(d.get("lambda", 0.0)))
+                     float(d.get("lambda", 0.0)), *(int(v) for v in d.get("window", (0, 0))))
 
 
 def _soa(p: dict, keys):

@@ -336,6 +336,11 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     }
     m.smooth = pg->smoothing;
     m.smooth_lambda = pg->lambda;
+    m.pwin_E = m.mode == M2M_REG_MPR ? pg->window_E : 0;
+    m.pwin_x = m.mode == M2M_REG_MPR ? pg->window_x : 0;
+    if (m.pwin_E < 0 || m.pwin_x < 0) return fail(ctx, M2M_ERR_ARG, "prior window half widths must be >= 0");
+    if ((m.pwin_E > 0 || m.pwin_x > 0) && pg->smoothing != M2M_SMOOTH_NONE)
+        return fail(ctx, M2M_ERR_ARG, "the prior window and prior smoothing exclude each other");
     m.win_group = -1;
     m.win_lo = m.win_n = 0;
     if (m.smooth != M2M_SMOOTH_NONE) {
@@ -414,6 +419,8 @@ static m2m_status build_model(m2m_ctx *ctx, const m2m_potential *pot, const m2m_
     h = fnv(h, &ctx->precision, sizeof(int));
     h = fnv(h, &m.smooth, sizeof(int));
     h = fnv(h, &m.smooth_lambda, sizeof(double));
+    h = fnv(h, &m.pwin_E, sizeof(int));
+    h = fnv(h, &m.pwin_x, sizeof(int));
     ctx->config_hash = h;
     return M2M_OK;
 }
@@ -581,6 +588,7 @@ static m2m_status upload_tables(m2m_ctx *ctx)
     CU(cudaMemset(ctx->d_lprior, 0, sizeof(double) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_prior_count, sizeof(long long) * (m.ncell + 1)));
     CU(cudaMalloc(&ctx->d_hist, sizeof(long long) * exchange_words(ctx)));
+    if (m.pwin_E > 0 || m.pwin_x > 0) CU(cudaMalloc(&ctx->d_pwin, sizeof(unsigned long long) * 3 * m.ncell));
     CU(cudaMalloc(&ctx->d_acc, sizeof(long long) * 2));
     CU(cudaMalloc(&ctx->d_sc, sizeof(Scalars)));
     CU(cudaMemset(ctx->d_c, 0, sizeof(double) * m.J));
@@ -664,7 +672,7 @@ Buffers buffers(m2m_ctx *c)
     b.Y = c->d_Y; b.sig = c->d_sig; b.obs_kind = c->d_kind; b.obs_post = c->d_post; b.obs_iscale = c->d_iscale;
     b.c = c->d_c; b.rec = c->d_rec; b.recf = c->d_recf; b.prior = c->d_prior; b.iprior = c->d_iprior;
     b.lprior = c->d_lprior; b.prior_count = c->d_prior_count; b.hist = c->d_hist;
-    b.prior_raw = c->d_prior_raw; b.sV = c->d_sV; b.sVT = c->d_sVT; b.sD = c->d_sD;
+    b.prior_raw = c->d_prior_raw; b.pwin = c->d_pwin; b.sV = c->d_sV; b.sVT = c->d_sVT; b.sD = c->d_sD;
     b.spart = c->d_spart; b.sz = c->d_sz; b.ss = c->d_ss;
     b.ytil = c->d_ytil; b.yraw = c->d_yraw; b.delta = c->d_delta; b.sc = c->d_sc;
     return b;
@@ -1755,7 +1763,7 @@ void destroy_impl(m2m_ctx *ctx)
     free_dev(ctx->d_kind); free_dev(ctx->d_c); free_dev(ctx->d_rec); free_dev(ctx->d_recf); free_dev(ctx->d_prior); free_dev(ctx->d_iprior); free_dev(ctx->d_lprior);
     free_dev(ctx->d_ytil);
     free_dev(ctx->d_yraw); free_dev(ctx->d_delta); free_dev(ctx->d_prior_count);
-    free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc);
+    free_dev(ctx->d_hist); free_dev(ctx->d_acc); free_dev(ctx->d_sc); free_dev(ctx->d_pwin);
     smooth_free(ctx);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;

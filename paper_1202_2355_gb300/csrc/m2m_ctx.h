@@ -46,6 +46,7 @@ struct m2m_ctx {
     double *d_rec = nullptr, *d_iprior = nullptr, *d_lprior = nullptr;
     float *d_recf = nullptr;
     long long *d_prior_count = nullptr, *d_hist = nullptr, *d_acc = nullptr;
+    unsigned long long *d_pwin = nullptr;  // window priors: cumulative-sum scratch
     // prior smoothing (m2m_smooth.cu)
     double *d_prior_raw = nullptr, *d_sV = nullptr, *d_sVT = nullptr, *d_sD = nullptr;
     double *d_spart = nullptr, *d_sz = nullptr, *d_ss = nullptr;

@@ -93,6 +93,9 @@ struct Model {
     // prior smoothing (Sec. 2.3.2): 0 off; lambda > 0 fixed, else chosen by GCV
     int smooth;
     double smooth_lambda;
+    // grid-less moving priors (Sec. 7): half widths, in cells, of the window of cells
+    // centred on each cell whose particles' mean weight is its prior; 0, 0: the cell mean
+    int pwin_E, pwin_x;
     // global-deposit kernel: apertures [win_lo, win_lo + win_n) of group win_group keep
     // block-shared sums (the densest range, placed at load); the rest deposit globally
     int win_group, win_lo, win_n;
@@ -290,6 +293,7 @@ struct Buffers {
     double *lprior;                  // per cell: ln prior (-inf when the prior reads as 0)
     long long *prior_count;          // per cell: particle count at the last update
     double *prior_raw;               // per cell: raw cell mean before smoothing (smoothing on)
+    unsigned long long *pwin;        // window priors: (WPS + 1) x ncell words of cumulative sums
     const double *sV, *sVT, *sD;     // smoothing: eigenvectors of the grid penalty (V, V^T) and eigenvalues
     double *spart, *sz, *ss;         // smoothing scratch: chunk partial sums, V^T y, smoothed coefficients
     long long *hist;                 // global fixed-point sums
@@ -1733,6 +1737,66 @@ __device__ void scf_finalize(const Model &m, const Buffers &b, double s_ren, int
 }
 
 // update steps, and clears the sums for the next step. red: blockDim doubles.
+// Priors of the grid-less variant (Sec. 7): the mean weight of the particles in the window of
+// cells |k' - k| <= pwin_E, |l' - l| <= pwin_x around each cell (k, l), cut at the grid's
+// edges. The window sums come from cumulative sums of the cells' integer words, first along
+// x (into pwin), then, after the row windows are written back over the cell words, along E,
+// so they equal the sums of the particles' own words in any order. q = 0 is the particle
+// count, q = 1..WPS the words of the weight sum; all unsigned, wrapping like the deposits.
+template <int WPS>
+__device__ void window_priors(const Model &m, const Buffers &b, double s_ren)
+{
+    constexpr int NQ = WPS + 1;
+    const int nE = m.nE, nx = m.nx, nc = m.ncell, hE = m.pwin_E, hx = m.pwin_x;
+    unsigned long long *H = reinterpret_cast<unsigned long long *>(b.hist);
+    unsigned long long *cum = b.pwin;
+    auto at = [&](int q, int c) -> unsigned long long * {
+        return q == 0 ? H + m.off_count + c : H + WPS * (m.J + 1 + c) + (q - 1);
+    };
+    for (int r = threadIdx.x; r < nE * NQ; r += blockDim.x) {  // cumulative sums along x
+        const int k = r / NQ, q = r % NQ;
+        unsigned long long acc = 0;
+        for (int l = 0; l < nx; ++l) {
+            const unsigned long long v = __ldcg(at(q, k * nx + l));
+            if (q == 0) b.prior_count[k * nx + l] = (long long)v;
+            acc += v;
+            cum[size_t(q) * nc + k * nx + l] = acc;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nc * NQ; r += blockDim.x) {  // row windows over the cell words
+        const int q = r / nc, c = r % nc, k = c / nx, l = c % nx;
+        const unsigned long long *row = cum + size_t(q) * nc + k * nx;
+        *at(q, c) = __ldcg(row + min(l + hx, nx - 1)) - (l - hx - 1 >= 0 ? __ldcg(row + l - hx - 1) : 0ull);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nx * NQ; r += blockDim.x) {  // cumulative sums along E
+        const int l = r / NQ, q = r % NQ;
+        unsigned long long acc = 0;
+        for (int k = 0; k < nE; ++k) {
+            acc += __ldcg(at(q, k * nx + l));
+            cum[size_t(q) * nc + k * nx + l] = acc;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const int k = c / nx, l = c % nx, hi = min(k + hE, nE - 1), lo = k - hE - 1;
+        unsigned long long box[NQ];
+        for (int q = 0; q < NQ; ++q) {
+            const unsigned long long *col = cum + size_t(q) * nc + l;
+            box[q] = __ldcg(col + size_t(hi) * nx) - (lo >= 0 ? __ldcg(col + size_t(lo) * nx) : 0ull);
+        }
+        const long long cnt = (long long)box[0];
+        double sum = double((long long)box[1]);
+        if (WPS == 2) sum += double((long long)box[2]) * (1.0 / 4294967296.0);
+        sum = sum / m.fx_w * s_ren;
+        const double pr = cnt > 0 ? sum / double(cnt) : 0.0;
+        b.prior[c] = pr;
+        b.iprior[c] = pr > 0.0 ? 1.0 / pr : 0.0;
+        b.lprior[c] = pr > 0.0 ? log(pr) : -HUGE_VAL;
+    }
+}
+
 template <int WPS>
 __device__ void finalize_block(const Model &m, const Buffers &b, long long n, int init, int prior_step,
                                double *red, int scf_step = 0)
@@ -1769,7 +1833,9 @@ __device__ void finalize_block(const Model &m, const Buffers &b, long long n, in
     const double chi2 = red[0];
     __syncthreads();
     if (scf_step) scf_finalize<WPS>(m, b, s_ren, init, red);
-    if (prior_step) {
+    if (prior_step && (m.pwin_E > 0 || m.pwin_x > 0)) {
+        window_priors<WPS>(m, b, s_ren);
+    } else if (prior_step) {
         for (int c = threadIdx.x; c < m.ncell; c += blockDim.x) {
             const long long cnt = __ldcg(b.hist + m.off_count + c);
             const double sum = fx_read<WPS>(b.hist, m.J + 1 + c) / m.fx_w * s_ren;
