@@ -11,7 +11,10 @@ a range of regularisation weights mu. Each final model is assessed by
 - the rms of the weights about their cell means (Sec. 5, Fig. res).
 The paper finds that MPR reaches lower Delta_grid and Delta_kin than GWR at a comparable
 fit, because its entropy pulls weights towards their cell's mean instead of towards the
-initial model.
+initial model. Mode "mprw" is the grid-less variant of Sec. 7: the prior of a particle is
+the mean weight in a window of cells of a finer lattice centred on its own cell (by default
+a 90 x 30 lattice with half widths 1, 1: a window of one 30 x 10 cell that moves in thirds
+of a cell); Delta_grid is still taken on the 30 x 10 grid.
 
 Synthetic stand-in for the paper's truncated target: a Hernquist sphere with constant
 anisotropy sigma_r/sigma_t = 1.5 (beta = 5/9) in Jeans equilibrium, Gaussian velocities;
@@ -64,12 +67,16 @@ def assess(fit: B.Fit, wl: W.Workload, target_grid, target_kin, min_count: int =
                 weight_rms_rel=B.weight_rms(wd, cm, 50) * fit.n / max(wm.sum(), 1e-300))
 
 
-def scan(n: int, n_target: int, steps: int, mus, precision: str = "mixed"):
+def scan(n: int, n_target: int, steps: int, mus, precision: str = "mixed", modes=("gwr", "mpr"),
+         lattice=(90, 30), window=(1, 1)):
     wl = workload(n, n_target)
     Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
-    for mode in ("initial", "gwr", "mpr"):
+    for mode in ("initial",) + tuple(modes):
         for mu in ([0.0] if mode == "initial" else mus):
-            prior = dict(wl.prior, mode="gwr" if mode == "initial" else mode)
+            if mode == "mprw":
+                prior = dict(wl.prior, mode="mpr", nE=lattice[0], nx=lattice[1], window=window)
+            else:
+                prior = dict(wl.prior, mode="gwr" if mode == "initial" else mode)
             fit = B.fit_from_workload(wl, Y, sig, Vp, sp, precision=precision, prior=prior,
                                       params=dict(wl.params, mu=mu))
             fit.load(wl.model)
@@ -94,10 +101,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--mu", default="0.01,0.1,1,10,100,1000")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--modes", default="gwr,mpr", help="any of gwr, mpr, mprw (grid-less window priors)")
+    ap.add_argument("--lattice", default="90,30", help="mprw: nE,nx of the prior lattice")
+    ap.add_argument("--window", default="1,1", help="mprw: half widths of the window, in lattice cells")
     a = ap.parse_args()
     mus = [float(x) for x in a.mu.split(",")]
+    lattice = tuple(int(v) for v in a.lattice.split(","))
+    window = tuple(int(v) for v in a.window.split(","))
     print(f"{'mode':8s} {'mu':>8s} {'chi2/J':>8s} {'D_grid':>8s} {'D_kin':>8s} {'rms w/w0':>9s}")
-    for r in scan(a.n, a.n_target, a.steps, mus, a.precision):
+    for r in scan(a.n, a.n_target, a.steps, mus, a.precision, tuple(a.modes.split(",")), lattice, window):
         print(f"{r['mode']:8s} {r['mu']:8.3g} {r['chi2_per_J']:8.3f} {r['delta_grid']:8.4f} "
               f"{r['delta_kin']:8.4f} {r['weight_rms_rel']:9.4f}  " + json.dumps(r), flush=True)
 
