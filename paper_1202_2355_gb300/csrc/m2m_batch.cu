@@ -25,6 +25,8 @@ struct BatchState {
     long long seg_cap = kMaxParticlesPerBlock;
     size_t smem = 0;
     void *kernel = nullptr;  // the k_step_batch instantiation for the fits' observable shape
+    bool bank = false;       // the kernel reads the fits' constants from its parameter bank
+    std::vector<unsigned char> h_bank;  // BatchBank<T> passed at every launch
     Model *d_models = nullptr;
     void *d_csts = nullptr, *d_states = nullptr;
     Buffers *d_bufs = nullptr;
@@ -42,16 +44,52 @@ static const int kBatchGraphSteps = 16;
 // ------------------------------------------------------------------ kernel choice
 
 template <class T, int WPS, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-static void *batch_fn()
+static void *batch_fn(bool bank)
 {
-    return reinterpret_cast<void *>(k_step_batch<T, WPS, kMinBlocksBatch<T>, M0, M1, M2, M3>);
+    if (bank) return reinterpret_cast<void *>(k_step_batch<T, WPS, kMinBlocksBatch<T>, true, M0, M1, M2, M3>);
+    return reinterpret_cast<void *>(k_step_batch<T, WPS, kMinBlocksBatch<T>, false, M0, M1, M2, M3>);
+}
+
+template <class T>
+using BatchFn = void (*)(const BatchArgs<T>, const BatchBank<T>);
+
+static bool group_hot_equal(const GroupDesc &a, const GroupDesc &b)
+{
+    bool eq = a.geometry == b.geometry && a.n_ap == b.n_ap && a.n_kinds == b.n_kinds && a.obs_off == b.obs_off &&
+              a.ap_off == b.ap_off && a.edge_off == b.edge_off && a.max_gh == b.max_gh && a.has_v2 == b.has_v2 &&
+              a.nx == b.nx && a.ny == b.ny && a.xlo == b.xlo && a.ylo == b.ylo && a.xw == b.xw && a.yw == b.yw &&
+              a.xlo_f == b.xlo_f && a.ylo_f == b.ylo_f && a.ixw == b.ixw && a.iyw == b.iyw && a.lut_off == b.lut_off &&
+              a.lut_n == b.lut_n && a.l0 == b.l0 && a.lscale == b.lscale && a.e0sq_f == b.e0sq_f &&
+              a.ensq_f == b.ensq_f && a.lut_identity == b.lut_identity && a.k_mass == b.k_mass && a.k_v2 == b.k_v2 &&
+              a.k_v1 == b.k_v1;
+    for (int n = 0; eq && n < 7; ++n) eq = a.k_gh[n] == b.k_gh[n];
+    for (int q = 0; eq && q < a.n_kinds; ++q)
+        eq = a.kinds[q] == b.kinds[q] && a.alm_l[q] == b.alm_l[q] && a.alm_m[q] == b.alm_m[q] &&
+             a.alm_norm[q] == b.alm_norm[q] && a.alm_norm_f[q] == b.alm_norm_f[q];
+    return eq;
+}
+
+// Whether two fits agree in every Model field that the per-particle path reads (the
+// fields step_particles takes from its shape Model); the rest differ freely.
+static bool hot_equal(const Model &a, const Model &b)
+{
+    bool eq = a.pot == b.pot && a.mode == b.mode && a.update_rule == b.update_rule && a.ap_cache == b.ap_cache &&
+              a.cache_accel == b.cache_accel && a.gx_group == b.gx_group && a.J == b.J && a.nslots == b.nslots &&
+              a.off_count == b.off_count && a.rec_len == b.rec_len && a.n_groups == b.n_groups &&
+              a.win_group == b.win_group && a.win_lo == b.win_lo && a.win_n == b.win_n && a.n_dups == b.n_dups &&
+              a.off_dups == b.off_dups;
+    for (int g = 0; eq && g < a.n_groups; ++g) eq = group_hot_equal(a.g[g], b.g[g]);
+    return eq;
 }
 
 // The specialised kernel when every fit has the same observable shape and it is
-// one of the compiled ones, else the generic one.
+// one of the compiled ones, else the generic one; from the parameter bank when the
+// fits fit in it and share the per-particle fields.
 template <class T, int WPS>
-static void *batch_pick(const std::vector<m2m_ctx *> &sub)
+static void *batch_pick(const std::vector<m2m_ctx *> &sub, bool &bank)
 {
+    bank = int(sub.size()) <= kBankFits<T>;
+    for (const m2m_ctx *c : sub) bank = bank && hot_equal(sub[0]->m, c->m);
     const Model &m0 = sub[0]->m;
     unsigned mk[4] = {0, 0, 0, 0};
     for (int g = 0; g < m0.n_groups; ++g) mk[g] = group_mask(m0.g[g]);
@@ -63,10 +101,12 @@ static void *batch_pick(const std::vector<m2m_ctx *> &sub)
     }
     constexpr unsigned kin1 = kBitV2 | bit_gh(4), kin2 = kBitV2 | bit_gh(3) | bit_gh(4);
     constexpr unsigned map = kBitPix | kBitMass | bit_gh(1) | bit_gh(2) | bit_gh(3) | bit_gh(4);
-    if (same && m0.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin1) return batch_fn<T, WPS, kBitMass, kin1, 0u, 0u>();
-    if (same && m0.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin2) return batch_fn<T, WPS, kBitMass, kin2, 0u, 0u>();
-    if (same && m0.n_groups == 1 && mk[0] == map) return batch_fn<T, WPS, map, 0u, 0u, 0u>();
-    return batch_fn<T, WPS, kDyn, kDyn, kDyn, kDyn>();
+    if (same && m0.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin1)
+        return batch_fn<T, WPS, kBitMass, kin1, 0u, 0u>(bank);
+    if (same && m0.n_groups == 2 && mk[0] == kBitMass && mk[1] == kin2)
+        return batch_fn<T, WPS, kBitMass, kin2, 0u, 0u>(bank);
+    if (same && m0.n_groups == 1 && mk[0] == map) return batch_fn<T, WPS, map, 0u, 0u, 0u>(bank);
+    return batch_fn<T, WPS, kDyn, kDyn, kDyn, kDyn>(bank);
 }
 
 // ------------------------------------------------------------------ segments
@@ -177,6 +217,12 @@ static m2m_status batch_prepare(m2m_ctx *ctx)
     m2m_status s;
     if ((s = upload(ctx, B.d_models, models.data(), sizeof(Model) * M)) != M2M_OK) return s;
     if ((s = upload(ctx, B.d_csts, csts.data(), sizeof(Cst<T>) * M)) != M2M_OK) return s;
+    B.h_bank.assign(sizeof(BatchBank<T>), 0);
+    if (B.bank) {
+        BatchBank<T> *bk = reinterpret_cast<BatchBank<T> *>(B.h_bank.data());
+        bk->shape = models[0];
+        for (int i = 0; i < M; ++i) bk->cst[i] = csts[i];
+    }
     if ((s = upload(ctx, B.d_states, states.data(), sizeof(State<T>) * M)) != M2M_OK) return s;
     if ((s = upload(ctx, B.d_bufs, bufs.data(), sizeof(Buffers) * M)) != M2M_OK) return s;
     if ((s = upload(ctx, B.d_seg, seg.data(), sizeof(Segment) * seg.size())) != M2M_OK) return s;
@@ -200,8 +246,8 @@ static void batch_launch(m2m_ctx *ctx)
     a.seg = B.d_seg;
     a.seg_off = B.d_seg_off;
     a.nseg = B.d_nseg;
-    using Fn = void (*)(const BatchArgs<T>);
-    reinterpret_cast<Fn>(B.kernel)<<<B.grid, B.block, B.smem, ctx->stream>>>(a);
+    const BatchBank<T> &bank = *reinterpret_cast<const BatchBank<T> *>(B.h_bank.data());
+    reinterpret_cast<BatchFn<T>>(B.kernel)<<<B.grid, B.block, B.smem, ctx->stream>>>(a, bank);
 }
 
 static m2m_status prepare(m2m_ctx *ctx)
@@ -292,7 +338,7 @@ template <class T, int WPS>
 static m2m_status batch_configure(m2m_ctx *ctx, const m2m_options *opt)
 {
     BatchState &B = *ctx->bs;
-    B.kernel = batch_pick<T, WPS>(ctx->sub);
+    B.kernel = batch_pick<T, WPS>(ctx->sub, B.bank);
     size_t smem = size_t(256) * sizeof(double);  // the finalize's block reduction
     for (const m2m_ctx *c : ctx->sub) smem = std::max(smem, smem_bytes<T>(c->m, 1, 1));
     CU(cudaDeviceGetAttribute(&B.maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
@@ -300,7 +346,7 @@ static m2m_status batch_configure(m2m_ctx *ctx, const m2m_options *opt)
     if (smem > size_t(B.maxsm))
         return fail(ctx, M2M_ERR_ARG, "the largest fit needs %zu B of shared memory (limit %d)", smem, B.maxsm);
     B.smem = smem;
-    using Fn = void (*)(const BatchArgs<T>);
+    using Fn = BatchFn<T>;
     CU(cudaFuncSetAttribute(reinterpret_cast<Fn>(B.kernel), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     B.block = opt->block > 0 ? opt->block : 256;
     if (B.block % 32 != 0 || B.block > 256) return fail(ctx, M2M_ERR_ARG, "block must be a multiple of 32, <= 256");
@@ -407,10 +453,10 @@ extern "C" m2m_status m2m_batch_autotune(m2m_ctx *ctx, int32_t steps, int32_t *b
     for (int blk : {256, 128}) {
         int occ = 0;
         if (ctx->precision == M2M_PREC_FP64) {
-            using Fn = void (*)(const BatchArgs<double>);
+            using Fn = BatchFn<double>;
             CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<Fn>(B.kernel), blk, B.smem));
         } else {
-            using Fn = void (*)(const BatchArgs<float>);
+            using Fn = BatchFn<float>;
             CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, reinterpret_cast<Fn>(B.kernel), blk, B.smem));
         }
         std::vector<int> bl;

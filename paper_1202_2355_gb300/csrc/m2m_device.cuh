@@ -708,8 +708,11 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const double *esq, c
             int b = __float2int_rd((__log2f(__double2float_rn(R2)) - G.l0) * G.lscale);
             b = b < 0 ? 0 : (b >= G.lut_n ? G.lut_n - 1 : b);
             p = G.lut_identity ? b : int(lut[G.lut_off + b]);
-            while (p > 0 && r < __double_as_longlong(e[p])) --p;
-            while (r >= __double_as_longlong(e[p + 1])) ++p;
+            // the candidate is right but within rounding of an edge or for crowded edges
+            if (r < __double_as_longlong(e[p]) || r >= __double_as_longlong(e[p + 1])) {
+                while (p > 0 && r < __double_as_longlong(e[p])) --p;
+                while (r >= __double_as_longlong(e[p + 1])) ++p;
+            }
         } else {
             int lo = 0, hi = G.n_ap;  // e[lo] <= R^2 < e[hi]
             while (hi - lo > 1) {
@@ -738,8 +741,11 @@ __device__ __forceinline__ int aperture(const GroupDesc &G, const float *e2s, co
         b = b < 0 ? 0 : (b >= G.lut_n ? G.lut_n - 1 : b);
         int p = G.lut_identity ? b : int(lut[G.lut_off + b]);
         const float *e = e2s + G.edge_off;
-        while (p > 0 && R2 < e[p]) --p;
-        while (R2 >= e[p + 1]) ++p;
+        // the candidate is right but within rounding of an edge or for crowded edges
+        if (R2 < e[p] || R2 >= e[p + 1]) {
+            while (p > 0 && R2 < e[p]) --p;
+            while (R2 >= e[p + 1]) ++p;
+        }
         return p;
     }
     const float fx = floorf((X - G.xlo_f) * G.ixw);
@@ -1384,8 +1390,8 @@ struct Acc<float> {
         if (v == 0.f) return;
         const long long L = __float2ll_rn(v * scale);
         int *h = static_cast<int *>(base) + 3 * slot;
-        const int hi = static_cast<int>(L >> 32);
-        if (hi) atomicAdd(h, hi);
+        // the hi limb is added even when 0: cheaper than the branch around it
+        atomicAdd(h, static_cast<int>(L >> 32));
         atomicAdd(h + 1, static_cast<int>((L >> 16) & 0xFFFF));
         atomicAdd(h + 2, static_cast<int>(L & 0xFFFF));
     }
@@ -1977,24 +1983,29 @@ __device__ __forceinline__ void block_tables(const Model &m, const Buffers &b, c
 // the pending force of change, the push, the deposit, the prior binning, and the
 // write-back of the state.
 template <class T, bool GA, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-__device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, const State<T> &P, const Buffers &b,
+__device__ __forceinline__ void step_particles(const Model &m, const Model &mh, const Cst<T> &k, const State<T> &P,
+                                               const Buffers &b,
                                                const Smem<T> &S, const StepFlags<T> &f, int push, long long i0,
                                                long long i1, long long stride, unsigned &err, Total<T> &wtot, T &wdep)
 {
+    // mh: the fields of the per-particle path (observable layout, regularisation and update
+    // modes, potential kind). It is the fit's own Model, or in the batched kernel one Model
+    // in the parameter space that every fit of the batch equals in those fields. m: the
+    // fit's own Model, for the prior binning and the self-consistent potential.
     // the self-consistent potential runs in the generic kernel only (the host picks it)
     constexpr bool kScf = M0 == kDyn;
     const Tables<T> tb{S.esq, S.lut, GA ? global_vp<T>(b) : S.vp, GA ? global_isp<T>(b) : S.isp, S.e2};
     const T *rec = GA ? global_records<T>(b) : S.c;
     auto deposit = [&](int slot, T v, T scale) {
         if constexpr (GA) global_add(b.hist, slot, v, scale);
-        else Acc<T>::add(S.h, m, slot, v, scale);
+        else Acc<T>::add(S.h, mh, slot, v, scale);
     };
     // the next particle's state is loaded while the current one is processed
-    const bool need_cell = f.pending && m.mode == 1;
-    const bool cache = m.ap_cache != 0;
+    const bool need_cell = f.pending && mh.mode == 1;
+    const bool cache = mh.ap_cache != 0;
     const bool need_ap = cache && f.pending;
     const bool gxc = sizeof(T) == 8 && P.gx != nullptr;  // FP64, aperture cache, a Gauss-Hermite group
-    const bool need_fa = keeps_accel<T>(m) && push;
+    const bool need_fa = keeps_accel<T>(mh) && push;
     T nx = T(0), ny = T(0), nz = T(0), nvx = T(0), nvy = T(0), nvz = T(0), nw = T(0), ngx = T(0), nfa = T(0);
     int ncell = 0;
     unsigned nap = kApUncached;
@@ -2022,47 +2033,47 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
         if constexpr (kLogWeights<T>) {
             u = wst + f.lwscale;
             if (f.pending) {
-                const T lp = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
-                u = foc_update_log<M0, M1, M2, M3>(m, k, tb, rec, code, gp, lp, u, x, y, z, vy, vz, err);
+                const T lp = mh.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
+                u = foc_update_log<M0, M1, M2, M3>(mh, k, tb, rec, code, gp, lp, u, x, y, z, vy, vz, err);
             }
             w = kexp(tb, u);
         } else {
             w = wst * f.wscale;
             if (f.pending) {
-                const T pr = m.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
-                w = foc_update<M0, M1, M2, M3>(m, k, tb, rec, code, gp, pr, w, x, y, z, vy, vz, err);
+                const T pr = mh.mode == 1 ? S.iprior[cell] : f.iwhat_flat;
+                w = foc_update<M0, M1, M2, M3>(mh, k, tb, rec, code, gp, pr, w, x, y, z, vy, vz, err);
             }
             u = w;
         }
-        if (keeps_accel<T>(m)) {
+        if (keeps_accel<T>(mh)) {
             T fa;
             if (push) {
                 fa = fa_in;
-                leapfrog_from(m, k, x, y, z, vx, vy, vz, fa);
+                leapfrog_from(mh, k, x, y, z, vx, vy, vz, fa);
             } else {
-                fa = accel_factor(m, k, x, y, z);
+                fa = accel_factor(mh, k, x, y, z);
             }
             P.fa[i] = fa;
         } else {
-            if (push) leapfrog<T, kScf>(m, k, x, y, z, vx, vy, vz);
+            if (push) leapfrog<T, kScf>(mh, k, x, y, z, vx, vy, vz);
         }
         if (!is_zero(w)) {
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
             unsigned code_out = 0;
             T gout = T(0);
-            each_group<0, M0, M1, M2, M3>(m, [&](auto Pl, int g) {
+            each_group<0, M0, M1, M2, M3>(mh, [&](auto Pl, int g) {
                 constexpr unsigned M = decltype(Pl)::mask;
-                const GroupDesc &G = m.g[g];
+                const GroupDesc &G = mh.g[g];
                 if (GP<M>::shells(G)) {  // never cached; never in the global-deposit kernel
                     shell_kernels(G, tb, x, y, z, w, [&](int j, T v, int, int) {
                         if constexpr (GA) global_add(b.hist, j, v, k.fx_gh);
-                        else Acc<T>::add(S.h, m, j, v, k.fx_gh);
+                        else Acc<T>::add(S.h, mh, j, v, k.fx_gh);
                     });
                     return;
                 }
                 const int p = aperture<M>(G, tb.esq, tb.lut, x, Y);
-                if (cache) code_out = ap_encode(m, code_out, g, p);
+                if (cache) code_out = ap_encode(mh, code_out, g, p);
                 if (p >= 0) {
                     // the v^2 sums' range assumes v^2 <= v2max (energy bound with headroom)
                     if (GP<M>::v2(G) && gt_nonneg(vlos * vlos, k.v2max)) err |= kErrOverflow;
@@ -2071,16 +2082,16 @@ __device__ __forceinline__ void step_particles(const Model &m, const Cst<T> &k, 
                         [&](int j, T v, int cls, int kk) {
                             const T scale = cls == kClassMass ? k.fx_w : (cls == kClassVel ? k.fx_v2 : k.fx_gh);
                             if constexpr (GA) {
-                                const unsigned a = unsigned(p - m.win_lo);
-                                if (g == m.win_group && a < unsigned(m.win_n))
-                                    Acc<T>::add(S.h, m, kk * m.win_n + int(a), v, scale);
+                                const unsigned a = unsigned(p - mh.win_lo);
+                                if (g == mh.win_group && a < unsigned(mh.win_n))
+                                    Acc<T>::add(S.h, mh, kk * mh.win_n + int(a), v, scale);
                                 else
                                     global_add(b.hist, j, v, scale);
                             } else {
-                                Acc<T>::add(S.h, m, j, v, scale);
+                                Acc<T>::add(S.h, mh, j, v, scale);
                             }
                         },
-                        gxc && g == m.gx_group ? &gout : nullptr);
+                        gxc && g == mh.gx_group ? &gout : nullptr);
                     if constexpr (kScf) {
                         if (f.scf_step && m.n_dups > 0)  // derivatives for the mass-to-light ratio (Sec. 6)
                             group_dkernels<M>(G, tb, p, vlos, w, [&](int j, T v, int cls) {
@@ -2173,7 +2184,7 @@ __global__ void __launch_bounds__(kStepMaxThreads<T, GA>, (GA && sizeof(T) == 4)
     unsigned err = 0;
     Total<T> wtot;
     T wdep = T(0);  // floating-point twin of wtot, for the fixed-point range check
-    step_particles<T, GA, M0, M1, M2, M3>(m, k, P, b, S, f, push, (long long)blockIdx.x * blockDim.x + threadIdx.x,
+    step_particles<T, GA, M0, M1, M2, M3>(m, m, k, P, b, S, f, push, (long long)blockIdx.x * blockDim.x + threadIdx.x,
                                           P.n, (long long)gridDim.x * blockDim.x, err, wtot, wdep);
     block_flush<T, WPS, GA>(m, k, b, S, f.prior_step, err, wtot, wdep, f.scf_step);
     if (m.shard) return;  // the sums of all shards are added by the caller; k_finalize follows
@@ -2254,8 +2265,26 @@ struct BatchArgs {
 static_assert(sizeof(Model) % 8 == 0 && sizeof(Cst<float>) % 8 == 0 && sizeof(Cst<double>) % 8 == 0,
               "descriptor copies need whole 8-byte words");
 
-template <class T, int WPS, int MINB, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
-__global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a)
+// The per-fit constants of a batch in the kernel's parameter space (the constant bank): the
+// per-particle loop reads them there, where no store can alias them, instead of from copies
+// in shared memory that every shared-memory atomic of the deposit could have changed.
+// shape: a Model that every fit of the batch equals in the fields of the per-particle path
+// (see step_particles); cst[i]: the constants of fit i. With more fits than the bank holds,
+// or fits that differ in those fields, the kernel runs from the shared-memory copies.
+template <class T>
+constexpr int kBankFits = sizeof(T) == 8 ? 112 : 224;
+
+template <class T>
+struct BatchBank {
+    Model shape;
+    Cst<T> cst[kBankFits<T>];
+};
+static_assert(sizeof(BatchBank<float>) + sizeof(BatchArgs<float>) <= 32764 &&
+                  sizeof(BatchBank<double>) + sizeof(BatchArgs<double>) <= 32764,
+              "kernel parameters are limited to 32764 bytes");
+
+template <class T, int WPS, int MINB, bool BANK, unsigned M0, unsigned M1, unsigned M2, unsigned M3>
+__global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a, const __grid_constant__ BatchBank<T> bank)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(16) unsigned long long mbuf[(sizeof(Model) + 7) / 8];
@@ -2294,8 +2323,12 @@ __global__ void __launch_bounds__(256, MINB) k_step_batch(const BatchArgs<T> a)
         unsigned err = 0;
         Total<T> wtot;
         T wdep = T(0);
-        step_particles<T, false, M0, M1, M2, M3>(m, k, P, b, S, f, 1, sg.begin + threadIdx.x, sg.end, blockDim.x,
-                                                 err, wtot, wdep);
+        if constexpr (BANK)
+            step_particles<T, false, M0, M1, M2, M3>(m, bank.shape, bank.cst[sg.model], P, b, S, f, 1,
+                                                     sg.begin + threadIdx.x, sg.end, blockDim.x, err, wtot, wdep);
+        else
+            step_particles<T, false, M0, M1, M2, M3>(m, m, k, P, b, S, f, 1, sg.begin + threadIdx.x, sg.end,
+                                                     blockDim.x, err, wtot, wdep);
         block_flush<T, WPS, false>(m, k, b, S, f.prior_step, err, wtot, wdep, f.scf_step);
         if (threadIdx.x == 0) am_last = atomicAdd(&b.sc->blocks_done, 1u) == a.nseg[cur] - 1;
         __syncthreads();
