@@ -1359,14 +1359,26 @@ struct Acc;
 template <>
 struct Acc<double> {
     static __host__ __device__ size_t bytes(const Model &m) { return sizeof(long long) * size_t(m.hist_words); }
+    // the fixed-point value of v * scale (two words)
+    struct Fx {
+        long long hi, lo;
+    };
+    __device__ static Fx fx(double v, double scale)
+    {
+        Fx r;
+        fx2(v, scale, r.hi, r.lo);
+        return r;
+    }
+    __device__ static void put(void *base, int slot, const Fx &q)
+    {
+        long long *h = static_cast<long long *>(base);
+        atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot), static_cast<unsigned long long>(q.hi));
+        if (q.lo) atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot + 1), static_cast<unsigned long long>(q.lo));
+    }
     __device__ static void add(void *base, const Model &, int slot, double v, double scale)
     {
         if (is_zero(v)) return;
-        long long *h = static_cast<long long *>(base);
-        long long hi, lo;
-        fx2(v, scale, hi, lo);
-        atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot), static_cast<unsigned long long>(hi));
-        if (lo) atomicAdd(reinterpret_cast<unsigned long long *>(h + 2 * slot + 1), static_cast<unsigned long long>(lo));
+        put(base, slot, fx(v, scale));
     }
     __device__ static void count(void *base, const Model &m, int c)
     {
@@ -1385,15 +1397,23 @@ struct Acc<float> {
     // round(v*scale) as L = hi 2^32 + mid 2^16 + lo with mid, lo in [0, 2^16) and hi signed:
     // the two's-complement fields of one 64-bit conversion. Per block the lo and mid sums
     // stay below 32768 * 65535 < 2^31, and the hi sum within the fixed-point range.
+    // the fixed-point value of v * scale (one 64-bit integer)
+    struct Fx {
+        long long L;
+    };
+    __device__ static Fx fx(float v, float scale) { return Fx{__float2ll_rn(v * scale)}; }
+    __device__ static void put(void *base, int slot, const Fx &q)
+    {
+        int *h = static_cast<int *>(base) + 3 * slot;
+        // the hi limb is added even when 0: cheaper than the branch around it
+        atomicAdd(h, static_cast<int>(q.L >> 32));
+        atomicAdd(h + 1, static_cast<int>((q.L >> 16) & 0xFFFF));
+        atomicAdd(h + 2, static_cast<int>(q.L & 0xFFFF));
+    }
     __device__ static void add(void *base, const Model &, int slot, float v, float scale)
     {
         if (v == 0.f) return;
-        const long long L = __float2ll_rn(v * scale);
-        int *h = static_cast<int *>(base) + 3 * slot;
-        // the hi limb is added even when 0: cheaper than the branch around it
-        atomicAdd(h, static_cast<int>(L >> 32));
-        atomicAdd(h + 1, static_cast<int>((L >> 16) & 0xFFFF));
-        atomicAdd(h + 2, static_cast<int>(L & 0xFFFF));
+        put(base, slot, fx(v, scale));
     }
     __device__ static void count(void *base, const Model &m, int c)
     {
@@ -1422,6 +1442,11 @@ struct Total<double> {
         hi += a;
         lo += b;
     }
+    __device__ void add_fx(const Acc<double>::Fx &q)
+    {
+        hi += q.hi;
+        lo += q.lo;
+    }
     __device__ long long word(int q, double) const { return q == 0 ? hi : lo; }
 };
 
@@ -1432,6 +1457,7 @@ template <>
 struct Total<float> {
     long long s = 0;
     __device__ void add(float v, float scale) { s += __float2ll_rn(v * scale); }
+    __device__ void add_fx(const Acc<float>::Fx &q) { s += q.L; }
     __device__ long long word(int, float) const { return s; }
 };
 
@@ -2060,6 +2086,8 @@ __device__ __forceinline__ void step_particles(const Model &m, const Model &mh, 
         if (!is_zero(w)) {
             T Y, vlos;
             project(k, y, z, vy, vz, Y, vlos);
+            // the fixed-point weight, shared by the total and the surface-mass deposits
+            const auto wfx = Acc<T>::fx(w, k.fx_w);
             unsigned code_out = 0;
             T gout = T(0);
             each_group<0, M0, M1, M2, M3>(mh, [&](auto Pl, int g) {
@@ -2087,6 +2115,8 @@ __device__ __forceinline__ void step_particles(const Model &m, const Model &mh, 
                                     Acc<T>::add(S.h, mh, kk * mh.win_n + int(a), v, scale);
                                 else
                                     global_add(b.hist, j, v, scale);
+                            } else if (cls == kClassMass) {  // v is w (the kernel is 1)
+                                Acc<T>::put(S.h, j, wfx);
                             } else {
                                 Acc<T>::add(S.h, mh, j, v, scale);
                             }
@@ -2106,7 +2136,7 @@ __device__ __forceinline__ void step_particles(const Model &m, const Model &mh, 
             }
             if (cache) P.ap[i] = static_cast<uint16_t>(code_out);
             if (gxc) P.gx[i] = gout;
-            wtot.add(w, k.fx_w);
+            wtot.add_fx(wfx);
             wdep += w;
         }
         if (f.prior_step) {
