@@ -94,6 +94,55 @@ def scan(n: int, n_target: int, steps: int, mus, precision: str = "mixed", modes
             yield row
 
 
+# initial particle models of the experiment of Sec. 4.3 (Table trunc_ics): Hernquist spheres,
+# isotropic, radially or tangentially biased (constant sigma_r/sigma_t standing in for the
+# paper's Osipkov-Merritt and quasi-separable models). The paper also gives them a larger
+# scale length (a = 1.5); here a = 1: at a = 1.5 the initial chi^2/J is ~500 and the explicit
+# update at this workload's eps dt overflows the weights within the first steps.
+INITIAL = {"iso": 1.0, "rad": 2.0, "tan": 0.7}
+
+
+def initial_model(n: int, kind: str, a: float = 1.0) -> dict:
+    ratio = INITIAL[kind]
+    beta = 1.0 - 1.0 / ratio ** 2
+    tab = synth.jeans_sigma2_table(lambda r: synth.hernquist_density(r, a=a), synth.hernquist_mass, beta=beta)
+    s2 = lambda r: synth.sigma2_from_table(tab, r) * (3.0 - 2.0 * beta) / 3.0  # noqa: E731
+    return synth.realise_spherical(0, n, s2, a=a, anisotropy=ratio)
+
+
+def vary_initial(n: int, n_target: int, steps: int, mu_of: dict, precision: str = "mixed", lattice=(90, 30),
+                 window=(1, 1)):
+    """Sec. 4.3: the same target and data fitted from each initial model of INITIAL, with each
+    regularisation at its own mu (mu_of: mode -> mu); yields the initial model's marks
+    (mode 'initial') and each final model's."""
+    wl = workload(n, n_target)
+    Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
+    tg = tk = None
+    for ic in INITIAL:
+        wl.model = initial_model(n, ic)
+        for mode in ("initial",) + tuple(mu_of):
+            mu = mu_of.get(mode, 0.0)
+            if mode == "mprw":
+                prior = dict(wl.prior, mode="mpr", nE=lattice[0], nx=lattice[1], window=window)
+            else:
+                prior = dict(wl.prior, mode="gwr" if mode == "initial" else mode)
+            fit = B.fit_from_workload(wl, Y, sig, Vp, sp, precision=precision, prior=prior,
+                                      params=dict(wl.params, mu=mu))
+            fit.load(wl.model)
+            if tg is None:
+                tg, _, _ = fit.diag_grid(wl.prior, particles=wl.target)
+                tk = fit.diag_kinematics(SHELLS, particles=wl.target)
+            if mode == "initial":
+                marks = assess(fit, wl, tg, tk)
+                fit.step(1)
+            else:
+                fit.step(steps)
+                marks = assess(fit, wl, tg, tk)
+            yield dict(initial=ic, mode=mode, mu=mu, steps=0 if mode == "initial" else steps,
+                       chi2_per_J=fit.chi2() / fit.J, **marks)
+            fit.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -104,8 +153,19 @@ def main():
     ap.add_argument("--modes", default="gwr,mpr", help="any of gwr, mpr, mprw (grid-less window priors)")
     ap.add_argument("--lattice", default="90,30", help="mprw: nE,nx of the prior lattice")
     ap.add_argument("--window", default="1,1", help="mprw: half widths of the window, in lattice cells")
+    ap.add_argument("--initial-models", action="store_true",
+                    help="Sec. 4.3: fit from isotropic, radial and tangential initial models, each mode at "
+                         "the mu given as --ic-mu gwr=...,mpr=...,mprw=...")
+    ap.add_argument("--ic-mu", default="gwr=1e4,mpr=1e5,mprw=1e5")
     a = ap.parse_args()
     mus = [float(x) for x in a.mu.split(",")]
+    if a.initial_models:
+        mu_of = {k: float(v) for k, v in (kv.split("=") for kv in a.ic_mu.split(","))}
+        print(f"{'initial':8s} {'mode':8s} {'mu':>8s} {'chi2/J':>8s} {'D_grid':>8s} {'D_kin':>8s}")
+        for r in vary_initial(a.n, a.n_target, a.steps, mu_of, a.precision):
+            print(f"{r['initial']:8s} {r['mode']:8s} {r['mu']:8.3g} {r['chi2_per_J']:8.3f} {r['delta_grid']:8.4f} "
+                  f"{r['delta_kin']:8.4f}  " + json.dumps(r), flush=True)
+        return
     lattice = tuple(int(v) for v in a.lattice.split(","))
     window = tuple(int(v) for v in a.window.split(","))
     print(f"{'mode':8s} {'mu':>8s} {'chi2/J':>8s} {'D_grid':>8s} {'D_kin':>8s} {'rms w/w0':>9s}")
