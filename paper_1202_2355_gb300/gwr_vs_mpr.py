@@ -31,6 +31,8 @@ from __future__ import annotations
 import argparse
 import json
 
+import numpy as np
+
 from . import binding as B
 from . import synth
 from . import workloads as W
@@ -40,10 +42,15 @@ SHELLS = dict(n_r=21, n_phi=1, n_ct=1, r_min=0.01, r_max=50.0)
 RATIO = 1.5  # sigma_r / sigma_t of the target
 
 
-def workload(n: int, n_target: int) -> W.Workload:
+def workload(n: int, n_target: int, alm: bool = False) -> W.Workload:
     """The 1M-particle workload's observables and potential; isotropic initial model
-    of n particles (seed 0) and an anisotropic target of n_target particles (seed 100)."""
+    of n particles (seed 0) and an anisotropic target of n_target particles (seed 100).
+    alm: add the 3-D density of eq. alm on 30 quasi-logarithmic radii in [0.05, 20] (a_00 and
+    a_20, errors at the target's shot noise), which constrains the mass in energy."""
     wl = W.make("c2", n=1000, n_target=1000)
+    if alm:
+        radii = np.exp(np.linspace(np.log(0.05), np.log(20.0), 30))
+        wl.groups = wl.groups + [W.Group("shells", ["alm_0_0", "alm_2_0"], [1.0, 1.0], edges=radii)]
     beta = 1.0 - 1.0 / RATIO ** 2
     tab = synth.jeans_sigma2_table(synth.hernquist_density, synth.hernquist_mass, beta=beta)
     # realise_spherical splits 3 sigma^2 into sigma_r^2 + 2 sigma_t^2 at the given ratio
@@ -68,8 +75,8 @@ def assess(fit: B.Fit, wl: W.Workload, target_grid, target_kin, min_count: int =
 
 
 def scan(n: int, n_target: int, steps: int, mus, precision: str = "mixed", modes=("gwr", "mpr"),
-         lattice=(90, 30), window=(1, 1)):
-    wl = workload(n, n_target)
+         lattice=(90, 30), window=(1, 1), alm: bool = False):
+    wl = workload(n, n_target, alm)
     Y, sig, Vp, sp, _ = B.build_targets(wl.groups, wl.incl_deg, wl.target, wl.err_per_obs(), wl.noise)
     for mode in ("initial",) + tuple(modes):
         for mu in ([0.0] if mode == "initial" else mus):
@@ -153,6 +160,7 @@ def main():
     ap.add_argument("--modes", default="gwr,mpr", help="any of gwr, mpr, mprw (grid-less window priors)")
     ap.add_argument("--lattice", default="90,30", help="mprw: nE,nx of the prior lattice")
     ap.add_argument("--window", default="1,1", help="mprw: half widths of the window, in lattice cells")
+    ap.add_argument("--alm", action="store_true", help="add the 3-D density data a_00, a_20 on 30 radii")
     ap.add_argument("--initial-models", action="store_true",
                     help="Sec. 4.3: fit from isotropic, radial and tangential initial models, each mode at "
                          "the mu given as --ic-mu gwr=...,mpr=...,mprw=...")
@@ -169,7 +177,7 @@ def main():
     lattice = tuple(int(v) for v in a.lattice.split(","))
     window = tuple(int(v) for v in a.window.split(","))
     print(f"{'mode':8s} {'mu':>8s} {'chi2/J':>8s} {'D_grid':>8s} {'D_kin':>8s} {'rms w/w0':>9s}")
-    for r in scan(a.n, a.n_target, a.steps, mus, a.precision, tuple(a.modes.split(",")), lattice, window):
+    for r in scan(a.n, a.n_target, a.steps, mus, a.precision, tuple(a.modes.split(",")), lattice, window, a.alm):
         print(f"{r['mode']:8s} {r['mu']:8.3g} {r['chi2_per_J']:8.3f} {r['delta_grid']:8.4f} "
               f"{r['delta_kin']:8.4f} {r['weight_rms_rel']:9.4f}  " + json.dumps(r), flush=True)
 
