@@ -313,6 +313,12 @@ m2m_status m2m_batch_size(m2m_ctx *batch, int32_t *nmodels);
  * nothing). Stepping it alone advances only that fit. */
 m2m_status m2m_batch_model(m2m_ctx *batch, int32_t i, m2m_ctx **model);
 
+/* chi^2 of the last step of every fit of the batch (eq. chi), nmodels values in fit
+ * order, in one device-to-host copy; synchronises the batch's stream and reports the
+ * first fit whose step flagged an error, like m2m_synchronize. The per-fit call
+ * m2m_get_chi2 on each handle gives the same values with one copy per fit. */
+m2m_status m2m_batch_get_chi2(m2m_ctx *batch, double *chi2, int32_t nmodels);
+
 /* Times the batched step for a set of launch shapes (threads per block, resident
  * blocks per SM, particles per segment; a segment is a contiguous run of one
  * fit's particles that a block processes before flushing its sums), each over

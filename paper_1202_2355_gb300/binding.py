@@ -139,6 +139,8 @@ def lib():
         L.m2m_step_begin.argtypes = [vp]
         L.m2m_step_end.argtypes = [vp]
         L.m2m_shard_weights_begin.argtypes = [vp]
+        L.m2m_batch_get_chi2.argtypes = [vp, _DP, C.c_int32]
+        L.m2m_batch_get_chi2.restype = C.c_int
         L.m2m_get_scf.argtypes = [vp, _DP, _DP, C.c_int32]
         L.m2m_get_scf.restype = C.c_int
         for name in ("m2m_diag_kinematics", "m2m_diag_grid", "m2m_kin_moments", "m2m_delta_kin",
@@ -542,6 +544,12 @@ class Batch:
 
     def synchronize(self):
         self._ck(lib().m2m_synchronize(self.h))
+
+    def chi2(self) -> np.ndarray:
+        """chi^2 of the last step of every fit, in one copy (m2m_batch_get_chi2)."""
+        out = np.zeros(len(self.fits))
+        self._ck(lib().m2m_batch_get_chi2(self.h, _dp(out), len(self.fits)))
+        return out
 
     def autotune(self, steps: int = 3):
         """(threads per block, blocks per SM, particles per segment) kept by the autotuner."""

@@ -33,6 +33,8 @@ struct BatchState {
     Segment *d_seg = nullptr;
     int *d_seg_off = nullptr;
     unsigned *d_nseg = nullptr;
+    Scalars **d_scs = nullptr;    // the fits' scalars, for m2m_batch_get_chi2
+    double *d_chi2 = nullptr;     // per fit: chi^2 and the error word (as a double)
     std::vector<long long> gens;  // the fits' load generations the arrays were built for
     bool ready = false;
     cudaGraphExec_t graph = nullptr;
@@ -168,6 +170,8 @@ static void free_arrays(BatchState &B)
     free_dev(B.d_seg);
     free_dev(B.d_seg_off);
     free_dev(B.d_nseg);
+    free_dev(B.d_scs);
+    free_dev(B.d_chi2);
     if (B.graph) cudaGraphExecDestroy(B.graph);
     B.graph = nullptr;
     B.ready = false;
@@ -228,6 +232,10 @@ static m2m_status batch_prepare(m2m_ctx *ctx)
     if ((s = upload(ctx, B.d_seg, seg.data(), sizeof(Segment) * seg.size())) != M2M_OK) return s;
     if ((s = upload(ctx, B.d_seg_off, off.data(), sizeof(int) * off.size())) != M2M_OK) return s;
     if ((s = upload(ctx, B.d_nseg, nseg.data(), sizeof(unsigned) * nseg.size())) != M2M_OK) return s;
+    std::vector<Scalars *> scs(M);
+    for (int i = 0; i < M; ++i) scs[i] = ctx->sub[i]->d_sc;
+    if ((s = upload(ctx, B.d_scs, scs.data(), sizeof(Scalars *) * M)) != M2M_OK) return s;
+    CU(cudaMalloc(&B.d_chi2, sizeof(double) * 2 * M));
     B.nseg_total = (long long)seg.size();
     B.gens = gens;
     B.ready = true;
@@ -316,6 +324,39 @@ m2m_status batch_synchronize(m2m_ctx *ctx)
         if (!c->loaded) continue;
         const m2m_status s = check_device_errors(c);
         if (s != M2M_OK) return fail(ctx, s, "fit %zu: %s", i, c->err.c_str());
+    }
+    return M2M_OK;
+}
+
+// chi^2 and the error word of every fit, gathered for one copy to the host.
+static __global__ void k_batch_chi2(Scalars *const *scs, double *out, int M)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        out[2 * i] = scs[i]->chi2;
+        out[2 * i + 1] = double(scs[i]->err);
+    }
+}
+
+extern "C" m2m_status m2m_batch_get_chi2(m2m_ctx *ctx, double *chi2, int32_t nmodels)
+{
+    if (!ctx) return M2M_ERR_ARG;
+    if (ctx->sub.empty()) return fail(ctx, M2M_ERR_STATE, "not a batch context");
+    const int M = int(ctx->sub.size());
+    if (nmodels != M || !chi2) return fail(ctx, M2M_ERR_ARG, "chi2 must hold the batch's %d values", M);
+    m2m_status s = prepare(ctx);
+    if (s != M2M_OK) return s;
+    BatchState &B = *ctx->bs;
+    std::vector<double> h(2 * size_t(M));
+    k_batch_chi2<<<(M + 127) / 128, 128, 0, ctx->stream>>>(B.d_scs, B.d_chi2, M);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(h.data(), B.d_chi2, sizeof(double) * 2 * M, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < M; ++i) {
+        chi2[i] = h[2 * i];
+        if (h[2 * i + 1] != 0.0) {  // the fit's own check decodes the error word
+            s = check_device_errors(ctx->sub[i]);
+            if (s != M2M_OK) return fail(ctx, s, "fit %d: %s", i, ctx->sub[i]->err.c_str());
+        }
     }
     return M2M_OK;
 }

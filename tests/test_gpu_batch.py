@@ -71,6 +71,7 @@ def test_batch_is_bit_identical_to_separate_fits(precision):
     batch.step(30)
     batch.synchronize()
     got = [_snapshot(f) for f in batch.fits]
+    chi2_all = batch.chi2()
     batch.close()
     for wl, t, g in zip(wls, targets, got):
         f = B.fit_from_workload(wl, t[1], t[2], t[0].Vp, t[0].sp, precision=precision)
@@ -78,6 +79,8 @@ def test_batch_is_bit_identical_to_separate_fits(precision):
         f.step(30)
         _same(g, _snapshot(f))
         f.close()
+    # the batched chi^2 read gives every fit's own value
+    assert np.array_equal(np.array([g["chi2"] for g in got]), chi2_all, equal_nan=True)
 
 
 def test_batch_fits_match_the_oracle_fp64():
