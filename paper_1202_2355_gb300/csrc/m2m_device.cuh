@@ -1410,9 +1410,9 @@ struct Acc<float> {
         atomicAdd(h + 1, static_cast<int>((q.L >> 16) & 0xFFFF));
         atomicAdd(h + 2, static_cast<int>(q.L & 0xFFFF));
     }
+    // a zero adds zeros: cheaper than the branch around it
     __device__ static void add(void *base, const Model &, int slot, float v, float scale)
     {
-        if (v == 0.f) return;
         put(base, slot, fx(v, scale));
     }
     __device__ static void count(void *base, const Model &m, int c)
