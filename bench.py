@@ -85,7 +85,7 @@ ACCEL_BYTES_MIXED = 8
 # the capture); absent: not captured since the kernel last changed. c5: the 12-fit
 # subset of the batch (fits 0, 8, ..., 88), traffic scaled to a full launch by the
 # particle count; c2: the whole 1M-particle fit.
-DRAM_PER_UNIT = {("c5", "mixed"): (63.93, 8_384_798), ("c2", "fp64"): (89.77, 1_000_000)}
+DRAM_PER_UNIT = {("c5", "mixed"): (63.82, 8_384_798), ("c2", "fp64"): (89.77, 1_000_000)}
 
 
 class ClockSampler:
