@@ -17,6 +17,35 @@ def weight_err(w_gpu, w_ora, W0, n):
     return np.abs(w_gpu - w_ora) / (np.abs(w_ora) + W0 / max(n, 1))
 
 
+def edge_flip_allowance(groups, p, w, J, incl_deg=0.0):
+    """Per observable, the most that particles within FP32 rounding of an annulus edge (R^2
+    within 1e-6 relative) can move between the two annuli beside that edge: w |K| for each,
+    with K = 1/area for surface mass, v_los^2 for v2 and 1.5 (the bound on 2 sqrt(pi) |u_n|)
+    for a Gauss-Hermite kind. FP32 and FP64 may put such a particle in different annuli."""
+    allow = np.zeros(J)
+    si, ci = np.sin(np.radians(incl_deg)), np.cos(np.radians(incl_deg))
+    Y = p["y"] * ci - p["z"] * si
+    R2 = p["x"] ** 2 + Y ** 2
+    vlos = p["vy"] * si + p["vz"] * ci
+    off = 0
+    for g in groups:
+        if g.geometry != "annuli":
+            off += len(g.kinds) * g.n_ap
+            continue
+        e2 = np.asarray(g.edges, np.float64) ** 2
+        k = np.clip(np.searchsorted(e2, R2), 1, len(e2) - 1)
+        k = np.where(np.abs(R2 / e2[k - 1] - 1) < np.abs(R2 / e2[k] - 1), k - 1, k)  # nearest edge
+        for i in np.nonzero(np.abs(R2 / e2[k] - 1) < 1e-6)[0]:
+            for kk, kind in enumerate(g.kinds):
+                K = (1.0 / (np.pi * (e2[1:] - e2[:-1])) if kind == "mass" else
+                     np.full(g.n_ap, vlos[i] ** 2) if kind == "v2" else np.full(g.n_ap, 1.5))
+                for a in (k[i] - 1, k[i]):
+                    if 0 <= a < g.n_ap:
+                        allow[off + kk * g.n_ap + a] += w[i] * K[a]
+        off += len(g.kinds) * g.n_ap
+    return allow
+
+
 class Pair:
     """The same fit run by the oracle and by the CUDA library."""
 
