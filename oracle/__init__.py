@@ -13,7 +13,9 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SO = os.path.join(_HERE, "_build", "liboracle.so")
+# M2M_ORACLE_SO names a library built elsewhere (the mutation test of the pins loads
+# deliberately broken copies of the oracle this way); it is then used as it is.
+_SO = os.environ.get("M2M_ORACLE_SO") or os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 MAX_GROUPS = 4
@@ -41,6 +43,8 @@ def kind_code(name: str) -> int:
 def build(force: bool = False) -> str:
     """Compile the oracle C source into a shared library (gcc, -ffp-contract=off)."""
     src = os.path.join(_HERE, "m2m_oracle.c")
+    if os.environ.get("M2M_ORACLE_SO"):
+        return _SO
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "m2m_oracle.h"))):
         os.makedirs(os.path.dirname(_SO), exist_ok=True)
