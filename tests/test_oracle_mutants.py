@@ -50,6 +50,17 @@ MUTANTS = [
     ("window: the upper edge left out", "for (int k2 = k - hE; k2 <= k + hE; ++k2)",
      "for (int k2 = k - hE; k2 < k + hE; ++k2)"),
     ("window: cells counted instead of particles", "nc += count[k2 * nx + l2];", "nc += 1;"),
+    ("self-consistent potential: inner shell power", "                f = pow(r, l) / pow(rk, l + 1);",
+     "                f = pow(r, l + 1) / pow(rk, l + 1);"),
+    ("self-consistent potential: outer radial derivative sign", "df = -(l + 1) * pow(rk, l) / pow(r, l + 2);",
+     "df = (l + 1) * pow(rk, l) / pow(r, l + 2);"),
+    ("self-consistent potential: multipole constant", "double C = -4.0 * OR_PI * p->G / (2.0 * l + 1.0);",
+     "double C = -4.0 * OR_PI * p->G / (2.0 * l - 1.0);"),
+    ("cloud in cell: weights swapped", "g0 = (p->scf_r[k0 + 1] - r) / d;", "g0 = (r - p->scf_r[k0]) / d;"),
+    ("smoothing: penalty sign", "for (size_t q = 0; q < (size_t)n * n; ++q) M[q] = lambda * P[q];",
+     "for (size_t q = 0; q < (size_t)n * n; ++q) M[q] = -lambda * P[q];"),
+    ("delta_grid: relative to the model", "double r = (wt - wm) / wt;", "double r = (wt - wm) / wm;"),
+    ("kinematic sums: second moment linear", "o[4 + c] += w * v[c] * v[c];", "o[4 + c] += w * v[c];"),
 ]
 
 
