@@ -61,6 +61,14 @@ MUTANTS = [
      "for (size_t q = 0; q < (size_t)n * n; ++q) M[q] = -lambda * P[q];"),
     ("delta_grid: relative to the model", "double r = (wt - wm) / wt;", "double r = (wt - wm) / wm;"),
     ("kinematic sums: second moment linear", "o[4 + c] += w * v[c] * v[c];", "o[4 + c] += w * v[c];"),
+    ("associated legendre: recurrence index", "double p2 = (x * (2.0 * ll - 1.0) * p1 - (ll + am - 1.0) * p0) / (ll - am);",
+     "double p2 = (x * (2.0 * ll - 1.0) * p1 - (ll + am) * p0) / (ll - am);"),
+    ("real harmonics: cos and sin swapped", "if (m > 0) return sqrt(2.0) * N * plm * cos(am * phi);",
+     "if (m > 0) return sqrt(2.0) * N * plm * sin(am * phi);"),
+    ("shell cloud in cell: weight of the outer point", "g_out[1] = (r - e[k - 1]) / d;", "g_out[1] = (e[k] - r) / d;"),
+    ("target fit: sign of the V_p correction", "V[p] += sqrt(2.0) * s_old * h1;", "V[p] -= sqrt(2.0) * s_old * h1;"),
+    ("circular orbit: L from v_c^2", "return R * sqrt(vc2);", "return R * vc2;"),
+    ("circularity: not normalised", "double xc = (Lc > 0.0) ? L / Lc : 0.0;", "double xc = (Lc > 0.0) ? L : 0.0;"),
 ]
 
 
