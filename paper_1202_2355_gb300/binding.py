@@ -284,6 +284,9 @@ def weight_rms(wdev2, counts, min_count: int = 50) -> float:
 
 
 def prior_grid(d: dict) -> PriorGrid:
+    """m2m_prior_grid from a dict: mode ('gwr'/'mpr'), nE, nx, e_spacing, signed_lz,
+    update_every, Emin, Emax; optional smoothing (0/1) with lambda, or window (half widths
+    in cells, E then x) for the grid-less priors."""
     return PriorGrid(MODE[d["mode"]], d["nE"], d["nx"], ESPACING[d["e_spacing"]], d["signed_lz"],
                      d["update_every"], d["Emin"], d["Emax"], int(d.get("smoothing", 0)),
                      float(d.get("lambda", 0.0)), *(int(v) for v in d.get("window", (0, 0))))
