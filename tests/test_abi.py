@@ -69,10 +69,10 @@ def test_binding_structs_match_the_header(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    pairs = [("m2m_potential", B.Potential, ["kind", "G", "q"]),
+    pairs = [("m2m_potential", B.Potential, ["kind", "G", "q", "scf_n", "scf_lmax", "scf_r", "ups", "eps_ups"]),
              ("m2m_obs_group", B.ObsGroup, ["geometry", "edges", "n_kinds", "kinds", "Vp", "sp"]),
              ("m2m_observables", B.Observables, ["incl_deg", "n_groups", "groups", "Y", "sigY"]),
-             ("m2m_prior_grid", B.PriorGrid, ["mode", "Emin", "smoothing", "lambda"]),
+             ("m2m_prior_grid", B.PriorGrid, ["mode", "Emin", "smoothing", "lambda", "window_E", "window_x"]),
              ("m2m_options", B.Options, ["precision", "dt", "stream", "block", "deposit"]),
              ("m2m_sph_grid", B.SphGrid, ["n_r", "r_min", "r_max"])]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "m2m.h"', "int main(void) {"]
