@@ -49,3 +49,20 @@ def test_roofline_headline_is_the_method_byte_fraction(bench):
         assert r["achieved"] == pytest.approx(b * 1e6 / 1e-3 / 1e9)
         assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert "alu" in bench.roofline("c2", "fp64", 1_000_000, 1.0)
+
+
+def test_reference_arm_runs_on_the_host_and_prints_one_line():
+    """bench.py --impl reference times the oracle on the host cores: one JSON line with the
+    reference fields, on a machine without a GPU as well."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
